@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark: time-to-1e-8 residual and smoother GDOF/s, SEM E=32^3 N=7, mixed vs FP64.
+
+Workload: the 3-D spectral-element Poisson problem on the perturbed unit box
+(E = 32^3 trilinear hexahedra, N = 7, n = 11,390,625 global DOFs), p-multigrid
+7 -> 3 -> 1 with the optimized 4th-kind Chebyshev smoother in the one-sided
+(4, 0) V-cycle (k = 2), flexible CG to a 1e-8 relative residual, uniform[-1,1]
+right-hand side (seed 1).  One "step" is one complete solve.
+
+value      = whole-job solve throughput: n * solves / seconds / 1e9 (GDOF/s solved to 1e-8)
+             for the mixed form (FP32 smoother/Ax/transfers, FP64 Krylov, Lanczos and coarse CG),
+             inputs resident in HBM.  time_to_1e8_s gives seconds per solve for both forms.
+e2e        = the same metric through chebmg_pcg_solve_host with pinned host b and u
+             (H2D of b and D2H of u inside the timed region).
+roofline   = the fine-level Chebyshev smoother step (element Ax + gather-scatter + recurrence),
+             algorithmic bytes w (6 L + 7 n) per step, against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference = the FP64 oracle (numpy, single thread) solving the same
+             recipe at E = 16^3 (a bounded sample), in the same unit.
+
+Replicas only: with N GPUs every rank solves its own copy (weak scaling, no collective on
+the data path); the timed region is bracketed by barriers and the max over ranks is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NE, NORDER, ORDERS, KIND, K_ORDER, SIDED = 32, 7, (7, 3, 1), "opt4th", 2, "one-sided"
+RTOL = 1e-8
+SAMPLE_NE = 16
+METRIC = "time-to-1e-8 residual and smoother GDOF/s, SEM E=32^3 N=7, mixed vs FP64"
+UNIT = "GDOF/s (DOFs solved to 1e-8 rel. residual per second)"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def config(extra=None):
+    c = {"workload": f"SEM Poisson E={NE}^3 N={NORDER}, p-MG {ORDERS}, {KIND} Chebyshev one-sided "
+                     f"({2 * K_ORDER},0), FCG to 1e-8",
+         "E": NE ** 3, "N": NORDER, "n_dof": (NE * NORDER + 1) ** 3, "orders": list(ORDERS),
+         "smoother": KIND, "k": K_ORDER, "sided": SIDED, "rtol": RTOL,
+         "l2": "inputs larger than L2 (FP32+FP64 geometric factors 1.2 GB, vectors 91 MB each)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline): one FP64 solve at E=16^3
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import workloads as W
+from oracle import krylov as K, multigrid as M, problems as P
+ne = %(ne)d
+v = W.sem_box_vertices(ne, ne, ne)
+H = P.sem_hierarchy(v, %(orders)r, kind=%(kind)r, k=%(k)d, sided=%(sided)r)
+b = W.sem_rhs(ne, ne, ne, %(N)d)
+times = []
+for _ in range(%(reps)d):
+    t = time.perf_counter()
+    x, it, hist = K.fcg(H.levels[0].apply_A, lambda r: M.vcycle(H, r), b, %(rtol)r)
+    times.append(time.perf_counter() - t)
+print(json.dumps({"n": H.levels[0].n, "iters": it, "times": times}))
+"""
+
+
+def run_oracle(reps: int):
+    code = ORACLE_SNIPPET % dict(root=ROOT, ne=SAMPLE_NE, orders=ORDERS, kind=KIND, k=K_ORDER, sided=SIDED,
+                                 N=NORDER, rtol=RTOL, reps=reps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def sample_desc(r):
+    return (f"FP64 numpy oracle, one thread, full FCG solve of the same recipe at E={SAMPLE_NE}^3 "
+            f"(n={r['n']}, {r['iters']} iterations), setup excluded")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
+                    help="set up, warm up, run one solve inside the NVTX range 'solve' and exit "
+                         "(for ncu --nvtx-include solve/)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        r = run_oracle(args.warmup + args.steps)
+        ts = r["times"][args.warmup:]
+        t = sum(ts) / len(ts)
+        v = r["n"] / t / 1e9
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config(),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc(r)},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import numpy as np
+    import torch
+
+    import paper_2210_03179_gb300 as cm
+    import workloads as W
+    from paper_2210_03179_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    verts = W.sem_box_vertices(NE, NE, NE)
+    b_np = W.sem_rhs(NE, NE, NE, NORDER)
+    n = b_np.size
+    common = dict(verts=verts, orders=ORDERS, kind=KIND, order=K_ORDER, sided=SIDED)
+    s32 = cm.Solver("sem", prec="mixed", **common)
+    lmax = [s32.lambda_max(j) for j in range(len(ORDERS) - 1)]
+    s64 = cm.Solver("sem", prec="fp64", lmax=lmax, **common)
+    stream = torch.cuda.current_stream()
+    b = torch.tensor(b_np, device="cuda")
+    u = torch.zeros_like(b)
+
+    def solve(s):
+        code, it, rel, _ = cm.chebmg_pcg_solve(s.ctx, b, u, RTOL, 500)
+        assert code == cm.CHEBMG_OK and rel <= RTOL, (code, it, rel)
+        return it
+
+    if args.profile_solve:
+        s = s32 if args.profile_solve == "mixed" else s64
+        solve(s)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("solve")
+        it = solve(s)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_solve": args.profile_solve, "iterations": it}))
+        s32.close()
+        s64.close()
+        return 0
+
+    def timed(fn, reps):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = None
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps), out
+
+    for _ in range(args.warmup):
+        it32 = solve(s32)
+    it64 = solve(s64)
+
+    # ---- headline: mixed-precision solves, inputs resident in HBM ----
+    clocks = Clocks(local)
+    l0 = cm.chebmg_launch_count()
+    t32, it32 = timed(lambda: solve(s32), args.steps)
+    launches = (cm.chebmg_launch_count() - l0) // args.steps
+    clk = clocks.stop()
+    t64, it64 = timed(lambda: solve(s64), max(1, min(args.steps, 3)))
+
+    # ---- end to end through the host-buffer entry point (pinned host memory) ----
+    bh = torch.tensor(b_np).pin_memory()
+    uh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    bh_np, uh_np = bh.numpy(), uh.numpy()
+
+    def solve_host():
+        code, it, rel = cm.chebmg_pcg_solve_host(s32.ctx, bh_np, uh_np, RTOL, 500)
+        assert code == cm.CHEBMG_OK
+        return it
+
+    solve_host()
+    te2e, _ = timed(solve_host, args.steps)
+
+    # ---- fine-level smoother step (Ax + gather-scatter + recurrence) ----
+    def smoother_step_time(s, dt, f32):
+        xb = torch.zeros(n, device="cuda", dtype=torch.float32 if f32 else torch.float64)
+        bb = xb.clone().uniform_(-1, 1)
+        hi, lo = 9, 1
+        cm.chebmg_smooth(s.ctx, 0, dt, bb, xb, hi, True)
+        t_hi, _ = timed(lambda: cm.chebmg_smooth(s.ctx, 0, dt, bb, xb, hi, True), 10)
+        t_lo, _ = timed(lambda: cm.chebmg_smooth(s.ctx, 0, dt, bb, xb, lo, True), 10)
+        return (t_hi - t_lo) / (hi - lo)
+
+    step32 = smoother_step_time(s32, cm.CHEBMG_F32, True)
+    step64 = smoother_step_time(s64, cm.CHEBMG_F64, False)
+    E = NE ** 3
+    L = E * (NORDER + 1) ** 3
+    alg_bytes32 = 4 * (6 * L + 7 * n)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    achieved = alg_bytes32 / step32 / 1e9
+    roofline = {"bound": "hbm", "kernel": "fine FP32 Chebyshev step: k_sem_ax<float,8> + k_cheb4_step<float>",
+                "achieved": achieved, "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                "frac": achieved / (hbm if hbm else 6800.0),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
+                "traffic": None, "alg_bytes_per_step": alg_bytes32, "step_us": step32 * 1e6}
+    flops64 = 111 * L + 8 * n
+    fp64_alu = {"bound": "alu", "kernel": "fine FP64 Chebyshev step", "achieved": flops64 / step64 / 1e12,
+                "peak": 1.25, "unit": "TFLOP/s", "frac": flops64 / step64 / 1e12 / 1.25,
+                "peak_source": "nominal FP64 rate of GB300", "step_us": step64 * 1e6}
+
+    world_n = world
+    value = world_n * n / t32 / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_n, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t32 * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": config({"parallelism": f"replicas x{world_n}"}),
+            "time_to_1e8_s": {"mixed": t32, "fp64": t64},
+            "iterations": {"mixed": it32, "fp64": it64},
+            "speedup_mixed_vs_fp64": t64 / t32,
+            "smoother_gdofs": {"fp32": n / step32 / 1e9, "fp64": n / step64 / 1e9},
+            "e2e": {"value": world_n * n / te2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": int(launches),
+            "roofline": roofline, "roofline_fp64": fp64_alu,
+            "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        r = run_oracle(1)
+        t = r["times"][0]
+        line["cpu_baseline"] = {"value": r["n"] / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample_desc(r), "seconds": t}
+    s32.close()
+    s64.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * chebmg -- Jacobi-scaled Chebyshev smoothing in symmetric and one-sided
+ * multigrid V-cycles, as a preconditioner for a flexible CG solve of the
+ * Poisson problem A u = b (Phillips & Fischer, "Optimal Chebyshev Smoothers and
+ * One-sided V-cycles", arXiv 2210.03179).
+ *
+ * C ABI.  Every pointer argument documented "device" is a caller-owned CUDA
+ * device pointer; "host" pointers are caller-owned host memory.  The library
+ * owns only its context and the workspace it allocates in a setup call; it
+ * never frees or retains caller memory.  All work is issued on the stream in
+ * chebmg_opts.stream (NULL = the legacy default stream); calls that return a
+ * host scalar synchronise that stream.
+ *
+ * Errors: every int-returning call returns CHEBMG_OK (0) or a negative code;
+ * chebmg_strerror() names it and chebmg_last_error() gives a one-line
+ * description of the most recent failure in this thread.  No C++ exception
+ * and no abort crosses the ABI.  A context is not thread-safe: calls on one
+ * context must be serialised by the caller.
+ *
+ * Vector layout:
+ *   SEM level of order N on an nex x ney x nez box: the global GLL lattice
+ *     (NX, NY, NZ) = (nex N + 1, ney N + 1, nez N + 1), n = NX NY NZ, global id
+ *     (gz NY + gy) NX + gx.  Nodes on the cube boundary are Dirichlet nodes: they
+ *     are ignored on input and written 0 on output.
+ *   FD level: the mx x my interior grid, x fastest (index j mx + i).
+ * Precision: "dtype" arguments select FP64 (CHEBMG_F64, double*) or FP32
+ * (CHEBMG_F32, float*) vectors.  FP32 level data exists only in a context set
+ * up with prec = CHEBMG_FP32_SMOOTHER; vcycle/pcg_solve/coarse_solve vectors are
+ * always FP64.
+ */
+#ifndef CHEBMG_H
+#define CHEBMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CHEBMG_OK 0
+#define CHEBMG_EINVAL -1      /* bad argument (size, level, kind, dtype, pointer) */
+#define CHEBMG_ECUDA -2       /* a CUDA runtime call failed */
+#define CHEBMG_ENOTCONV -3    /* tolerance not reached within maxit; outputs valid */
+#define CHEBMG_EBREAKDOWN -4  /* p^T A p <= 0, NaN/Inf residual, or Lanczos breakdown */
+#define CHEBMG_ETIMEOUT -5    /* a bounded device wait gave up; context still usable */
+#define CHEBMG_ENOMEM -6      /* device allocation failed */
+#define CHEBMG_EMESH -7       /* mesh with a non-positive Jacobian */
+
+/* ---- options ------------------------------------------------------------- */
+typedef struct chebmg_ctx chebmg_ctx;
+
+/* Smoother kinds (Sec. 2): Algorithm 1 with lambda_min = lmin_ratio lambda_max
+ * ("1st-Cheb"), Algorithm 2 with beta_i = 1 (4th kind), Algorithm 2 with the
+ * optimized beta_i of Table 5 (Sec. 8.1). */
+enum { CHEBMG_CHEB_1ST = 1, CHEBMG_CHEB_4TH = 4, CHEBMG_CHEB_4TH_OPT = 5 };
+/* V-cycle shape (Sec. 2, Eqs. 2.2 and 2.4): symmetric (k,k) or one-sided (2k,0). */
+enum { CHEBMG_SYMMETRIC = 0, CHEBMG_ONE_SIDED = 1 };
+/* Precision policy: all FP64, or FP32 smoother/Ax/transfers inside an FP64
+ * outer solve (FP64 dots, Lanczos and coarse solve). */
+enum { CHEBMG_FP64 = 0, CHEBMG_FP32_SMOOTHER = 1 };
+enum { CHEBMG_F64 = 0, CHEBMG_F32 = 1 };
+
+typedef struct {
+  int kind;              /* CHEBMG_CHEB_1ST | CHEBMG_CHEB_4TH | CHEBMG_CHEB_4TH_OPT */
+  int order;             /* k >= 1: (k,k) symmetric or (2k,0) one-sided */
+  int sided;             /* CHEBMG_SYMMETRIC | CHEBMG_ONE_SIDED */
+  int prec;              /* CHEBMG_FP64 | CHEBMG_FP32_SMOOTHER */
+  double lmin_ratio;     /* 1st kind: lambda_min / lambda_max (0.1) */
+  double lmax_scale;     /* multiplies the Lanczos estimate (1.0) */
+  int lanczos_steps;     /* Lanczos steps per level (30) */
+  const double* lmax_override; /* host, one per smoothed level, or NULL */
+  double coarse_rtol;    /* SEM p=1 coarse CG relative tolerance (1e-10) */
+  int coarse_maxit;      /* SEM coarse CG iteration cap (5000) */
+  void* stream;          /* cudaStream_t, NULL = default stream */
+} chebmg_opts;
+
+/* Fill opts with the defaults listed above (kind 4th-opt, order 2, one-sided, FP64). */
+void chebmg_default_opts(chebmg_opts* opts);
+
+/* ---- setup ------------------------------------------------------------------ */
+
+/* 2-D five-point Poisson problem of Sec. 3 on [0,Lx] x [0,Ly] with an m x m
+ * interior grid (h = L/(m+1)); geometric coarsening by `coarsening` (2, or 8
+ * for the aggressive n/8 hierarchy) while the grid is larger than `coarsest`;
+ * Galerkin coarse operators A_{j+1} = P^T A_j P (Eq. 2.1) with bilinear P, and a
+ * dense Cholesky solve on the coarsest grid.  Requires (m+1) divisible by the
+ * coarsening factor at every level.  Returns EINVAL on bad sizes. */
+int chebmg_setup_fd2d(int m, double Lx, double Ly, int coarsening, int coarsest,
+                      const chebmg_opts* opts, chebmg_ctx** ctx);
+
+/* 3-D spectral-element Poisson problem (Sec. 1, Eq. 1.3) with p-multigrid
+ * (Sec. 4.1) on an nex x ney x nez box of trilinear hexahedra.
+ * verts: host, (nez+1)(ney+1)(nex+1) x 3 doubles, [vz][vy][vx][xyz], copied.
+ * orders: host, nlevels polynomial orders, strictly decreasing, each in 1..9
+ *   (e.g. {7, 3, 1}); the last level is solved by FP64 Jacobi-PCG to coarse_rtol.
+ * Returns EMESH if any quadrature point has a non-positive Jacobian. */
+int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* orders,
+                     int nlevels, const chebmg_opts* opts, chebmg_ctx** ctx);
+
+void chebmg_destroy(chebmg_ctx* ctx);
+
+/* ---- queries ---------------------------------------------------------------- */
+int chebmg_num_levels(const chebmg_ctx* ctx, int* nlevels);
+/* Number of entries n of level-`level` vectors. */
+int chebmg_level_size(const chebmg_ctx* ctx, int level, int64_t* n);
+/* lambda_max of S A used by the smoother on `level` (after lmax_scale/override). */
+int chebmg_lambda_max(const chebmg_ctx* ctx, int level, double* out);
+/* Kernel launches issued by this context since setup (for accounting). */
+int chebmg_launch_count(const chebmg_ctx* ctx, int64_t* count);
+
+/* ---- per-level operators (device vectors, dtype as above) ---------------- */
+
+/* y = A x on `level`: SEM matrix-free element Ax with direct-stiffness
+ * summation and Dirichlet mask (Eq. 1.3); FD five-point / Galerkin stencil. */
+int chebmg_apply_A(chebmg_ctx* ctx, int level, int dtype, const void* x, void* y);
+
+/* out = S = diag(A)^{-1} (Jacobi, Sec. 2), 0 on Dirichlet nodes. */
+int chebmg_inv_diagonal(chebmg_ctx* ctx, int level, int dtype, void* out);
+
+/* One smoother application of the context's kind and the given order on
+ * `level` for A x = b: Algorithm 1 or 2 with x updated in place.  x_is_zero
+ * skips the initial residual (x is then overwritten with the result). */
+int chebmg_smooth(chebmg_ctx* ctx, int level, int dtype, const void* b, void* x, int order,
+                  int x_is_zero);
+
+/* rc = P^T rf from `level` to level+1 (SEM p-MG or FD bilinear restriction). */
+int chebmg_restrict(chebmg_ctx* ctx, int level, int dtype, const void* rf, void* rc);
+
+/* zf = P zc (accumulate = 0) or zf += P zc (accumulate = 1), level+1 -> level. */
+int chebmg_prolong(chebmg_ctx* ctx, int level, int dtype, const void* zc, void* zf,
+                   int accumulate);
+
+/* z = A_l^{-1} r on the coarsest level: FD dense Cholesky; SEM Jacobi-PCG to
+ * coarse_rtol (iters may be NULL).  FP64 device vectors. */
+int chebmg_coarse_solve(chebmg_ctx* ctx, const double* r, double* z, int* iters);
+
+/* ---- solver --------------------------------------------------------------- */
+
+/* z = B r: one V-cycle (Eq. 2.2) from the finest level, FP64 device vectors. */
+int chebmg_vcycle(chebmg_ctx* ctx, const double* r, double* z);
+
+/* Flexible CG (x0 = 0) preconditioned by one V-cycle per iteration until
+ * ||b - A u|| / ||b|| <= rtol (relative residual of Sec. 5.1).  b, u: FP64
+ * device vectors.  iters, relres: host outputs (may be NULL).  history: host,
+ * maxit+1 doubles of relative residuals, or NULL.  Returns ENOTCONV (u and
+ * relres valid) if maxit is reached, EBREAKDOWN on p^T A p <= 0 or NaN. */
+int chebmg_pcg_solve(chebmg_ctx* ctx, const double* b, double* u, double rtol, int maxit,
+                     int* iters, double* relres, double* history);
+
+/* Same as chebmg_pcg_solve with HOST b and u: copies b in and u out on the
+ * context stream (end-to-end entry point). */
+int chebmg_pcg_solve_host(chebmg_ctx* ctx, const double* b_host, double* u_host, double rtol,
+                          int maxit, int* iters, double* relres);
+
+/* ---- errors ------------------------------------------------------------------ */
+const char* chebmg_strerror(int code);
+const char* chebmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEBMG_H */

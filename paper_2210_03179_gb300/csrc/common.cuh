@@ -1,0 +1,111 @@
+// Internal declarations shared by the CUDA translation units of libchebmg.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "setup_host.h"
+
+namespace chebmg {
+
+// Number of kernel launches issued by this library in this process.
+extern std::atomic<int64_t> g_launches;
+
+// Scalar slots of the device-side reduction buffer (FP64).
+enum Slot {
+  S_RZ = 0,      // (r, z) of the current Krylov iteration
+  S_PQ,          // (p, A p)
+  S_RR,          // (r, r)
+  S_ZR,          // (z_new, r_new)
+  S_ZRO,         // (z_new, r_old)
+  S_BB,          // (b, b)
+  S_ALPHA,
+  S_BETA,
+  S_T0,          // scratch
+  S_T1,
+  S_NSLOTS
+};
+enum PostOp { POST_NONE = 0, POST_ALPHA, POST_BETA_FLEX, POST_BETA_CG, POST_SET_RZ_FROM_ZR };
+
+constexpr int kRedBlocks = 592;    // 152 SMs x 4: partial sums per reduction pass
+
+template <typename T>
+struct Stencil9 {
+  T c[9];
+};
+
+// ---- SEM kernels (y must be zeroed by the caller; results accumulate) ----
+template <typename T>
+void sem_ax(int Q, int64_t E, const uint32_t* gid, const T* G, const T* D, const T* u, T* y,
+            cudaStream_t s);
+template <typename T>
+void sem_restrict(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc,
+                  const T* J, const T* rf, T* rc, cudaStream_t s);
+template <typename T>
+void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc,
+                 const T* J, const T* zc, T* zf, int accumulate, cudaStream_t s);
+
+// ---- FD kernels ----
+template <typename T>
+void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s);
+template <typename T>
+void fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* rf, T* rc, cudaStream_t s);
+template <typename T>
+void fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* zc, T* zf, int accumulate,
+                cudaStream_t s);
+void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s);
+
+// ---- Chebyshev recurrences (Algorithms 1 and 2), elementwise over n ----
+// 4th kind init: x_is_zero: x = 0, r = b; else r = b - y, y = 0.  d = c0 S r.
+template <typename T>
+void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0,
+                int x_is_zero, cudaStream_t s);
+// 4th kind step: x += beta d; r -= y; d = c1 d + c2 S r; y = 0.
+template <typename T>
+void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1,
+                double c2, cudaStream_t s);
+// 1st kind init: r = S (b - y) (or S b), d = r / theta, y = 0 (x = 0 if x_is_zero).
+template <typename T>
+void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
+                int x_is_zero, cudaStream_t s);
+// 1st kind step: x += d; r -= S y; d = c1 d + c2 r; y = 0.
+template <typename T>
+void cheb1_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double c1, double c2,
+                cudaStream_t s);
+// x += a * d
+template <typename T>
+void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s);
+// r = b - y; y = 0
+template <typename T>
+void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s);
+template <typename Tin, typename Tout>
+void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s);
+// out = mask(invD) ? in : 0   (mask: invD != 0)
+void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s);
+
+// ---- FP64 reductions into scal[slot] (deterministic two-pass) ----
+// out slots: scal[slot0] = (a0, b0), scal[slot1] = (a1, b1) if a1 != nullptr; then post-op.
+void dot2(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1,
+          int slot0, int slot1, int post, double* partial, double* scal, cudaStream_t s);
+
+// ---- Krylov vector updates with device scalars ----
+// FCG: alpha = scal[ALPHA]; rold = r; x += alpha p; r -= alpha q; partial (r, r) -> scal[RR]
+void fcg_update_xr(int64_t n, double* x, double* r, double* rold, const double* p,
+                   const double* q, double* partial, double* scal, cudaStream_t s);
+// p = z + scal[BETA] p
+void update_p(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s);
+// CG (coarse): x += alpha p; r -= alpha q; z = S r; partials (r, r) and (r, z)
+void cg_update(int64_t n, double* x, double* r, double* z, const double* p, const double* q,
+               const double* invD, double* partial, double* scal, cudaStream_t s);
+
+// ---- Lanczos helpers ----
+void splitmix_fill(int64_t n, uint64_t seed, const double* invD, double* v, cudaStream_t s);
+// t = sqrt(invD) * v
+void sqrt_scale(int64_t n, const double* invD, const double* v, double* t, cudaStream_t s);
+// w = sqrt(invD) * y - alpha v - beta vprev  (alpha, beta from host)
+void lanczos_w(int64_t n, const double* invD, const double* y, const double* v,
+               const double* vprev, double alpha, double beta, double* w, cudaStream_t s);
+void scale(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+
+}  // namespace chebmg

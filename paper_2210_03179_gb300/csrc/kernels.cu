@@ -1,0 +1,717 @@
+// CUDA kernels of the Jacobi-Chebyshev multigrid hot path (sm_103a).
+//
+// SEM operator (Sec. 1, Eq. 1.3): per element w_m = sum_n G_mn (Dhat_n u),
+// y_e = sum_m Dhat_m^T w_m, then direct-stiffness summation into the global
+// vector by atomics, skipping Dirichlet nodes.  p-multigrid transfers
+// (Sec. 4.1) apply J x J x J per element.  FD (Sec. 3): a constant 3x3
+// stencil per level (five-point on the finest, Galerkin nine-point below).
+// Chebyshev recurrences: Algorithms 1 and 2 split into an operator pass and
+// an elementwise pass.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace chebmg {
+
+std::atomic<int64_t> g_launches{0};
+
+namespace {
+
+inline unsigned grid_for(int64_t n, int bs) {
+  int64_t g = (n + bs - 1) / bs;
+  if (g > 4096 * 152) g = 4096 * 152;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+inline void count() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace
+
+// ===========================================================================
+// SEM element operator
+// ===========================================================================
+template <int Q>
+struct SemShape {
+  static constexpr int NP = Q * Q * Q;
+  static constexpr int EPB = NP >= 512 ? 1 : 512 / NP;   // elements per block
+  static constexpr int THREADS = EPB * NP;
+};
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(SemShape<Q>::THREADS)
+k_sem_ax(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G,
+         const T* __restrict__ Dg, const T* __restrict__ u, T* __restrict__ y) {
+  constexpr int NP = SemShape<Q>::NP;
+  constexpr int EPB = SemShape<Q>::EPB;
+  __shared__ T sD[Q * Q];
+  __shared__ T s_u[EPB * NP];
+  __shared__ T s_r[EPB * NP];
+  __shared__ T s_s[EPB * NP];
+  __shared__ T s_t[EPB * NP];
+  const int tid = threadIdx.x;
+  const int le = tid / NP;
+  const int p = tid - le * NP;
+  const int i = p % Q, j = (p / Q) % Q, k = p / (Q * Q);
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  if (tid < Q * Q) sD[tid] = Dg[tid];
+  const bool valid = e < E;
+  const uint32_t id = valid ? gid[e * NP + p] : kGidDirichlet;
+  T* su = s_u + le * NP;
+  su[p] = (id & kGidDirichlet) ? T(0) : u[id & kGidMask];
+  __syncthreads();
+  T ur = 0, us = 0, ut = 0;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    ur += sD[i * Q + l] * su[(k * Q + j) * Q + l];
+    us += sD[j * Q + l] * su[(k * Q + l) * Q + i];
+    ut += sD[k * Q + l] * su[(l * Q + j) * Q + i];
+  }
+  T wr = 0, ws = 0, wt = 0;
+  if (valid) {
+    const T* Ge = G + (size_t)e * 6 * NP + p;
+    const T g00 = Ge[0], g01 = Ge[NP], g02 = Ge[2 * NP];
+    const T g11 = Ge[3 * NP], g12 = Ge[4 * NP], g22 = Ge[5 * NP];
+    wr = g00 * ur + g01 * us + g02 * ut;
+    ws = g01 * ur + g11 * us + g12 * ut;
+    wt = g02 * ur + g12 * us + g22 * ut;
+  }
+  T* sr = s_r + le * NP;
+  T* ss = s_s + le * NP;
+  T* st = s_t + le * NP;
+  sr[p] = wr;
+  ss[p] = ws;
+  st[p] = wt;
+  __syncthreads();
+  T acc = 0;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    acc += sD[l * Q + i] * sr[(k * Q + j) * Q + l];
+    acc += sD[l * Q + j] * ss[(k * Q + l) * Q + i];
+    acc += sD[l * Q + k] * st[(l * Q + j) * Q + i];
+  }
+  if (valid && !(id & kGidDirichlet)) atomicAdd(&y[id & kGidMask], acc);
+}
+
+template <typename T, int Q>
+static void launch_sem_ax(int64_t E, const uint32_t* gid, const T* G, const T* D, const T* u, T* y,
+                          cudaStream_t s) {
+  using S = SemShape<Q>;
+  const unsigned blocks = (unsigned)((E + S::EPB - 1) / S::EPB);
+  k_sem_ax<T, Q><<<blocks, S::THREADS, 0, s>>>(E, gid, G, D, u, y);
+  count();
+}
+
+template <typename T>
+void sem_ax(int Q, int64_t E, const uint32_t* gid, const T* G, const T* D, const T* u, T* y,
+            cudaStream_t s) {
+  switch (Q) {
+    case 2: launch_sem_ax<T, 2>(E, gid, G, D, u, y, s); break;
+    case 3: launch_sem_ax<T, 3>(E, gid, G, D, u, y, s); break;
+    case 4: launch_sem_ax<T, 4>(E, gid, G, D, u, y, s); break;
+    case 5: launch_sem_ax<T, 5>(E, gid, G, D, u, y, s); break;
+    case 6: launch_sem_ax<T, 6>(E, gid, G, D, u, y, s); break;
+    case 7: launch_sem_ax<T, 7>(E, gid, G, D, u, y, s); break;
+    case 8: launch_sem_ax<T, 8>(E, gid, G, D, u, y, s); break;
+    case 9: launch_sem_ax<T, 9>(E, gid, G, D, u, y, s); break;
+    case 10: launch_sem_ax<T, 10>(E, gid, G, D, u, y, s); break;
+    default: break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// p-multigrid transfers.  One block per element, runtime orders (Q <= 10).
+// Restriction uses the owner copy of each fine node: P^T = Q_c^T J3^T O^T,
+// which equals Q_c^T J3^T Q_f W because J3 Q_c maps into continuous fields.
+// ---------------------------------------------------------------------------
+constexpr int kTransferThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kTransferThreads)
+k_sem_restrict(int Qf, int Qc, const uint32_t* __restrict__ gidf, const uint32_t* __restrict__ gidc,
+               const T* __restrict__ J, const T* __restrict__ rf, T* __restrict__ rc) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sJ = reinterpret_cast<T*>(smem_raw);      // [Qf][Qc]
+  T* a = sJ + Qf * Qc;                         // [kf][jf][if]
+  T* b = a + Qf * Qf * Qf;                     // [kf][jf][ic]
+  T* c = b + Qf * Qf * Qc;                     // [kf][jc][ic]
+  const int64_t e = blockIdx.x;
+  const int NPf = Qf * Qf * Qf, NPc = Qc * Qc * Qc;
+  for (int q = threadIdx.x; q < Qf * Qc; q += blockDim.x) sJ[q] = J[q];
+  for (int p = threadIdx.x; p < NPf; p += blockDim.x) {
+    const uint32_t id = gidf[e * NPf + p];
+    a[p] = ((id & kGidOwner) && !(id & kGidDirichlet)) ? rf[id & kGidMask] : T(0);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < Qf * Qf * Qc; q += blockDim.x) {
+    const int ic = q % Qc, jf = (q / Qc) % Qf, kf = q / (Qc * Qf);
+    T acc = 0;
+    for (int l = 0; l < Qf; ++l) acc += sJ[l * Qc + ic] * a[(kf * Qf + jf) * Qf + l];
+    b[q] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < Qf * Qc * Qc; q += blockDim.x) {
+    const int ic = q % Qc, jc = (q / Qc) % Qc, kf = q / (Qc * Qc);
+    T acc = 0;
+    for (int l = 0; l < Qf; ++l) acc += sJ[l * Qc + jc] * b[(kf * Qf + l) * Qc + ic];
+    c[q] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NPc; q += blockDim.x) {
+    const int ic = q % Qc, jc = (q / Qc) % Qc, kc = q / (Qc * Qc);
+    T acc = 0;
+    for (int l = 0; l < Qf; ++l) acc += sJ[l * Qc + kc] * c[(l * Qc + jc) * Qc + ic];
+    const uint32_t id = gidc[e * NPc + q];
+    if (!(id & kGidDirichlet)) atomicAdd(&rc[id & kGidMask], acc);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTransferThreads)
+k_sem_prolong(int Qf, int Qc, const uint32_t* __restrict__ gidf, const uint32_t* __restrict__ gidc,
+              const T* __restrict__ J, const T* __restrict__ zc, T* __restrict__ zf, int accumulate) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sJ = reinterpret_cast<T*>(smem_raw);      // [Qf][Qc]
+  T* a = sJ + Qf * Qc;                         // [kc][jc][ic]
+  T* b = a + Qc * Qc * Qc;                     // [kc][jc][if]
+  T* c = b + Qc * Qc * Qf;                     // [kc][jf][if]
+  const int64_t e = blockIdx.x;
+  const int NPf = Qf * Qf * Qf, NPc = Qc * Qc * Qc;
+  for (int q = threadIdx.x; q < Qf * Qc; q += blockDim.x) sJ[q] = J[q];
+  for (int p = threadIdx.x; p < NPc; p += blockDim.x) {
+    const uint32_t id = gidc[e * NPc + p];
+    a[p] = (id & kGidDirichlet) ? T(0) : zc[id & kGidMask];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < Qc * Qc * Qf; q += blockDim.x) {
+    const int iF = q % Qf, jc = (q / Qf) % Qc, kc = q / (Qf * Qc);
+    T acc = 0;
+    for (int l = 0; l < Qc; ++l) acc += sJ[iF * Qc + l] * a[(kc * Qc + jc) * Qc + l];
+    b[q] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < Qc * Qf * Qf; q += blockDim.x) {
+    const int iF = q % Qf, jF = (q / Qf) % Qf, kc = q / (Qf * Qf);
+    T acc = 0;
+    for (int l = 0; l < Qc; ++l) acc += sJ[jF * Qc + l] * b[(kc * Qc + l) * Qf + iF];
+    c[q] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NPf; q += blockDim.x) {
+    const int iF = q % Qf, jF = (q / Qf) % Qf, kF = q / (Qf * Qf);
+    const uint32_t id = gidf[e * NPf + q];
+    if (!(id & kGidOwner)) continue;
+    T* dst = &zf[id & kGidMask];
+    if (id & kGidDirichlet) {
+      if (!accumulate) *dst = T(0);
+      continue;
+    }
+    T acc = 0;
+    for (int l = 0; l < Qc; ++l) acc += sJ[kF * Qc + l] * c[(l * Qf + jF) * Qf + iF];
+    *dst = accumulate ? *dst + acc : acc;
+  }
+}
+
+template <typename T>
+static size_t transfer_smem(int Qf, int Qc) {
+  return sizeof(T) * (size_t)(Qf * Qc + Qf * Qf * Qf + Qf * Qf * Qc + Qf * Qc * Qc);
+}
+
+template <typename T>
+void sem_restrict(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc, const T* J,
+                  const T* rf, T* rc, cudaStream_t s) {
+  k_sem_restrict<T><<<(unsigned)E, kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(Qf, Qc, gidf, gidc,
+                                                                                   J, rf, rc);
+  count();
+}
+
+template <typename T>
+void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc, const T* J,
+                 const T* zc, T* zf, int accumulate, cudaStream_t s) {
+  k_sem_prolong<T><<<(unsigned)E, kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(
+      Qf, Qc, gidf, gidc, J, zc, zf, accumulate);
+  count();
+}
+
+// ===========================================================================
+// FD kernels
+// ===========================================================================
+template <typename T>
+__global__ void k_fd_apply(int mx, int my, Stencil9<T> st, const T* __restrict__ u, T* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= mx || j >= my) return;
+  T acc = 0;
+#pragma unroll
+  for (int a = -1; a <= 1; ++a) {
+    const int jj = j + a;
+    if (jj < 0 || jj >= my) continue;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+      const int ii = i + b;
+      if (ii < 0 || ii >= mx) continue;
+      acc += st.c[(a + 1) * 3 + (b + 1)] * u[(size_t)jj * mx + ii];
+    }
+  }
+  y[(size_t)j * mx + i] = acc;
+}
+
+template <typename T>
+void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s) {
+  dim3 bs(32, 8);
+  dim3 gs((mx + 31) / 32, (my + 7) / 8);
+  k_fd_apply<T><<<gs, bs, 0, s>>>(mx, my, st, u, y);
+  count();
+}
+
+// rc(I,J) = sum_{|a|,|b| < c} w_a w_b rf(c(I+1)-1+b, c(J+1)-1+a), w_d = (c - |d|)/c
+template <typename T>
+__global__ void k_fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* __restrict__ rf,
+                              T* __restrict__ rc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Jc = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= mcx || Jc >= mcy) return;
+  const int fi = c * (I + 1) - 1, fj = c * (Jc + 1) - 1;
+  const T inv_c = T(1) / T(c);
+  T acc = 0;
+  for (int a = -(c - 1); a <= c - 1; ++a) {
+    const int jj = fj + a;
+    if (jj < 0 || jj >= mfy) continue;
+    const T wa = T(c - (a < 0 ? -a : a)) * inv_c;
+    T row = 0;
+    for (int b = -(c - 1); b <= c - 1; ++b) {
+      const int ii = fi + b;
+      if (ii < 0 || ii >= mfx) continue;
+      row += T(c - (b < 0 ? -b : b)) * inv_c * rf[(size_t)jj * mfx + ii];
+    }
+    acc += wa * row;
+  }
+  rc[(size_t)Jc * mcx + I] = acc;
+}
+
+template <typename T>
+__global__ void k_fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* __restrict__ zc,
+                             T* __restrict__ zf, int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= mfx || j >= mfy) return;
+  const T inv_c = T(1) / T(c);
+  const int I0 = (i + 1) / c - 1, J0 = (j + 1) / c - 1;
+  const int di = i - (c * (I0 + 1) - 1), dj = j - (c * (J0 + 1) - 1);
+  T wi[2] = {T(c - di) * inv_c, T(di) * inv_c};
+  T wj[2] = {T(c - dj) * inv_c, T(dj) * inv_c};
+  T acc = 0;
+  for (int a = 0; a < 2; ++a) {
+    const int Jc = J0 + a;
+    if (Jc < 0 || Jc >= mcy || wj[a] == T(0)) continue;
+    for (int b = 0; b < 2; ++b) {
+      const int I = I0 + b;
+      if (I < 0 || I >= mcx || wi[b] == T(0)) continue;
+      acc += wj[a] * wi[b] * zc[(size_t)Jc * mcx + I];
+    }
+  }
+  T* dst = &zf[(size_t)j * mfx + i];
+  *dst = accumulate ? *dst + acc : acc;
+}
+
+template <typename T>
+void fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* rf, T* rc, cudaStream_t s) {
+  dim3 bs(16, 16);
+  dim3 gs((mcx + 15) / 16, (mcy + 15) / 16);
+  k_fd_restrict<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, rf, rc);
+  count();
+}
+
+template <typename T>
+void fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* zc, T* zf, int accumulate,
+                cudaStream_t s) {
+  dim3 bs(32, 8);
+  dim3 gs((mfx + 31) / 32, (mfy + 7) / 8);
+  k_fd_prolong<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, zc, zf, accumulate);
+  count();
+}
+
+__global__ void k_dense_matvec(int n, const double* __restrict__ M, const double* __restrict__ x,
+                               double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) acc += M[(size_t)i * n + j] * x[j];
+  y[i] = acc;
+}
+
+void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s) {
+  k_dense_matvec<<<(n + 127) / 128, 128, 0, s>>>(n, M, x, y);
+  count();
+}
+
+// ===========================================================================
+// Chebyshev recurrences and vector updates
+// ===========================================================================
+template <typename T>
+__global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                             T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD, T c0,
+                             int x_is_zero) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    T rv;
+    if (x_is_zero) {
+      rv = b[g];
+      x[g] = T(0);
+    } else {
+      rv = b[g] - y[g];
+      y[g] = T(0);
+    }
+    r[g] = rv;
+    d[g] = c0 * invD[g] * rv;
+  }
+}
+
+template <typename T>
+__global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
+                             T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const T dv = d[g];
+    const T rv = r[g] - y[g];
+    x[g] += beta * dv;
+    r[g] = rv;
+    d[g] = c1 * dv + c2 * invD[g] * rv;
+    y[g] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_cheb1_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                             T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD,
+                             T inv_theta, int x_is_zero) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    T rv;
+    if (x_is_zero) {
+      rv = invD[g] * b[g];
+      x[g] = T(0);
+    } else {
+      rv = invD[g] * (b[g] - y[g]);
+      y[g] = T(0);
+    }
+    r[g] = rv;
+    d[g] = rv * inv_theta;
+  }
+}
+
+template <typename T>
+__global__ void k_cheb1_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
+                             T* __restrict__ y, const T* __restrict__ invD, T c1, T c2) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const T dv = d[g];
+    const T rv = r[g] - invD[g] * y[g];
+    x[g] += dv;
+    r[g] = rv;
+    d[g] = c1 * dv + c2 * rv;
+    y[g] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_axpy(int64_t n, T a, const T* __restrict__ d, T* __restrict__ x) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    x[g] += a * d[g];
+}
+
+template <typename T>
+__global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y, T* __restrict__ r) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    r[g] = b[g] - y[g];
+    y[g] = T(0);
+  }
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = (Tout)in[g];
+}
+
+__global__ void k_masked_copy(int64_t n, const double* __restrict__ in, const double* __restrict__ invD,
+                              double* __restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = invD[g] != 0.0 ? in[g] : 0.0;
+}
+
+constexpr int kVecThreads = 256;
+
+template <typename T>
+void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0, int x_is_zero,
+                cudaStream_t s) {
+  k_cheb4_init<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)c0, x_is_zero);
+  count();
+}
+template <typename T>
+void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
+                cudaStream_t s) {
+  k_cheb4_step<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2);
+  count();
+}
+template <typename T>
+void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
+                int x_is_zero, cudaStream_t s) {
+  k_cheb1_init<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)inv_theta,
+                                                                    x_is_zero);
+  count();
+}
+template <typename T>
+void cheb1_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double c1, double c2, cudaStream_t s) {
+  k_cheb1_step<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)c1, (T)c2);
+  count();
+}
+template <typename T>
+void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s) {
+  k_axpy<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, (T)a, d, x);
+  count();
+}
+template <typename T>
+void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s) {
+  k_residual<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, b, y, r);
+  count();
+}
+template <typename Tin, typename Tout>
+void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s) {
+  k_cast<Tin, Tout><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, in, out);
+  count();
+}
+void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s) {
+  k_masked_copy<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, in, invD, out);
+  count();
+}
+
+// ===========================================================================
+// Deterministic FP64 reductions: fixed kRedBlocks partials, fixed-order finish
+// ===========================================================================
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of two values; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[kRedThreads / 32], sb[kRedThreads / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = l < kRedThreads / 32 ? sa[l] : 0.0;
+    b = l < kRedThreads / 32 ? sb[l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_dot2_partial(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
+               const double* __restrict__ a1, const double* __restrict__ b1, double* __restrict__ partial) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    s0 += a0[g] * b0[g];
+    if (a1) s1 += a1[g] * b1[g];
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s0;
+    partial[kRedBlocks + blockIdx.x] = s1;
+  }
+}
+
+__device__ void apply_post(int post, double* scal) {
+  switch (post) {
+    case POST_ALPHA: scal[S_ALPHA] = scal[S_RZ] / scal[S_PQ]; break;
+    case POST_BETA_FLEX:   // Polak-Ribiere: beta = (z_new, r_new - r_old) / (z_old, r_old)
+      scal[S_BETA] = (scal[S_ZR] - scal[S_ZRO]) / scal[S_RZ];
+      scal[S_RZ] = scal[S_ZR];
+      break;
+    case POST_BETA_CG:     // Fletcher-Reeves for the coarse CG: beta = rz_new / rz_old
+      scal[S_BETA] = scal[S_ZR] / scal[S_RZ];
+      scal[S_RZ] = scal[S_ZR];
+      break;
+    case POST_SET_RZ_FROM_ZR: scal[S_RZ] = scal[S_ZR]; break;
+    default: break;
+  }
+}
+
+// One block: sums the partials of two slots in a fixed order, then the post-op.
+__global__ void __launch_bounds__(kRedThreads)
+k_dot2_finish(const double* __restrict__ partial, int slot0, int slot1, int post, double* __restrict__ scal) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int q = threadIdx.x; q < kRedBlocks; q += blockDim.x) {
+    s0 += partial[q];
+    s1 += partial[kRedBlocks + q];
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    if (slot0 >= 0) scal[slot0] = s0;
+    if (slot1 >= 0) scal[slot1] = s1;
+    apply_post(post, scal);
+  }
+}
+
+void dot2(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, int slot0,
+          int slot1, int post, double* partial, double* scal, cudaStream_t s) {
+  k_dot2_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a0, b0, a1, b1, partial);
+  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, slot0, a1 ? slot1 : -1, post, scal);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_fcg_update_xr(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ rold,
+                const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ partial,
+                const double* __restrict__ scal) {
+  const double alpha = scal[S_ALPHA];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double rv = r[g];
+    rold[g] = rv;
+    x[g] += alpha * p[g];
+    const double rn = rv - alpha * q[g];
+    r[g] = rn;
+    s0 += rn * rn;
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s0;
+    partial[kRedBlocks + blockIdx.x] = 0.0;
+  }
+}
+
+void fcg_update_xr(int64_t n, double* x, double* r, double* rold, const double* p, const double* q,
+                   double* partial, double* scal, cudaStream_t s) {
+  k_fcg_update_xr<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, rold, p, q, partial, scal);
+  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, -1, POST_NONE, scal);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+__global__ void k_update_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
+                           const double* __restrict__ scal) {
+  const double beta = scal[S_BETA];
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    p[g] = z[g] + beta * p[g];
+}
+
+void update_p(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s) {
+  k_update_p<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, z, p, scal);
+  count();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
+            const double* __restrict__ p, const double* __restrict__ q, const double* __restrict__ invD,
+            double* __restrict__ partial, const double* __restrict__ scal) {
+  const double alpha = scal[S_ALPHA];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    x[g] += alpha * p[g];
+    const double rn = r[g] - alpha * q[g];
+    r[g] = rn;
+    const double zn = invD[g] * rn;
+    z[g] = zn;
+    s0 += rn * rn;
+    s1 += rn * zn;
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s0;
+    partial[kRedBlocks + blockIdx.x] = s1;
+  }
+}
+
+void cg_update(int64_t n, double* x, double* r, double* z, const double* p, const double* q,
+               const double* invD, double* partial, double* scal, cudaStream_t s) {
+  k_cg_update<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, z, p, q, invD, partial, scal);
+  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, S_ZR, POST_BETA_CG, scal);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+// ===========================================================================
+// Lanczos helpers
+// ===========================================================================
+__global__ void k_splitmix_fill(int64_t n, uint64_t seed, const double* __restrict__ invD, double* __restrict__ v) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    // SplitMix64 (Steele, Lea & Flood 2014), output g of the stream seeded with `seed`
+    uint64_t z = seed + (uint64_t)(g + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    v[g] = invD[g] > 0.0 ? 2.0 * u - 1.0 : 0.0;
+  }
+}
+
+void splitmix_fill(int64_t n, uint64_t seed, const double* invD, double* v, cudaStream_t s) {
+  k_splitmix_fill<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, seed, invD, v);
+  count();
+}
+
+__global__ void k_sqrt_scale(int64_t n, const double* __restrict__ invD, const double* __restrict__ v,
+                             double* __restrict__ t) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    t[g] = sqrt(invD[g]) * v[g];
+}
+
+void sqrt_scale(int64_t n, const double* invD, const double* v, double* t, cudaStream_t s) {
+  k_sqrt_scale<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, invD, v, t);
+  count();
+}
+
+__global__ void k_lanczos_w(int64_t n, const double* __restrict__ invD, const double* __restrict__ y,
+                            const double* __restrict__ v, const double* __restrict__ vprev, double alpha,
+                            double beta, double* __restrict__ w) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    w[g] = sqrt(invD[g]) * y[g] - alpha * v[g] - beta * vprev[g];
+}
+
+void lanczos_w(int64_t n, const double* invD, const double* y, const double* v, const double* vprev,
+               double alpha, double beta, double* w, cudaStream_t s) {
+  k_lanczos_w<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, invD, y, v, vprev, alpha, beta, w);
+  count();
+}
+
+__global__ void k_scale(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    y[g] = a * x[g];
+}
+
+void scale(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
+  k_scale<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, a, x, y);
+  count();
+}
+
+// ===========================================================================
+// explicit instantiations
+// ===========================================================================
+#define CHEBMG_INST(T)                                                                                \
+  template void sem_ax<T>(int, int64_t, const uint32_t*, const T*, const T*, const T*, T*, cudaStream_t); \
+  template void sem_restrict<T>(int, int, int64_t, const uint32_t*, const uint32_t*, const T*, const T*,  \
+                                T*, cudaStream_t);                                                     \
+  template void sem_prolong<T>(int, int, int64_t, const uint32_t*, const uint32_t*, const T*, const T*,   \
+                               T*, int, cudaStream_t);                                                 \
+  template void fd_apply<T>(int, int, const Stencil9<T>&, const T*, T*, cudaStream_t);                  \
+  template void fd_restrict<T>(int, int, int, int, int, const T*, T*, cudaStream_t);                    \
+  template void fd_prolong<T>(int, int, int, int, int, const T*, T*, int, cudaStream_t);                \
+  template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t);  \
+  template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t); \
+  template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t);  \
+  template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t);         \
+  template void axpy<T>(int64_t, double, const T*, T*, cudaStream_t);                                   \
+  template void residual<T>(int64_t, const T*, T*, T*, cudaStream_t);
+
+CHEBMG_INST(float)
+CHEBMG_INST(double)
+template void cast<double, float>(int64_t, const double*, float*, cudaStream_t);
+template void cast<float, double>(int64_t, const float*, double*, cudaStream_t);
+template void cast<double, double>(int64_t, const double*, double*, cudaStream_t);
+
+}  // namespace chebmg

@@ -1,0 +1,285 @@
+// Host-side construction of the SEM and FD discretisations.  See setup_host.h.
+#include "setup_host.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace chebmg {
+
+namespace {
+
+// Legendre P_{N-1}(x) and P_N(x) by Bonnet's recurrence.
+void legendre_pair(int N, double x, double& pm1, double& p) {
+  double a = 1.0, b = x;   // P_0, P_1
+  if (N == 0) { pm1 = 0.0; p = 1.0; return; }
+  for (int k = 2; k <= N; ++k) {
+    double c = ((2.0 * k - 1.0) * x * b - (k - 1.0) * a) / k;
+    a = b;
+    b = c;
+  }
+  pm1 = a;
+  p = b;
+}
+
+}  // namespace
+
+void gll_rule(int N, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(N + 1, 0.0);
+  w.assign(N + 1, 0.0);
+  // Interior GLL points are the roots of q(x) = (1 - x^2) P_N'(x).  With
+  // (1 - x^2) P_N' = N (P_{N-1} - x P_N) and, from Legendre's equation,
+  // q'(x) = -N (N+1) P_N(x), Newton's step is x += (P_{N-1} - x P_N) / ((N+1) P_N).
+  for (int j = 0; j <= N; ++j) {
+    double xj = -std::cos(M_PI * j / N);
+    if (j > 0 && j < N) {
+      for (int it = 0; it < 100; ++it) {
+        double pm1, p;
+        legendre_pair(N, xj, pm1, p);
+        double dx = (pm1 - xj * p) / ((N + 1.0) * p);
+        xj += dx;
+        if (std::fabs(dx) < 1e-16) break;
+      }
+    }
+    x[j] = xj;
+  }
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int j = 0; j <= N; ++j) {
+    double pm1, p;
+    legendre_pair(N, x[j], pm1, p);
+    w[j] = 2.0 / (N * (N + 1.0) * p * p);
+  }
+}
+
+void gll_derivative(int N, const std::vector<double>& x, std::vector<double>& Dm) {
+  // Closed form for GLL nodes: l_j'(x_i) = P_N(x_i) / (P_N(x_j) (x_i - x_j)), i != j;
+  // the diagonal vanishes except at the end points, -+ N(N+1)/4.
+  const int Q = N + 1;
+  Dm.assign(Q * Q, 0.0);
+  std::vector<double> PN(Q);
+  for (int i = 0; i < Q; ++i) {
+    double pm1;
+    legendre_pair(N, x[i], pm1, PN[i]);
+  }
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < Q; ++j)
+      if (i != j) Dm[i * Q + j] = PN[i] / (PN[j] * (x[i] - x[j]));
+  Dm[0] = -N * (N + 1.0) / 4.0;
+  Dm[Q * Q - 1] = N * (N + 1.0) / 4.0;
+}
+
+void lagrange_interp(const std::vector<double>& xc, const std::vector<double>& y,
+                     std::vector<double>& J) {
+  // Barycentric form of the Lagrange basis.
+  const int nc = (int)xc.size(), ny = (int)y.size();
+  std::vector<double> lam(nc, 1.0);
+  for (int b = 0; b < nc; ++b)
+    for (int m = 0; m < nc; ++m)
+      if (m != b) lam[b] *= 1.0 / (xc[b] - xc[m]);
+  J.assign((size_t)ny * nc, 0.0);
+  for (int a = 0; a < ny; ++a) {
+    int hit = -1;
+    for (int b = 0; b < nc; ++b)
+      if (y[a] == xc[b]) hit = b;
+    if (hit >= 0) {
+      J[(size_t)a * nc + hit] = 1.0;
+      continue;
+    }
+    double den = 0.0;
+    for (int b = 0; b < nc; ++b) den += lam[b] / (y[a] - xc[b]);
+    for (int b = 0; b < nc; ++b) J[(size_t)a * nc + b] = (lam[b] / (y[a] - xc[b])) / den;
+  }
+}
+
+bool build_sem_level(int nex, int ney, int nez, const double* verts, int N, SemHostLevel& L) {
+  L.N = N;
+  L.NQ = N + 1;
+  L.NP = L.NQ * L.NQ * L.NQ;
+  L.nex = nex;
+  L.ney = ney;
+  L.nez = nez;
+  L.E = (int64_t)nex * ney * nez;
+  const int64_t NX = (int64_t)nex * N + 1, NY = (int64_t)ney * N + 1, NZ = (int64_t)nez * N + 1;
+  L.n = NX * NY * NZ;
+  gll_rule(N, L.x, L.w);
+  gll_derivative(N, L.x, L.Dm);
+  const int Q = L.NQ, NP = L.NP;
+  L.gid.assign((size_t)L.E * NP, 0u);
+  L.G.assign((size_t)L.E * 6 * NP, 0.0);
+  L.dirichlet.assign((size_t)L.n, 0);
+  L.diag.assign((size_t)L.n, 0.0);
+
+  for (int64_t gz = 0; gz < NZ; ++gz)
+    for (int64_t gy = 0; gy < NY; ++gy)
+      for (int64_t gx = 0; gx < NX; ++gx) {
+        bool b = gx == 0 || gx == NX - 1 || gy == 0 || gy == NY - 1 || gz == 0 || gz == NZ - 1;
+        L.dirichlet[(gz * NY + gy) * NX + gx] = b ? 1 : 0;
+      }
+
+  double minJ = 1e300;
+  bool ok = true;
+  std::vector<double> diag_local((size_t)L.E * NP, 0.0);
+
+#pragma omp parallel for schedule(static) reduction(min : minJ)
+  for (int64_t e = 0; e < L.E; ++e) {
+    const int ex = (int)(e % nex), ey = (int)((e / nex) % ney), ez = (int)(e / ((int64_t)nex * ney));
+    double V[2][2][2][3];
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          const double* v = verts + 3 * (((int64_t)(ez + c) * (ney + 1) + (ey + b)) * (nex + 1) + (ex + a));
+          for (int l = 0; l < 3; ++l) V[c][b][a][l] = v[l];
+        }
+    uint32_t* gid = &L.gid[(size_t)e * NP];
+    double* G = &L.G[(size_t)e * 6 * NP];
+    for (int k = 0; k < Q; ++k)
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          const int p = (k * Q + j) * Q + i;
+          // exact derivatives of the trilinear map at (r, s, t) = (x_i, x_j, x_k)
+          const double r = L.x[i], s = L.x[j], t = L.x[k];
+          const double fr[2] = {0.5 * (1 - r), 0.5 * (1 + r)}, dr[2] = {-0.5, 0.5};
+          const double fs[2] = {0.5 * (1 - s), 0.5 * (1 + s)}, ds[2] = {-0.5, 0.5};
+          const double ft[2] = {0.5 * (1 - t), 0.5 * (1 + t)}, dt[2] = {-0.5, 0.5};
+          double Jm[3][3] = {{0}};   // Jm[l][m] = d x_l / d r_m
+          for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+              for (int a = 0; a < 2; ++a)
+                for (int l = 0; l < 3; ++l) {
+                  Jm[l][0] += dr[a] * fs[b] * ft[c] * V[c][b][a][l];
+                  Jm[l][1] += fr[a] * ds[b] * ft[c] * V[c][b][a][l];
+                  Jm[l][2] += fr[a] * fs[b] * dt[c] * V[c][b][a][l];
+                }
+          // adjugate: adj[m][l] = cofactor C[l][m]; J^{-1} = adj / det
+          double adj[3][3];
+          adj[0][0] = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+          adj[0][1] = Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2];
+          adj[0][2] = Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1];
+          adj[1][0] = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+          adj[1][1] = Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0];
+          adj[1][2] = Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2];
+          adj[2][0] = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+          adj[2][1] = Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1];
+          adj[2][2] = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+          const double det = Jm[0][0] * adj[0][0] + Jm[0][1] * adj[1][0] + Jm[0][2] * adj[2][0];
+          minJ = std::min(minJ, det);
+          // G_mn = w_i w_j w_k |J| (J^{-1} J^{-T})_mn = w3 / det * (adj adj^T)_mn
+          const double scale = L.w[i] * L.w[j] * L.w[k] / det;
+          const int mm[6] = {0, 0, 0, 1, 1, 2}, nn[6] = {0, 1, 2, 1, 2, 2};
+          for (int q = 0; q < 6; ++q) {
+            double acc = 0.0;
+            for (int l = 0; l < 3; ++l) acc += adj[mm[q]][l] * adj[nn[q]][l];
+            G[q * NP + p] = scale * acc;
+          }
+          const int64_t gx = (int64_t)ex * N + i, gy = (int64_t)ey * N + j, gz = (int64_t)ez * N + k;
+          const int64_t g = (gz * NY + gy) * NX + gx;
+          uint32_t id = (uint32_t)g;
+          bool bnd = gx == 0 || gx == NX - 1 || gy == 0 || gy == NY - 1 || gz == 0 || gz == NZ - 1;
+          if (bnd) id |= kGidDirichlet;
+          const bool own = std::min<int64_t>(gx / N, nex - 1) == ex &&
+                           std::min<int64_t>(gy / N, ney - 1) == ey &&
+                           std::min<int64_t>(gz / N, nez - 1) == ez;
+          if (own) id |= kGidOwner;
+          gid[p] = id;
+        }
+    // diagonal of A_e: sum_l G_rr(l,j,k) D[l,i]^2 + ... + 2 G_rs D[i,i] D[j,j] + ...
+    const double* D = L.Dm.data();
+    for (int k = 0; k < Q; ++k)
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          const int p = (k * Q + j) * Q + i;
+          double acc = 0.0;
+          for (int l = 0; l < Q; ++l) {
+            acc += G[0 * NP + (k * Q + j) * Q + l] * D[l * Q + i] * D[l * Q + i];
+            acc += G[3 * NP + (k * Q + l) * Q + i] * D[l * Q + j] * D[l * Q + j];
+            acc += G[5 * NP + (l * Q + j) * Q + i] * D[l * Q + k] * D[l * Q + k];
+          }
+          const double di = D[i * Q + i], dj = D[j * Q + j], dk = D[k * Q + k];
+          acc += 2.0 * (G[1 * NP + p] * di * dj + G[2 * NP + p] * di * dk + G[4 * NP + p] * dj * dk);
+          diag_local[(size_t)e * NP + p] = acc;
+        }
+  }
+  L.min_jacobian = minJ;
+  if (!(minJ > 0.0)) ok = false;
+  for (int64_t q = 0; q < L.E * NP; ++q) {
+    const uint32_t id = L.gid[q];
+    if (!(id & kGidDirichlet)) L.diag[id & kGidMask] += diag_local[q];
+  }
+  return ok;
+}
+
+void fd_fine_stencil(double hx, double hy, double st[9]) {
+  for (int q = 0; q < 9; ++q) st[q] = 0.0;
+  st[4] = 2.0 / (hx * hx) + 2.0 / (hy * hy);
+  st[3] = st[5] = -1.0 / (hx * hx);
+  st[1] = st[7] = -1.0 / (hy * hy);
+}
+
+void fd_galerkin_stencil(const double fine[9], int c, double coarse[9]) {
+  // Coarse basis function of node (0,0) on the fine lattice: bilinear hat of
+  // half-width c.  A_c(0, (B,A)) = <phi_{(A c, B c)}, A phi_0> on an
+  // unbounded lattice (the Dirichlet truncation does not change interior-
+  // restricted entries for vertex-centred coarsening).
+  const int R = 3 * c;
+  const int W = 2 * R + 1;
+  auto hat = [c](int i) { return std::max(0.0, 1.0 - std::abs(i) / (double)c); };
+  std::vector<double> Aphi((size_t)W * W, 0.0);
+  for (int j = -R + 1; j < R; ++j)
+    for (int i = -R + 1; i < R; ++i) {
+      double acc = 0.0;
+      for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b) acc += fine[(a + 1) * 3 + (b + 1)] * hat(i + b) * hat(j + a);
+      Aphi[(size_t)(j + R) * W + (i + R)] = acc;
+    }
+  for (int A = -1; A <= 1; ++A)
+    for (int B = -1; B <= 1; ++B) {
+      double acc = 0.0;
+      for (int j = -R + 1; j < R; ++j)
+        for (int i = -R + 1; i < R; ++i)
+          acc += hat(i - B * c) * hat(j - A * c) * Aphi[(size_t)(j + R) * W + (i + R)];
+      coarse[(A + 1) * 3 + (B + 1)] = acc;
+    }
+}
+
+bool fd_dense_inverse(const double st[9], int mx, int my, std::vector<double>& inv) {
+  const int n = mx * my;
+  std::vector<double> A((size_t)n * n, 0.0);
+  for (int j = 0; j < my; ++j)
+    for (int i = 0; i < mx; ++i)
+      for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b) {
+          const int ii = i + b, jj = j + a;
+          if (ii < 0 || ii >= mx || jj < 0 || jj >= my) continue;
+          A[(size_t)(j * mx + i) * n + (jj * mx + ii)] += st[(a + 1) * 3 + (b + 1)];
+        }
+  // Cholesky A = L L^T (lower triangle of A overwritten)
+  for (int k = 0; k < n; ++k) {
+    double d = A[(size_t)k * n + k];
+    for (int m = 0; m < k; ++m) d -= A[(size_t)k * n + m] * A[(size_t)k * n + m];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    A[(size_t)k * n + k] = d;
+    for (int i = k + 1; i < n; ++i) {
+      double s = A[(size_t)i * n + k];
+      for (int m = 0; m < k; ++m) s -= A[(size_t)i * n + m] * A[(size_t)k * n + m];
+      A[(size_t)i * n + k] = s / d;
+    }
+  }
+  inv.assign((size_t)n * n, 0.0);
+  std::vector<double> y(n);
+  for (int col = 0; col < n; ++col) {
+    for (int i = 0; i < n; ++i) {   // L y = e_col
+      double s = (i == col) ? 1.0 : 0.0;
+      for (int m = 0; m < i; ++m) s -= A[(size_t)i * n + m] * y[m];
+      y[i] = s / A[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {   // L^T x = y
+      double s = y[i];
+      for (int m = i + 1; m < n; ++m) s -= A[(size_t)m * n + i] * inv[(size_t)m * n + col];
+      inv[(size_t)i * n + col] = s / A[(size_t)i * n + i];
+    }
+  }
+  return true;
+}
+
+}  // namespace chebmg

@@ -1,0 +1,198 @@
+"""GPU-vs-oracle parity for the SEM path: element Ax + gather-scatter, Jacobi diagonal,
+p-multigrid transfers, smoothers, coarse CG, V-cycle and flexible CG (Secs. 1, 2, 4.1)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov as K
+from oracle import multigrid as M
+from oracle import problems as P
+from oracle.chebyshev import smooth as oracle_smooth
+from oracle.sem import SemLevel, SemTransfer
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2210_03179_gb300 as cm  # noqa: E402
+from gpu_util import N, T, empty, relerr  # noqa: E402
+
+F64, F32 = cm.CHEBMG_F64, cm.CHEBMG_F32
+
+# 3 x 4 x 5 = 60 elements: several thread blocks per level and a ragged last block
+# (N = 1: 64 elements per block; N = 3: 8; N = 4: 8 -> 7 full + 4).
+MESH = (3, 4, 5)
+
+
+@pytest.fixture(scope="module")
+def verts():
+    return W.sem_box_vertices(*MESH)
+
+
+def solver(v, orders, kind="opt4th", k=2, sided="one-sided", prec="fp64", lmax=None, **kw):
+    return cm.Solver("sem", verts=v, orders=orders, kind=kind, order=k, sided=sided, prec=prec, lmax=lmax, **kw)
+
+
+@pytest.mark.parametrize("orders", [(7, 3, 1), (9, 5, 2), (8, 4), (6, 1), (2, 1), (4, 3, 2, 1)])
+def test_operator_diagonal_and_transfers(verts, orders):
+    levels = [SemLevel(verts, Nn) for Nn in orders]
+    s = solver(verts, orders, lmax=[1.0] * (len(orders) - 1))
+    rng = np.random.default_rng(sum(orders))
+    for j, L in enumerate(levels):
+        assert s.size(j) == L.n
+        x = rng.uniform(-1, 1, L.n)
+        y = empty(L.n)
+        cm.chebmg_apply_A(s.ctx, j, F64, T(x), y)
+        ref = L.apply_A(x)
+        assert relerr(N(y), ref) < 1e-12
+        assert np.all(N(y)[L.dirichlet] == 0.0)
+        d = empty(L.n)
+        cm.chebmg_inv_diagonal(s.ctx, j, F64, d)
+        assert relerr(N(d), L.inv_diagonal()) < 1e-12
+    for j in range(len(levels) - 1):
+        Tr = SemTransfer(levels[j], levels[j + 1])
+        nf, nc = levels[j].n, levels[j + 1].n
+        rf = rng.uniform(-1, 1, nf)
+        rc = empty(nc)
+        cm.chebmg_restrict(s.ctx, j, F64, T(rf), rc)
+        assert relerr(N(rc), Tr.restrict(rf)) < 1e-12
+        zc = rng.uniform(-1, 1, nc)
+        zf = empty(nf)
+        cm.chebmg_prolong(s.ctx, j, F64, T(zc), zf, accumulate=False)
+        assert relerr(N(zf), Tr.prolong(zc)) < 1e-12
+        base = rng.uniform(-1, 1, nf)
+        base[levels[j].dirichlet] = 0
+        zf = T(base)
+        cm.chebmg_prolong(s.ctx, j, F64, T(zc), zf, accumulate=True)
+        assert relerr(N(zf), base + Tr.prolong(zc)) < 1e-12
+    s.close()
+
+
+def test_dirichlet_inputs_are_ignored(verts):
+    L = SemLevel(verts, 3)
+    s = solver(verts, (3, 1), lmax=[1.0])
+    x = np.random.default_rng(0).uniform(-1, 1, L.n)
+    xz = x.copy()
+    xz[L.dirichlet] = 0
+    y1, y2 = empty(L.n), empty(L.n)
+    cm.chebmg_apply_A(s.ctx, 0, F64, T(x), y1)
+    cm.chebmg_apply_A(s.ctx, 0, F64, T(xz), y2)
+    # FP64 atomics add element contributions in a run-dependent order: equal up to rounding
+    assert relerr(N(y1), N(y2)) < 1e-14
+    s.close()
+
+
+@pytest.mark.parametrize("kind", ["1st", "4th", "opt4th"])
+@pytest.mark.parametrize("order", [1, 2, 4, 6])
+def test_smoother_matches_algorithms(verts, kind, order):
+    H = P.sem_hierarchy(verts, (7, 3, 1), kind=kind, k=1, sided="symmetric")
+    lmax = [L.lmax for L in H.levels[:-1]]
+    s = solver(verts, (7, 3, 1), kind=kind, k=1, sided="symmetric", lmax=lmax)
+    rng = np.random.default_rng(order)
+    for j in range(2):
+        L = H.levels[j]
+        b = rng.uniform(-1, 1, L.n)
+        b[L.dirichlet] = 0
+        for x_zero in (True, False):
+            x0 = None if x_zero else np.where(L.dirichlet, 0.0, rng.uniform(-1, 1, L.n))
+            ref = oracle_smooth(L, b, order, kind, L.lmax, 0.1, x0=x0)
+            x = empty(L.n) if x_zero else T(x0)
+            cm.chebmg_smooth(s.ctx, j, F64, T(b), x, order, x_zero)
+            assert relerr(N(x), ref) < 1e-12
+    s.close()
+
+
+def test_coarse_cg_and_lanczos(verts):
+    H = P.sem_hierarchy(verts, (5, 3, 1))
+    s = solver(verts, (5, 3, 1))
+    for j, L in enumerate(H.levels[:-1]):
+        assert abs(s.lambda_max(j) / L.lmax - 1) < 1e-10
+    Lc = H.levels[-1]
+    r = np.random.default_rng(9).uniform(-1, 1, Lc.n)
+    r[Lc.dirichlet] = 0
+    z = empty(Lc.n)
+    iters = cm.chebmg_coarse_solve(s.ctx, T(r), z)
+    zz = N(z)
+    assert np.linalg.norm(r - Lc.apply_A(zz)) <= 1.01e-10 * np.linalg.norm(r)
+    x_ref, it_ref = K.pcg_jacobi(Lc.apply_A, Lc.invD, r, 1e-10)
+    assert abs(iters - it_ref) <= 1
+    assert relerr(zz, x_ref) < 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("kind,k,sided", [("opt4th", 2, "one-sided"), ("4th", 2, "symmetric"),
+                                          ("1st", 3, "symmetric"), ("opt4th", 1, "one-sided"),
+                                          ("opt4th", 3, "one-sided")])
+def test_vcycle(verts, kind, k, sided):
+    H = P.sem_hierarchy(verts, (7, 3, 1), kind=kind, k=k, sided=sided)
+    s = solver(verts, (7, 3, 1), kind=kind, k=k, sided=sided, lmax=[L.lmax for L in H.levels[:-1]])
+    r = W.sem_rhs(*MESH, 7, seed=4)
+    z = empty(len(r))
+    cm.chebmg_vcycle(s.ctx, T(r), z)
+    # the coarse CG stops at 1e-10, so the cycles agree to about that level
+    assert relerr(N(z), M.vcycle(H, r)) < 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("sided", ["one-sided", "symmetric"])
+def test_pcg_solve_iterations_match(verts, k, sided):
+    H = P.sem_hierarchy(verts, (7, 3, 1), kind="opt4th", k=k, sided=sided)
+    s = solver(verts, (7, 3, 1), kind="opt4th", k=k, sided=sided, lmax=[L.lmax for L in H.levels[:-1]])
+    b = W.sem_rhs(*MESH, 7)
+    A = H.levels[0].apply_A
+    x_ref, it_ref, hist_ref = K.fcg(A, lambda r: M.vcycle(H, r), b, 1e-8)
+    u = empty(len(b))
+    code, it, rel, hist = cm.chebmg_pcg_solve(s.ctx, T(b), u, 1e-8, 200, history=True)
+    assert code == cm.CHEBMG_OK and rel <= 1e-8
+    assert abs(it - it_ref) <= 1
+    assert np.linalg.norm(b - A(N(u))) <= 1.01e-8 * np.linalg.norm(b)
+    assert relerr(N(u), x_ref) < 1e-6
+    s.close()
+
+
+def test_mixed_precision_solve(verts):
+    H = P.sem_hierarchy(verts, (7, 3, 1))
+    lmax = [L.lmax for L in H.levels[:-1]]
+    s64 = solver(verts, (7, 3, 1), lmax=lmax)
+    s32 = solver(verts, (7, 3, 1), prec="mixed", lmax=lmax)
+    b = W.sem_rhs(*MESH, 7)
+    u64, u32 = empty(len(b)), empty(len(b))
+    c64, it64, rel64, _ = cm.chebmg_pcg_solve(s64.ctx, T(b), u64, 1e-8, 200)
+    c32, it32, rel32, _ = cm.chebmg_pcg_solve(s32.ctx, T(b), u32, 1e-8, 200)
+    assert c64 == c32 == cm.CHEBMG_OK and rel32 <= 1e-8
+    assert it32 <= it64 + 2
+    A = H.levels[0].apply_A
+    assert np.linalg.norm(b - A(N(u32))) <= 1.01e-8 * np.linalg.norm(b)
+    # FP32 operator and smoother vs FP64 oracle: single-precision error only
+    L = H.levels[0]
+    x = np.where(L.dirichlet, 0, np.random.default_rng(2).uniform(-1, 1, L.n))
+    y = empty(L.n, True)
+    cm.chebmg_apply_A(s32.ctx, 0, F32, T(x, torch.float32), y)
+    assert relerr(N(y), A(x.astype(np.float32).astype(np.float64))) < 2e-5
+    s64.close()
+    s32.close()
+
+
+def test_host_entry_point(verts):
+    H = P.sem_hierarchy(verts, (5, 3, 1))
+    s = solver(verts, (5, 3, 1), lmax=[L.lmax for L in H.levels[:-1]])
+    b = W.sem_rhs(*MESH, 5)
+    u = np.zeros_like(b)
+    code, it, rel = cm.chebmg_pcg_solve_host(s.ctx, b, u, 1e-8, 200)
+    assert code == cm.CHEBMG_OK and rel <= 1e-8
+    assert np.linalg.norm(b - H.levels[0].apply_A(u)) <= 1.01e-8 * np.linalg.norm(b)
+    s.close()
+
+
+def test_setup_rejects_bad_input():
+    v = W.sem_box_vertices(2, 2, 2)
+    with pytest.raises(cm.ChebmgError):
+        solver(v, (3, 5))                       # orders must decrease
+    bad = v.copy()
+    bad[1, 1, 1] = bad[1, 1, 1] + 0.9           # fold an element
+    with pytest.raises(cm.ChebmgError) as e:
+        solver(bad, (3, 1))
+    assert e.value.code == cm.CHEBMG_EMESH
