@@ -153,6 +153,31 @@ int chebmg_pcg_solve(chebmg_ctx* ctx, const double* b, double* u, double rtol, i
 int chebmg_pcg_solve_host(chebmg_ctx* ctx, const double* b_host, double* u_host, double rtol,
                           int maxit, int* iters, double* relres);
 
+/* ---- allocation-free smoother ---------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory where they smooth (for example a plugin inside an application
+ * whose device memory belongs entirely to that application's pool, or a real-time loop in
+ * which cudaMalloc/cudaFree are forbidden because they may synchronise the device).
+ *
+ * Applies one smoother of the given kind and order (Algorithm 1 with lambda_min =
+ * lmin_ratio * lmax, or Algorithm 2 with beta_i = 1 / the optimized table) to the
+ * five-point operator on an m x m interior grid of [0,Lx] x [0,Ly] (spacing L/(m+1)),
+ * x updated in place as by chebmg_smooth on level 0 of an FD context; lmax is lambda_max
+ * of S A supplied by the caller.  b, x: caller-owned FP64 device vectors of m*m entries,
+ * x fastest.  No context, no device or host allocation.
+ *
+ * Limits and sharing: the work vectors live in one static device array of 4 x 262144
+ * doubles (8 MiB) that every device which loads the library reserves until the process
+ * exits; m*m > 262144 returns CHEBMG_EINVAL.  All calls on a device share that array, so
+ * calls whose work may overlap on the GPU (different streams, or host threads) race and
+ * must be serialised by the caller.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Returns EINVAL on bad arguments, ECUDA on a CUDA error. */
+int chebmg_fd_smooth_noalloc(int m, double Lx, double Ly, int kind, int order, double lmax,
+                             double lmin_ratio, const double* b, double* x, int x_is_zero,
+                             void* stream);
+
 /* ---- errors ------------------------------------------------------------------ */
 const char* chebmg_strerror(int code);
 const char* chebmg_last_error(void);

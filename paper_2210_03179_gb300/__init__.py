@@ -89,6 +89,8 @@ _SIGNATURES = {
                                  POINTER(c_double), POINTER(c_double)]),
     "chebmg_pcg_solve_host": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_double, c_int,
                                       POINTER(c_int), POINTER(c_double)]),
+    "chebmg_fd_smooth_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_int, c_double, c_double, c_void_p,
+                                         c_void_p, c_int, c_void_p]),
     "chebmg_strerror": (ctypes.c_char_p, [c_int]),
     "chebmg_last_error": (ctypes.c_char_p, []),
 }
@@ -266,6 +268,16 @@ def chebmg_pcg_solve_host(ctx, b_host: np.ndarray, u_host: np.ndarray, rtol=1e-8
                                               byref(it), byref(rel)),
                   "chebmg_pcg_solve_host", allow=(CHEBMG_ENOTCONV,))
     return code, it.value, rel.value
+
+
+def chebmg_fd_smooth_noalloc(m, Lx, Ly, kind, order, lmax, lmin_ratio, b, x, x_is_zero, stream=None):
+    """Context-free FD smoother that allocates nothing (see include/chebmg.h)."""
+    n = int(m) * int(m)
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().chebmg_fd_smooth_noalloc(int(m), float(Lx), float(Ly), k, int(order), float(lmax),
+                                          float(lmin_ratio), _ptr(b, n, CHEBMG_F64, "b"), _ptr(x, n, CHEBMG_F64, "x"),
+                                          1 if x_is_zero else 0, _stream_handle(stream)),
+           "chebmg_fd_smooth_noalloc")
 
 
 class Solver:

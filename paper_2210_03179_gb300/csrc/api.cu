@@ -68,6 +68,10 @@ const double kBeta[16][16] = {
 
 namespace chebmg {
 
+// Row k (1..16) of the optimized 4th-kind coefficient table, for other translation units.
+const double* beta_row(int k) { return (k >= 1 && k <= 16) ? kBeta[k - 1] : nullptr; }
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 enum { VB = 0, VX = 1, VR = 2, VD = 3, VY = 4, NV = 5 };
 enum { TYPE_SEM = 0, TYPE_FD = 1 };
 

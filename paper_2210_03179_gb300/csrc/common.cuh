@@ -108,4 +108,9 @@ void lanczos_w(int64_t n, const double* invD, const double* y, const double* v,
                const double* vprev, double alpha, double beta, double* w, cudaStream_t s);
 void scale(int64_t n, double a, const double* x, double* y, cudaStream_t s);
 
+// Defined in api.cu: row k of the optimized-beta table (nullptr outside 1..16) and the
+// per-thread message returned by chebmg_last_error().
+const double* beta_row(int k);
+void set_last_error(const char* msg);
+
 }  // namespace chebmg
