@@ -153,6 +153,16 @@ int chebmg_pcg_solve(chebmg_ctx* ctx, const double* b, double* u, double rtol, i
 int chebmg_pcg_solve_host(chebmg_ctx* ctx, const double* b_host, double* u_host, double rtol,
                           int maxit, int* iters, double* relres);
 
+/* ---- self-test -------------------------------------------------------------- */
+
+/* Failure-path self-test of the persistent SEM coarse solver (not part of the paper's
+ * method): launches it with one phantom block that never arrives at the grid barrier, so
+ * every bounded wait runs out (after about a second), the kernel records a timeout and
+ * returns instead of hanging.  *status receives the code the solver reports
+ * (CHEBMG_ETIMEOUT expected); the context stays usable.  EINVAL if the context has no
+ * persistent coarse solver. */
+int chebmg_selftest_coarse_timeout(chebmg_ctx* ctx, int* status);
+
 /* ---- allocation-free smoother ---------------------------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers that cannot

@@ -91,6 +91,7 @@ _SIGNATURES = {
                                       POINTER(c_int), POINTER(c_double)]),
     "chebmg_fd_smooth_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_int, c_double, c_double, c_void_p,
                                          c_void_p, c_int, c_void_p]),
+    "chebmg_selftest_coarse_timeout": (c_int, [c_void_p, POINTER(c_int)]),
     "chebmg_strerror": (ctypes.c_char_p, [c_int]),
     "chebmg_last_error": (ctypes.c_char_p, []),
 }
@@ -268,6 +269,13 @@ def chebmg_pcg_solve_host(ctx, b_host: np.ndarray, u_host: np.ndarray, rtol=1e-8
                                               byref(it), byref(rel)),
                   "chebmg_pcg_solve_host", allow=(CHEBMG_ENOTCONV,))
     return code, it.value, rel.value
+
+
+def chebmg_selftest_coarse_timeout(ctx) -> int:
+    """Runs the persistent coarse solver with a barrier that can never complete; returns its status."""
+    st = c_int()
+    _check(lib().chebmg_selftest_coarse_timeout(ctx, byref(st)), "chebmg_selftest_coarse_timeout")
+    return st.value
 
 
 def chebmg_fd_smooth_noalloc(m, Lx, Ly, kind, order, lmax, lmin_ratio, b, x, x_is_zero, stream=None):

@@ -115,6 +115,16 @@ struct chebmg_ctx {
   double *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr, *cb = nullptr, *cx = nullptr;
   double* cinv = nullptr;       // FD coarsest dense inverse
   int last_coarse_iters = 0;
+  // SEM coarsest level assembled in ELL form for the persistent coarse PCG kernel
+  int* ell_col = nullptr;
+  double* ell_val = nullptr;
+  int nslot = 0;
+  int coarse_grid = 0;
+  bool coop_ok = false;
+  unsigned* cctl = nullptr;     // [5] control words of the persistent kernel
+  unsigned* hcctl = nullptr;    // pinned host copy
+  double* cpart_pq = nullptr;
+  double* cpart_rr = nullptr;
 };
 
 namespace {
@@ -151,7 +161,21 @@ Stencil9<T> stencil(const Level& L) {
 
 void read_scal(chebmg_ctx* c) {
   CK(cudaMemcpyAsync(c->hscal, c->scal, sizeof(double) * S_NSLOTS, cudaMemcpyDeviceToHost, c->s));
+  if (c->cctl) CK(cudaMemcpyAsync(c->hcctl, c->cctl, sizeof(unsigned) * 5, cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
+}
+
+// Worst error recorded by persistent coarse solves since the last reset (0 if none).
+int coarse_sticky_error(chebmg_ctx* c) {
+  if (!c->cctl) return CHEBMG_OK;
+  const unsigned w = c->hcctl[4];
+  if (w == CS_TIMEOUT) return CHEBMG_ETIMEOUT;
+  if (w == CS_BREAKDOWN) return CHEBMG_EBREAKDOWN;
+  return CHEBMG_OK;
+}
+
+void reset_coarse_sticky(chebmg_ctx* c) {
+  if (c->cctl) CK(cudaMemsetAsync(c->cctl + 4, 0, sizeof(unsigned), c->s));
 }
 
 void read_cscal(chebmg_ctx* c) {
@@ -257,6 +281,33 @@ int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {
   }
   const double* S = static_cast<const double*>(C.invD[CHEBMG_F64]);
   double *r = c->cr, *z = c->cz, *p = c->cp, *q = c->cq;
+  if (c->coop_ok) {
+    // whole Jacobi-PCG in one cooperative launch; no host round trip.  Status and
+    // iterations land in cctl[2..3], errors also in the sticky cctl[4].
+    CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 4, c->s));
+    CoarseCG a;
+    a.n = n;
+    a.nslot = c->nslot;
+    a.col = c->ell_col;
+    a.val = c->ell_val;
+    a.invD = S;
+    a.b = b;
+    a.x = x;
+    a.r = r;
+    a.z = z;
+    a.p = p;
+    a.q = q;
+    a.part_pq = c->cpart_pq;
+    a.part_rr = c->cpart_rr;
+    a.ctl = c->cctl;
+    a.rtol = c->o.coarse_rtol;
+    a.maxit = c->o.coarse_maxit;
+    a.phantom_blocks = 0;
+    cudaError_t e = cudaSuccess;
+    if (coarse_pcg_launch(a, c->coarse_grid, c->s, &e)) return CHEBMG_OK;
+    cudaGetLastError();
+    c->coop_ok = false;   // cooperative launch refused: use the host-driven loop from now on
+  }
   // x = 0, r = b, z = S r, p = z, RZ = (r, z), RR = (r, r): one CG update with alpha = 0, p = q = 0
   double* sc = c->cscal;
   double* part = c->cpartial;
@@ -440,6 +491,19 @@ void common_alloc(chebmg_ctx* c) {
   c->cq = dalloc<double>(c, nc);
   c->cb = dalloc<double>(c, nc);
   c->cx = dalloc<double>(c, nc);
+  if (c->ell_col) {
+    int coop = 0;
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev));
+    c->coarse_grid = coarse_pcg_grid(nc);
+    c->coop_ok = coop != 0 && c->coarse_grid > 0;
+    c->cctl = dalloc<unsigned>(c, 5);
+    CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 5, c->s));
+    CK(cudaMallocHost(&h, sizeof(unsigned) * 5));
+    c->hcctl = static_cast<unsigned*>(h);
+    std::memset(c->hcctl, 0, sizeof(unsigned) * 5);
+    c->cpart_pq = dalloc<double>(c, std::max(1, c->coarse_grid));
+    c->cpart_rr = dalloc<double>(c, 2 * std::max(1, c->coarse_grid));
+  }
 }
 
 template <typename T>
@@ -507,6 +571,7 @@ void destroy_ctx(chebmg_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hcscal) cudaFreeHost(c->hcscal);
+  if (c->hcctl) cudaFreeHost(c->hcctl);
   delete c;
 }
 
@@ -665,6 +730,14 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
           L.Jn[CHEBMG_F64] = upload<double>(c, J);
           if (c->fp32) L.Jn[CHEBMG_F32] = upload<float>(c, J);
         }
+        if (j + 1 == nlevels) {
+          std::vector<int> col;
+          std::vector<double> val;
+          assemble_ell(h, c->nslot, col, val);
+          c->ell_col = dalloc<int>(c, (int64_t)col.size());
+          CK(cudaMemcpy(c->ell_col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
+          c->ell_val = upload<double>(c, val);
+        }
         c->L.push_back(L);
         alloc_vectors(c, c->L.back(), c->fp32);
         std::vector<double>().swap(h.G);
@@ -787,8 +860,16 @@ int chebmg_coarse_solve(chebmg_ctx* c, const double* r, double* z, int* iters) {
   return guard([&]() -> int {
     enter(c);
     if (!r || !z) throw Error(CHEBMG_EINVAL, "NULL vector");
+    reset_coarse_sticky(c);
     int rc = coarse_solve64(c, r, z);
     CK(cudaStreamSynchronize(c->s));
+    if (c->coop_ok && c->L.back().type == TYPE_SEM) {
+      read_scal(c);
+      c->last_coarse_iters = (int)c->hcctl[3];
+      const unsigned st = c->hcctl[2];
+      rc = st == CS_OK ? CHEBMG_OK : st == CS_NOTCONV ? CHEBMG_ENOTCONV
+           : coarse_sticky_error(c) != CHEBMG_OK ? coarse_sticky_error(c) : CHEBMG_EBREAKDOWN;
+    }
     if (iters) *iters = c->last_coarse_iters;
     return rc;
   });
@@ -798,9 +879,12 @@ int chebmg_vcycle(chebmg_ctx* c, const double* r, double* z) {
   return guard([&]() -> int {
     enter(c);
     if (!r || !z) throw Error(CHEBMG_EINVAL, "NULL vector");
+    reset_coarse_sticky(c);
     int rc = vcycle_top(c, r, z);
     check_launch();
-    return rc == CHEBMG_ENOTCONV ? CHEBMG_OK : rc;
+    read_scal(c);
+    if (rc == CHEBMG_OK || rc == CHEBMG_ENOTCONV) rc = coarse_sticky_error(c);
+    return rc;
   });
 }
 
@@ -814,6 +898,7 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
     const double* S = static_cast<const double*>(L.invD[CHEBMG_F64]);
     double *r = c->kr, *z = c->kz, *p = c->kp, *q = c->kq, *ro = c->kro;
     if (iters) *iters = 0;
+    reset_coarse_sticky(c);
     masked_copy(n, b, S, r, c->s);
     zero<double>(c, u, n);
     dot2(n, r, r, nullptr, nullptr, S_BB, -1, POST_NONE, c->partial, c->scal, c->s);
@@ -837,6 +922,12 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
       fcg_update_xr(n, u, r, ro, p, q, c->partial, c->scal, c->s);
       read_scal(c);
       const double pq = c->hscal[S_PQ], rr = c->hscal[S_RR];
+      const int crc = coarse_sticky_error(c);
+      if (crc != CHEBMG_OK) {
+        if (iters) *iters = it;
+        g_last_error = "coarse solve inside the V-cycle failed";
+        return crc;
+      }
       if (!(pq > 0.0) || !std::isfinite(rr)) {
         if (iters) *iters = it;
         if (relres) *relres = std::sqrt(rr / bb);
@@ -873,6 +964,42 @@ int chebmg_pcg_solve_host(chebmg_ctx* c, const double* b_host, double* u_host, d
     CK(cudaMemcpyAsync(u_host, u, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     return rc;
+  });
+}
+
+int chebmg_selftest_coarse_timeout(chebmg_ctx* c, int* status) {
+  return guard([&]() -> int {
+    enter(c);
+    if (!status) throw Error(CHEBMG_EINVAL, "status is NULL");
+    if (!c->cctl || !c->coop_ok) throw Error(CHEBMG_EINVAL, "no persistent coarse solver in this context");
+    Level& C = c->L.back();
+    const int64_t n = C.n;
+    CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 5, c->s));
+    CoarseCG a;
+    a.n = n;
+    a.nslot = c->nslot;
+    a.col = c->ell_col;
+    a.val = c->ell_val;
+    a.invD = static_cast<const double*>(C.invD[CHEBMG_F64]);
+    a.b = c->cb;
+    a.x = c->cx;
+    a.r = c->cr;
+    a.z = c->cz;
+    a.p = c->cp;
+    a.q = c->cq;
+    a.part_pq = c->cpart_pq;
+    a.part_rr = c->cpart_rr;
+    a.ctl = c->cctl;
+    a.rtol = c->o.coarse_rtol;
+    a.maxit = c->o.coarse_maxit;
+    a.phantom_blocks = 1;    // one arrival that never comes: every barrier wait runs out
+    cudaError_t e = cudaSuccess;
+    if (!coarse_pcg_launch(a, c->coarse_grid, c->s, &e)) throw Error(CHEBMG_ECUDA, cudaGetErrorString(e));
+    read_scal(c);
+    *status = coarse_sticky_error(c);
+    CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 5, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return CHEBMG_OK;
   });
 }
 

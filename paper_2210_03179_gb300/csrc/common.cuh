@@ -99,6 +99,33 @@ void update_p(int64_t n, const double* z, double* p, const double* scal, cudaStr
 void cg_update(int64_t n, double* x, double* r, double* z, const double* p, const double* q,
                const double* invD, double* partial, double* scal, cudaStream_t s);
 
+// ---- persistent coarse solve (one cooperative launch per solve) ----
+// Control words: ctl[0] barrier arrivals, ctl[1] barrier generation, ctl[2] status of the
+// last solve, ctl[3] its iterations, ctl[4] sticky worst error since the caller reset it.
+enum CoarseStatus { CS_NONE = 0, CS_OK = 1, CS_NOTCONV = 2, CS_BREAKDOWN = 3, CS_TIMEOUT = 4 };
+struct CoarseCG {
+  int64_t n;
+  int nslot;
+  const int* col;        // ELL, slot-major
+  const double* val;
+  const double* invD;
+  const double* b;
+  double* x;
+  double* r;
+  double* z;
+  double* p;
+  double* q;
+  double* part_pq;       // [gridDim]
+  double* part_rr;       // [2 * gridDim]
+  unsigned* ctl;         // [5], ctl[0..1] zero at launch
+  double rtol;
+  int maxit;
+  unsigned phantom_blocks;   // self-test only: barrier also waits for this many blocks that never come
+};
+// Returns false (nothing launched) if a cooperative launch is not possible.
+bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err);
+int coarse_pcg_grid(int64_t n);
+
 // ---- Lanczos helpers ----
 void splitmix_fill(int64_t n, uint64_t seed, const double* invD, double* v, cudaStream_t s);
 // t = sqrt(invD) * v

@@ -9,6 +9,8 @@
 // an elementwise pass.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace chebmg {
@@ -633,6 +635,207 @@ void cg_update(int64_t n, double* x, double* r, double* z, const double* p, cons
   k_cg_update<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, z, p, q, invD, partial, scal);
   k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, S_ZR, POST_BETA_CG, scal);
   g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+// ===========================================================================
+// Persistent coarse Jacobi-PCG: the whole solve in one cooperative launch.
+// ELL SpMV, deterministic block partial sums read back by every block in the
+// same order (so all blocks take identical alpha/beta/stop decisions), and a
+// grid barrier whose waits are bounded: a block that waits too long records a
+// timeout and returns, and every other block then also returns at its next
+// (bounded) wait, so the kernel always finishes.
+// ===========================================================================
+constexpr int kCoarseThreads = 256;
+constexpr unsigned kSpinLimit = 1u << 24;   // x ~64 ns sleep: about a second
+
+__device__ __forceinline__ void block_allsum2(double& a, double& b) {
+  __shared__ double sa[kCoarseThreads / 32], sb[kCoarseThreads / 32];
+  __syncthreads();
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  double ta = 0.0, tb = 0.0;
+#pragma unroll
+  for (int q = 0; q < kCoarseThreads / 32; ++q) {   // same order in every thread
+    ta += sa[q];
+    tb += sb[q];
+  }
+  a = ta;
+  b = tb;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned& gen, unsigned expected) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gen + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl[0], 1u);
+    if (arrived == expected - 1) {
+      atomicExch(&ctl[0], 0u);
+      __threadfence();
+      atomicExch(&ctl[1], target);
+    } else {
+      unsigned spins = 0;
+      while (*(volatile unsigned*)&ctl[1] != target) {
+        if (++spins > kSpinLimit) {
+          atomicMax((int*)&ctl[4], (int)CS_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  gen += 1;
+  return s_ok != 0;
+}
+
+// Sum of the per-block partials (two arrays of gridDim entries, stride `st`), same order everywhere.
+__device__ __forceinline__ void sum_partials(const double* part, int stride, int off0, int off1, double& a, double& b) {
+  double ta = 0.0, tb = 0.0;
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+    ta += ((volatile const double*)part)[q * stride + off0];
+    if (off1 >= 0) tb += ((volatile const double*)part)[q * stride + off1];
+  }
+  block_allsum2(ta, tb);
+  a = ta;
+  b = tb;
+}
+
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
+  const int64_t n = a.n;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned gen = 0;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t g = t0; g < n; g += stride) {
+    const double S = a.invD[g];
+    const double rv = S != 0.0 ? a.b[g] : 0.0;
+    const double zv = S * rv;
+    a.x[g] = 0.0;
+    a.r[g] = rv;
+    a.z[g] = zv;
+    a.p[g] = zv;
+    rr += rv * rv;
+    rz += rv * zv;
+  }
+  block_allsum2(rr, rz);
+  if (threadIdx.x == 0) {
+    a.part_rr[2 * blockIdx.x] = rr;
+    a.part_rr[2 * blockIdx.x + 1] = rz;
+  }
+  if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
+  double bb, rz_old;
+  sum_partials(a.part_rr, 2, 0, 1, bb, rz_old);
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  if (!(bb > 0.0)) {
+    if (lead) {
+      a.ctl[2] = bb == 0.0 ? CS_OK : CS_BREAKDOWN;
+      a.ctl[3] = 0;
+      if (bb != 0.0) atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
+    }
+    return;
+  }
+  const double tol2 = a.rtol * a.rtol * bb;
+  for (int it = 1; it <= a.maxit; ++it) {
+    double pq = 0.0, dummy = 0.0;
+    for (int64_t g = t0; g < n; g += stride) {
+      double s = 0.0;
+      // p of other blocks' rows was written before the last barrier: read it from L2
+      for (int k = 0; k < a.nslot; ++k) s += a.val[k * n + g] * __ldcg(&a.p[a.col[k * n + g]]);
+      a.q[g] = s;
+      pq += a.p[g] * s;
+    }
+    block_allsum2(pq, dummy);
+    if (threadIdx.x == 0) a.part_pq[blockIdx.x] = pq;
+    if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
+    double pq_tot;
+    sum_partials(a.part_pq, 1, 0, -1, pq_tot, dummy);
+    if (!(pq_tot > 0.0)) {
+      if (lead) {
+        a.ctl[2] = CS_BREAKDOWN;
+        a.ctl[3] = it;
+        atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
+      }
+      return;
+    }
+    const double alpha = rz_old / pq_tot;
+    rr = 0.0;
+    rz = 0.0;
+    for (int64_t g = t0; g < n; g += stride) {
+      a.x[g] += alpha * a.p[g];
+      const double rn = a.r[g] - alpha * a.q[g];
+      const double zn = a.invD[g] * rn;
+      a.r[g] = rn;
+      a.z[g] = zn;
+      rr += rn * rn;
+      rz += rn * zn;
+    }
+    block_allsum2(rr, rz);
+    if (threadIdx.x == 0) {
+      a.part_rr[2 * blockIdx.x] = rr;
+      a.part_rr[2 * blockIdx.x + 1] = rz;
+    }
+    if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
+    double rr_tot, rz_new;
+    sum_partials(a.part_rr, 2, 0, 1, rr_tot, rz_new);
+    if (!(rr_tot == rr_tot)) {
+      if (lead) {
+        a.ctl[2] = CS_BREAKDOWN;
+        a.ctl[3] = it;
+        atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
+      }
+      return;
+    }
+    if (rr_tot <= tol2) {
+      if (lead) {
+        a.ctl[2] = CS_OK;
+        a.ctl[3] = it;
+      }
+      return;
+    }
+    const double beta = rz_new / rz_old;
+    rz_old = rz_new;
+    for (int64_t g = t0; g < n; g += stride) a.p[g] = a.z[g] + beta * a.p[g];
+    if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
+  }
+  if (lead) {
+    a.ctl[2] = CS_NOTCONV;
+    a.ctl[3] = a.maxit;
+  }
+}
+
+int coarse_pcg_grid(int64_t n) {
+  static int cached = -1;
+  if (cached < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_pcg, kCoarseThreads, 0);
+    cached = sms * (per_sm > 0 ? 1 : 0);
+  }
+  const int64_t need = (n + kCoarseThreads - 1) / kCoarseThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(cached, need));
+}
+
+bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err) {
+  CoarseCG arg = a;
+  void* params[] = {&arg};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_coarse_pcg, dim3(grid), dim3(kCoarseThreads),
+                                              params, 0, s);
+  count();
+  if (err) *err = e;
+  return e == cudaSuccess;
 }
 
 // ===========================================================================

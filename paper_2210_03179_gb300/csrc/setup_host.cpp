@@ -208,6 +208,92 @@ bool build_sem_level(int nex, int ney, int nez, const double* verts, int N, SemH
   return ok;
 }
 
+void assemble_ell(const SemHostLevel& L, int& nslot, std::vector<int>& col, std::vector<double>& val) {
+  const int Q = L.NQ, NP = L.NP;
+  const double* D = L.Dm.data();
+  struct Trip {
+    uint32_t row, col;
+    double v;
+  };
+  std::vector<Trip> trips;
+  trips.reserve((size_t)L.E * NP * 27);
+  std::vector<double> Ae((size_t)NP * NP);
+  for (int64_t e = 0; e < L.E; ++e) {
+    std::fill(Ae.begin(), Ae.end(), 0.0);
+    const double* G = &L.G[(size_t)e * 6 * NP];
+    // A_e[p][q] = sum_pt sum_mn Dhat_m(pt, p) G_mn(pt) Dhat_n(pt, q); Dhat_m(pt, .) is nonzero
+    // only on the line through pt in direction m, with values D[pt_m][a].
+    for (int k = 0; k < Q; ++k)
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          const int pt = (k * Q + j) * Q + i;
+          const int c[3] = {i, j, k};
+          const double g[3][3] = {{G[0 * NP + pt], G[1 * NP + pt], G[2 * NP + pt]},
+                                  {G[1 * NP + pt], G[3 * NP + pt], G[4 * NP + pt]},
+                                  {G[2 * NP + pt], G[4 * NP + pt], G[5 * NP + pt]}};
+          auto node = [&](int dir, int a) {
+            int cc[3] = {i, j, k};
+            cc[dir] = a;
+            return (cc[2] * Q + cc[1]) * Q + cc[0];
+          };
+          for (int m = 0; m < 3; ++m)
+            for (int a = 0; a < Q; ++a) {
+              const double dm = D[c[m] * Q + a];
+              if (dm == 0.0) continue;
+              const int p = node(m, a);
+              for (int n = 0; n < 3; ++n) {
+                const double gm = dm * g[m][n];
+                for (int b = 0; b < Q; ++b) {
+                  const double dn = D[c[n] * Q + b];
+                  if (dn == 0.0) continue;
+                  Ae[(size_t)p * NP + node(n, b)] += gm * dn;
+                }
+              }
+            }
+        }
+    const uint32_t* gid = &L.gid[(size_t)e * NP];
+    for (int p = 0; p < NP; ++p) {
+      if (gid[p] & kGidDirichlet) continue;
+      for (int q = 0; q < NP; ++q) {
+        if (gid[q] & kGidDirichlet) continue;
+        trips.push_back({gid[p] & kGidMask, gid[q] & kGidMask, Ae[(size_t)p * NP + q]});
+      }
+    }
+  }
+  std::stable_sort(trips.begin(), trips.end(), [](const Trip& a, const Trip& b) {
+    return a.row != b.row ? a.row < b.row : a.col < b.col;
+  });
+  const int64_t n = L.n;
+  std::vector<int> count((size_t)n, 0);
+  std::vector<int> rcol;
+  std::vector<double> rval;
+  std::vector<int64_t> start((size_t)n + 1, 0);
+  // merge duplicates (sum in element order) into compressed rows
+  for (size_t t = 0; t < trips.size();) {
+    size_t u = t;
+    double acc = 0.0;
+    while (u < trips.size() && trips[u].row == trips[t].row && trips[u].col == trips[t].col) acc += trips[u++].v;
+    rcol.push_back((int)trips[t].col);
+    rval.push_back(acc);
+    count[trips[t].row] += 1;
+    t = u;
+  }
+  nslot = 1;
+  for (int64_t g = 0; g < n; ++g) {
+    start[g + 1] = start[g] + count[g];
+    nslot = std::max(nslot, count[g]);
+  }
+  col.assign((size_t)nslot * n, 0);
+  val.assign((size_t)nslot * n, 0.0);
+  for (int64_t g = 0; g < n; ++g) {
+    for (int s = 0; s < nslot; ++s) {
+      const bool live = s < count[g];
+      col[(size_t)s * n + g] = live ? rcol[start[g] + s] : (int)g;
+      val[(size_t)s * n + g] = live ? rval[start[g] + s] : 0.0;
+    }
+  }
+}
+
 void fd_fine_stencil(double hx, double hy, double st[9]) {
   for (int q = 0; q < 9; ++q) st[q] = 0.0;
   st[4] = 2.0 / (hx * hx) + 2.0 / (hy * hy);

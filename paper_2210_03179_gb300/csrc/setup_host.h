@@ -37,6 +37,12 @@ struct SemHostLevel {
 // quadrature point has a non-positive Jacobian.
 bool build_sem_level(int nex, int ney, int nez, const double* verts, int N, SemHostLevel& out);
 
+// Assembled operator of a SEM level in ELL form (slot-major: entry s of row g at s*n + g),
+// rows and columns of Dirichlet nodes removed (their rows are empty, padded with col = g,
+// val = 0).  Element matrices come from the same six geometric factors as the matrix-free
+// operator, summed per (row, col) in element order.
+void assemble_ell(const SemHostLevel& L, int& nslot, std::vector<int>& col, std::vector<double>& val);
+
 // Five-point operator on an mx x my grid with spacings hx, hy as a 3x3 stencil
 // st[(a+1)*3 + (b+1)] for the neighbour (i+b, j+a).
 void fd_fine_stencil(double hx, double hy, double st[9]);

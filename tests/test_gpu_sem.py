@@ -196,3 +196,22 @@ def test_setup_rejects_bad_input():
     with pytest.raises(cm.ChebmgError) as e:
         solver(bad, (3, 1))
     assert e.value.code == cm.CHEBMG_EMESH
+
+
+def test_bounded_barrier_wait_reports_timeout_and_context_survives(verts):
+    # The persistent coarse solver waits at a grid barrier with a bounded spin; with a
+    # phantom block that never arrives every wait runs out and the kernel returns a
+    # timeout status instead of hanging.  The same context must still solve correctly.
+    import time
+    H = P.sem_hierarchy(verts, (3, 1), kind="opt4th", k=1, sided="symmetric")
+    s = solver(verts, (3, 1), kind="opt4th", k=1, sided="symmetric", lmax=[H.levels[0].lmax])
+    t0 = time.time()
+    st = cm.chebmg_selftest_coarse_timeout(s.ctx)
+    assert st == cm.CHEBMG_ETIMEOUT
+    assert time.time() - t0 < 30
+    Lc = H.levels[-1]
+    r = np.where(Lc.dirichlet, 0.0, np.random.default_rng(1).uniform(-1, 1, Lc.n))
+    z = empty(Lc.n)
+    cm.chebmg_coarse_solve(s.ctx, T(r), z)
+    assert np.linalg.norm(r - Lc.apply_A(N(z))) <= 1.01e-10 * np.linalg.norm(r)
+    s.close()
