@@ -137,17 +137,22 @@ class Clocks:
 
 # ---------------------------------------------------------------------------
 def main():
+    global NE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ne", type=int, default=NE,
+                    help="elements per direction (profiling runs only; the benchmark uses 32)")
     ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
                     help="set up, warm up, run one solve inside the NVTX range 'solve' and exit "
                          "(for ncu --nvtx-include solve/)")
     args = ap.parse_args()
 
+    if args.profile_solve:
+        NE = args.ne
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -293,7 +298,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t32 * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": config({"parallelism": f"replicas x{world_n}"}),
+            "config": config({"parallelism": f"replicas x{world_n}",
+                              "ax8_elements_per_block": {"fp32": cm.chebmg_tile_choice(s32.ctx, 0, 1),
+                                                         "fp64": cm.chebmg_tile_choice(s64.ctx, 0, 0)}}),
             "time_to_1e8_s": {"mixed": t32, "fp64": t64},
             "iterations": {"mixed": it32, "fp64": it64},
             "speedup_mixed_vs_fp64": t64 / t32,

@@ -106,8 +106,11 @@ int chebmg_num_levels(const chebmg_ctx* ctx, int* nlevels);
 int chebmg_level_size(const chebmg_ctx* ctx, int level, int64_t* n);
 /* lambda_max of S A used by the smoother on `level` (after lmax_scale/override). */
 int chebmg_lambda_max(const chebmg_ctx* ctx, int level, double* out);
-/* Kernel launches issued by this context since setup (for accounting). */
+/* Kernel launches issued by this library in this process (ctx unused; for accounting). */
 int chebmg_launch_count(const chebmg_ctx* ctx, int64_t* count);
+/* Elements per thread block chosen by the setup-time autotuner for the order-7 element
+ * operator on `level` in `dtype` (0 if the level does not use that kernel). */
+int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* elements_per_block);
 
 /* ---- per-level operators (device vectors, dtype as above) ---------------- */
 

@@ -78,6 +78,7 @@ _SIGNATURES = {
     "chebmg_level_size": (c_int, [c_void_p, c_int, POINTER(c_int64)]),
     "chebmg_lambda_max": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "chebmg_launch_count": (c_int, [c_void_p, POINTER(c_int64)]),
+    "chebmg_tile_choice": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
     "chebmg_apply_A": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "chebmg_inv_diagonal": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "chebmg_smooth": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_int]),
@@ -201,6 +202,12 @@ def chebmg_lambda_max(ctx, level) -> float:
 def chebmg_launch_count(ctx=None) -> int:
     v = c_int64()
     _check(lib().chebmg_launch_count(ctx, byref(v)), "chebmg_launch_count")
+    return v.value
+
+
+def chebmg_tile_choice(ctx, level, dtype) -> int:
+    v = c_int()
+    _check(lib().chebmg_tile_choice(ctx, int(level), int(dtype), byref(v)), "chebmg_tile_choice")
     return v.value
 
 

@@ -91,6 +91,7 @@ struct Level {
   void* D[2] = {nullptr, nullptr};
   void* Jn[2] = {nullptr, nullptr};   // interpolation from level+1 to this level, [Qf][Qc]
   void* v[2][NV] = {{nullptr}};
+  int eb[2] = {2, 2};   // elements per block of the order-7 operator, per dtype (autotuned)
 };
 
 }  // namespace chebmg
@@ -123,8 +124,10 @@ struct chebmg_ctx {
   bool coop_ok = false;
   unsigned* cctl = nullptr;     // [5] control words of the persistent kernel
   unsigned* hcctl = nullptr;    // pinned host copy
-  double* cpart_pq = nullptr;
-  double* cpart_rr = nullptr;
+  double* cpart = nullptr;      // [2][3 * coarse_grid]
+  double* cvec[1] = {nullptr};  // u = M r of the persistent coarse CG
+  unsigned* dstat = nullptr;    // [4] device-side error flags of the operator kernels
+  unsigned* hdstat = nullptr;
 };
 
 namespace {
@@ -162,11 +165,13 @@ Stencil9<T> stencil(const Level& L) {
 void read_scal(chebmg_ctx* c) {
   CK(cudaMemcpyAsync(c->hscal, c->scal, sizeof(double) * S_NSLOTS, cudaMemcpyDeviceToHost, c->s));
   if (c->cctl) CK(cudaMemcpyAsync(c->hcctl, c->cctl, sizeof(unsigned) * 5, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaMemcpyAsync(c->hdstat, c->dstat, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
 }
 
 // Worst error recorded by persistent coarse solves since the last reset (0 if none).
 int coarse_sticky_error(chebmg_ctx* c) {
+  if (c->hdstat[0]) return CHEBMG_ETIMEOUT;     // an operator kernel's bounded wait ran out
   if (!c->cctl) return CHEBMG_OK;
   const unsigned w = c->hcctl[4];
   if (w == CS_TIMEOUT) return CHEBMG_ETIMEOUT;
@@ -189,7 +194,10 @@ void apply_into(chebmg_ctx* c, int j, const T* x, T* y) {
   Level& L = c->L[j];
   const int dt = dt_of<T>();
   if (L.type == TYPE_SEM) {
-    sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s);
+    if (L.Q == 8)
+      sem_ax8<T>(L.E, L.gid, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s);
+    else
+      sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s);
   } else {
     fd_apply<T>(L.mx, L.my, stencil<T>(L), x, y, c->s);
   }
@@ -269,6 +277,26 @@ void prolong_to(chebmg_ctx* c, int j, const T* zc, T* zf, int accumulate) {
   check_launch();
 }
 
+CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
+  Level& C = c->L.back();
+  CoarseCG a;
+  a.n = C.n;
+  a.nslot = c->nslot;
+  a.col = c->ell_col;
+  a.val = c->ell_val;
+  a.invD = static_cast<const double*>(C.invD[CHEBMG_F64]);
+  a.b = b;
+  a.x = x;
+  a.u = c->cvec[0];
+  a.part = c->cpart;
+  a.tot = c->cpart + 3 * std::max(1, c->coarse_grid);
+  a.ctl = c->cctl;
+  a.rtol = c->o.coarse_rtol;
+  a.maxit = c->o.coarse_maxit;
+  a.phantom_blocks = 0;
+  return a;
+}
+
 // FP64 coarse solve on the last level: FD dense inverse, SEM Jacobi-PCG.
 int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {
   Level& C = c->L.back();
@@ -285,23 +313,7 @@ int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {
     // whole Jacobi-PCG in one cooperative launch; no host round trip.  Status and
     // iterations land in cctl[2..3], errors also in the sticky cctl[4].
     CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 4, c->s));
-    CoarseCG a;
-    a.n = n;
-    a.nslot = c->nslot;
-    a.col = c->ell_col;
-    a.val = c->ell_val;
-    a.invD = S;
-    a.b = b;
-    a.x = x;
-    a.r = r;
-    a.z = z;
-    a.p = p;
-    a.q = q;
-    a.part_pq = c->cpart_pq;
-    a.part_rr = c->cpart_rr;
-    a.ctl = c->cctl;
-    a.rtol = c->o.coarse_rtol;
-    a.maxit = c->o.coarse_maxit;
+    CoarseCG a = coarse_args(c, b, x);
     a.phantom_blocks = 0;
     cudaError_t e = cudaSuccess;
     if (coarse_pcg_launch(a, c->coarse_grid, c->s, &e)) return CHEBMG_OK;
@@ -467,12 +479,17 @@ void alloc_vectors(chebmg_ctx* c, Level& L, bool with32) {
 }
 
 void common_alloc(chebmg_ctx* c) {
+  c->dstat = dalloc<unsigned>(c, 4);
+  CK(cudaMemsetAsync(c->dstat, 0, sizeof(unsigned) * 4, c->s));
   c->partial = dalloc<double>(c, 2 * kRedBlocks);
   c->scal = dalloc<double>(c, S_NSLOTS);
   CK(cudaMemsetAsync(c->scal, 0, sizeof(double) * S_NSLOTS, c->s));
   void* h = nullptr;
   CK(cudaMallocHost(&h, sizeof(double) * S_NSLOTS));
   c->hscal = static_cast<double*>(h);
+  CK(cudaMallocHost(&h, sizeof(unsigned) * 4));
+  c->hdstat = static_cast<unsigned*>(h);
+  std::memset(c->hdstat, 0, sizeof(unsigned) * 4);
   c->cpartial = dalloc<double>(c, 2 * kRedBlocks);
   c->cscal = dalloc<double>(c, S_NSLOTS);
   CK(cudaMemsetAsync(c->cscal, 0, sizeof(double) * S_NSLOTS, c->s));
@@ -501,8 +518,8 @@ void common_alloc(chebmg_ctx* c) {
     CK(cudaMallocHost(&h, sizeof(unsigned) * 5));
     c->hcctl = static_cast<unsigned*>(h);
     std::memset(c->hcctl, 0, sizeof(unsigned) * 5);
-    c->cpart_pq = dalloc<double>(c, std::max(1, c->coarse_grid));
-    c->cpart_rr = dalloc<double>(c, 2 * std::max(1, c->coarse_grid));
+    c->cpart = dalloc<double>(c, 3 * std::max(1, c->coarse_grid) + 3);
+    c->cvec[0] = dalloc<double>(c, nc);
   }
 }
 
@@ -514,8 +531,51 @@ T* upload(chebmg_ctx* c, const std::vector<double>& h) {
   return d;
 }
 
+// Picks the elements-per-block of the order-7 operator by timing each candidate on the
+// level's own data (3 launches each, best of them) -- a small autotuner run once at setup.
+template <typename T>
+void autotune_ax8(chebmg_ctx* c, int j) {
+  Level& L = c->L[j];
+  const int dt = dt_of<T>();
+  if (L.type != TYPE_SEM || L.Q != 8 || !L.G[dt]) return;
+  T* x = vec<T>(L, VB);
+  T* y = vec<T>(L, VY);
+  CK(cudaMemsetAsync(x, 0, sizeof(T) * L.n, c->s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_eb = 2;
+  for (int eb : {1, 2, 4}) {
+    L.eb[dt] = eb;
+    apply_into<T>(c, j, x, y);   // warm-up / first-launch configuration
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CK(cudaEventRecord(e0, c->s));
+      apply_into<T>(c, j, x, y);
+      CK(cudaEventRecord(e1, c->s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      t_min = std::min(t_min, ms);
+    }
+    if (t_min < best) {
+      best = t_min;
+      best_eb = eb;
+    }
+  }
+  L.eb[dt] = best_eb;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaMemsetAsync(y, 0, sizeof(T) * L.n, c->s));
+}
+
 void finish_setup(chebmg_ctx* c) {
   const int nl = (int)c->L.size();
+  for (int j = 0; j < nl; ++j) {
+    autotune_ax8<double>(c, j);
+    if (c->fp32) autotune_ax8<float>(c, j);
+  }
   c->pre = c->o.sided == CHEBMG_ONE_SIDED ? 2 * c->o.order : c->o.order;
   c->post = c->o.sided == CHEBMG_ONE_SIDED ? 0 : c->o.order;
   for (int j = 0; j + 1 < nl; ++j) {
@@ -572,6 +632,7 @@ void destroy_ctx(chebmg_ctx* c) {
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hcscal) cudaFreeHost(c->hcscal);
   if (c->hcctl) cudaFreeHost(c->hcctl);
+  if (c->hdstat) cudaFreeHost(c->hdstat);
   delete c;
 }
 
@@ -719,6 +780,7 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
         L.G[CHEBMG_F64] = upload<double>(c, h.G);
         L.invD[CHEBMG_F64] = upload<double>(c, invd);
         L.D[CHEBMG_F64] = upload<double>(c, h.Dm);
+        if (h.N == 7) CK(sem_ax8_set_D(h.Dm.data()));
         if (smoothed32) {
           L.G[CHEBMG_F32] = upload<float>(c, h.G);
           L.invD[CHEBMG_F32] = upload<float>(c, invd);
@@ -770,6 +832,14 @@ int chebmg_level_size(const chebmg_ctx* c, int level, int64_t* n) {
 int chebmg_lambda_max(const chebmg_ctx* c, int level, double* out) {
   if (!c || !out || level < 0 || level + 1 >= (int)c->L.size()) return CHEBMG_EINVAL;
   *out = c->L[level].lmax;
+  return CHEBMG_OK;
+}
+
+int chebmg_tile_choice(const chebmg_ctx* c, int level, int dtype, int* elements_per_block) {
+  if (!c || !elements_per_block || level < 0 || level >= (int)c->L.size() || (dtype != 0 && dtype != 1))
+    return CHEBMG_EINVAL;
+  const Level& L = c->L[level];
+  *elements_per_block = (L.type == TYPE_SEM && L.Q == 8) ? L.eb[dtype] : 0;
   return CHEBMG_OK;
 }
 
@@ -975,23 +1045,7 @@ int chebmg_selftest_coarse_timeout(chebmg_ctx* c, int* status) {
     Level& C = c->L.back();
     const int64_t n = C.n;
     CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 5, c->s));
-    CoarseCG a;
-    a.n = n;
-    a.nslot = c->nslot;
-    a.col = c->ell_col;
-    a.val = c->ell_val;
-    a.invD = static_cast<const double*>(C.invD[CHEBMG_F64]);
-    a.b = c->cb;
-    a.x = c->cx;
-    a.r = c->cr;
-    a.z = c->cz;
-    a.p = c->cp;
-    a.q = c->cq;
-    a.part_pq = c->cpart_pq;
-    a.part_rr = c->cpart_rr;
-    a.ctl = c->cctl;
-    a.rtol = c->o.coarse_rtol;
-    a.maxit = c->o.coarse_maxit;
+    CoarseCG a = coarse_args(c, c->cb, c->cx);
     a.phantom_blocks = 1;    // one arrival that never comes: every barrier wait runs out
     cudaError_t e = cudaSuccess;
     if (!coarse_pcg_launch(a, c->coarse_grid, c->s, &e)) throw Error(CHEBMG_ECUDA, cudaGetErrorString(e));

@@ -46,6 +46,14 @@ template <typename T>
 void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc,
                  const T* J, const T* zc, T* zf, int accumulate, cudaStream_t s);
 
+// Order-7 element operator (line passes, even-odd D, TMA-staged geometric factors).
+// sem_ax8_set_D uploads the even-odd blocks of the 8x8 GLL derivative matrix (row-major).
+cudaError_t sem_ax8_set_D(const double* D);
+// eb = elements per thread block (1, 2 or 4), chosen per level by a setup-time autotuner.
+template <typename T>
+void sem_ax8(int64_t E, const uint32_t* gid, const T* G, const T* u, T* y, unsigned* err, int eb,
+             cudaStream_t s);
+
 // ---- FD kernels ----
 template <typename T>
 void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s);
@@ -111,17 +119,16 @@ struct CoarseCG {
   const double* invD;
   const double* b;
   double* x;
-  double* r;
-  double* z;
-  double* p;
-  double* q;
-  double* part_pq;       // [gridDim]
-  double* part_rr;       // [2 * gridDim]
+  double* u;             // u = M r, exchanged between blocks once per iteration
+  double* part;          // [3 * gridDim] block partials of (r, u), (A u, u), (r, r)
+  double* tot;           // [3] their totals, published by the last block to reach the barrier
   unsigned* ctl;         // [5], ctl[0..1] zero at launch
   double rtol;
   int maxit;
   unsigned phantom_blocks;   // self-test only: barrier also waits for this many blocks that never come
 };
+// Rows per thread the persistent coarse kernel can keep in registers.
+constexpr int kCoarseMaxRowsPerThread = 8;
 // Returns false (nothing launched) if a cooperative launch is not possible.
 bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err);
 int coarse_pcg_grid(int64_t n);

@@ -700,119 +700,205 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned& gen, unsig
   return s_ok != 0;
 }
 
-// Sum of the per-block partials (two arrays of gridDim entries, stride `st`), same order everywhere.
-__device__ __forceinline__ void sum_partials(const double* part, int stride, int off0, int off1, double& a, double& b) {
-  double ta = 0.0, tb = 0.0;
-  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
-    ta += ((volatile const double*)part)[q * stride + off0];
-    if (off1 >= 0) tb += ((volatile const double*)part)[q * stride + off1];
+// Block sum of three values: one warp adds the per-thread values through shared memory
+// (few FP64 additions: GB300 issues about two FP64 operations per clock per SM).  Result in
+// all threads; fixed order.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double sh[3][kCoarseThreads];
+  __shared__ double res[3];
+  __syncthreads();
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  sh[2][threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kCoarseThreads / 32; ++q) {
+      t0 += sh[0][threadIdx.x + 32 * q];
+      t1 += sh[1][threadIdx.x + 32 * q];
+      t2 += sh[2][threadIdx.x + 32 * q];
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (threadIdx.x == 0) {
+      res[0] = t0;
+      res[1] = t1;
+      res[2] = t2;
+    }
   }
-  block_allsum2(ta, tb);
-  a = ta;
-  b = tb;
+  __syncthreads();
+  a = res[0];
+  b = res[1];
+  c = res[2];
 }
 
+// Grid barrier that also reduces: the last block to arrive sums the 3 * gridDim partials in a
+// fixed order, publishes the totals and releases the others, who then read three numbers.
+// Waits are bounded as in grid_barrier.
+__device__ __forceinline__ bool barrier_reduce3(unsigned* ctl, unsigned& gen, unsigned expected,
+                                                const double* part, double* tot, double& A, double& B,
+                                                double& C) {
+  __shared__ int s_last, s_ok;
+  __syncthreads();
+  const unsigned target = gen + 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctl[0], 1u) == expected - 1;
+    s_ok = 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+      a += ((volatile const double*)part)[3 * q];
+      b += ((volatile const double*)part)[3 * q + 1];
+      c += ((volatile const double*)part)[3 * q + 2];
+    }
+    block_sum3(a, b, c);
+    if (threadIdx.x == 0) {
+      tot[0] = a;
+      tot[1] = b;
+      tot[2] = c;
+      __threadfence();
+      atomicExch(&ctl[0], 0u);
+      __threadfence();
+      atomicExch(&ctl[1], target);
+    }
+  } else if (threadIdx.x == 0) {
+    unsigned spins = 0;
+    while (*(volatile unsigned*)&ctl[1] != target) {
+      if (++spins > kSpinLimit) {
+        atomicMax((int*)&ctl[4], (int)CS_TIMEOUT);
+        s_ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  gen += 1;
+  A = ((volatile const double*)tot)[0];
+  B = ((volatile const double*)tot)[1];
+  C = ((volatile const double*)tot)[2];
+  return s_ok != 0;
+}
+
+// Persistent Jacobi-preconditioned CG in the Chronopoulos-Gear form: one reduction per
+// iteration (gamma = (r, u), delta = (A u, u), rho = (r, r) with u = M r) and two grid
+// barriers -- after u is published for the neighbours' product, and after the product and
+// the partial sums (that one also forms the totals).  Each thread owns up to RPT rows whose
+// x, r, s, p, w stay in registers for the whole solve; the ELL matrix is read through the
+// read-only cache path.
+template <int NS, int RPT>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
   const int64_t n = a.n;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  unsigned gen = 0;
-  double rr = 0.0, rz = 0.0;
-  for (int64_t g = t0; g < n; g += stride) {
-    const double S = a.invD[g];
-    const double rv = S != 0.0 ? a.b[g] : 0.0;
-    const double zv = S * rv;
-    a.x[g] = 0.0;
-    a.r[g] = rv;
-    a.z[g] = zv;
-    a.p[g] = zv;
-    rr += rv * rv;
-    rz += rv * zv;
-  }
-  block_allsum2(rr, rz);
-  if (threadIdx.x == 0) {
-    a.part_rr[2 * blockIdx.x] = rr;
-    a.part_rr[2 * blockIdx.x + 1] = rz;
-  }
-  if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
-  double bb, rz_old;
-  sum_partials(a.part_rr, 2, 0, 1, bb, rz_old);
+  const unsigned expected = gridDim.x + a.phantom_blocks;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-  if (!(bb > 0.0)) {
-    if (lead) {
-      a.ctl[2] = bb == 0.0 ? CS_OK : CS_BREAKDOWN;
-      a.ctl[3] = 0;
-      if (bb != 0.0) atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
-    }
-    return;
+  const int ns = NS > 0 ? NS : a.nslot;
+  unsigned gen = 0;
+  double x[RPT], r[RPT], s[RPT], p[RPT], w[RPT], S[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t g = t0 + q * stride;
+    const bool live = g < n;
+    S[q] = live ? __ldg(&a.invD[g]) : 0.0;
+    r[q] = (live && S[q] != 0.0) ? a.b[g] : 0.0;
+    x[q] = s[q] = p[q] = w[q] = 0.0;
+    if (live) a.u[g] = S[q] * r[q];
   }
-  const double tol2 = a.rtol * a.rtol * bb;
-  for (int it = 1; it <= a.maxit; ++it) {
-    double pq = 0.0, dummy = 0.0;
-    for (int64_t g = t0; g < n; g += stride) {
-      double s = 0.0;
-      // p of other blocks' rows was written before the last barrier: read it from L2
-      for (int k = 0; k < a.nslot; ++k) s += a.val[k * n + g] * __ldcg(&a.p[a.col[k * n + g]]);
-      a.q[g] = s;
-      pq += a.p[g] * s;
-    }
-    block_allsum2(pq, dummy);
-    if (threadIdx.x == 0) a.part_pq[blockIdx.x] = pq;
-    if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
-    double pq_tot;
-    sum_partials(a.part_pq, 1, 0, -1, pq_tot, dummy);
-    if (!(pq_tot > 0.0)) {
-      if (lead) {
-        a.ctl[2] = CS_BREAKDOWN;
-        a.ctl[3] = it;
-        atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
+  double gam_old = 0.0, alpha_old = 0.0, bb = 0.0, tol2 = 0.0;
+  for (int it = 0;; ++it) {
+    if (!grid_barrier(a.ctl, gen, expected)) return;
+    // w = A u for the owned rows, and this block's partial sums
+    double gam = 0.0, del = 0.0, rho = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int64_t g = t0 + q * stride;
+      if (g >= n) continue;
+      double acc = 0.0;
+      if (NS > 0) {
+#pragma unroll
+        for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
+          acc += __ldg(&a.val[k * n + g]) * __ldcg(&a.u[__ldg(&a.col[k * n + g])]);
+      } else {
+#pragma unroll 9
+        for (int k = 0; k < ns; ++k) acc += __ldg(&a.val[k * n + g]) * __ldcg(&a.u[__ldg(&a.col[k * n + g])]);
       }
-      return;
+      w[q] = acc;
+      const double uq = S[q] * r[q];
+      gam += r[q] * uq;
+      del += acc * uq;
+      rho += r[q] * r[q];
     }
-    const double alpha = rz_old / pq_tot;
-    rr = 0.0;
-    rz = 0.0;
-    for (int64_t g = t0; g < n; g += stride) {
-      a.x[g] += alpha * a.p[g];
-      const double rn = a.r[g] - alpha * a.q[g];
-      const double zn = a.invD[g] * rn;
-      a.r[g] = rn;
-      a.z[g] = zn;
-      rr += rn * rn;
-      rz += rn * zn;
-    }
-    block_allsum2(rr, rz);
+    block_sum3(gam, del, rho);
     if (threadIdx.x == 0) {
-      a.part_rr[2 * blockIdx.x] = rr;
-      a.part_rr[2 * blockIdx.x + 1] = rz;
+      a.part[3 * blockIdx.x] = gam;
+      a.part[3 * blockIdx.x + 1] = del;
+      a.part[3 * blockIdx.x + 2] = rho;
     }
-    if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
-    double rr_tot, rz_new;
-    sum_partials(a.part_rr, 2, 0, 1, rr_tot, rz_new);
-    if (!(rr_tot == rr_tot)) {
+    double G, Dl, Rh;
+    if (!barrier_reduce3(a.ctl, gen, expected, a.part, a.tot, G, Dl, Rh)) return;
+    int status = 0;
+    if (it == 0) {
+      bb = Rh;
+      tol2 = a.rtol * a.rtol * bb;
+      if (!(bb > 0.0)) status = bb == 0.0 ? CS_OK : CS_BREAKDOWN;
+    }
+    if (!status && !(Rh == Rh)) status = CS_BREAKDOWN;
+    if (!status && Rh <= tol2) status = CS_OK;
+    if (!status && it >= a.maxit) status = CS_NOTCONV;
+    const double beta = it == 0 ? 0.0 : G / gam_old;
+    const double den = it == 0 ? Dl : Dl - beta * G / alpha_old;
+    if (!status && (!(den > 0.0) || !(G > 0.0))) status = CS_BREAKDOWN;
+    if (status) {
+      // x holds the iterate after `it` updates
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int64_t g = t0 + q * stride;
+        if (g < n) a.x[g] = x[q];
+      }
       if (lead) {
-        a.ctl[2] = CS_BREAKDOWN;
-        a.ctl[3] = it;
-        atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
+        a.ctl[2] = (unsigned)status;
+        a.ctl[3] = (unsigned)it;
+        if (status == CS_BREAKDOWN) atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
       }
       return;
     }
-    if (rr_tot <= tol2) {
-      if (lead) {
-        a.ctl[2] = CS_OK;
-        a.ctl[3] = it;
-      }
-      return;
+    const double alpha = G / den;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int64_t g = t0 + q * stride;
+      if (g >= n) continue;
+      p[q] = fma(beta, p[q], S[q] * r[q]);
+      s[q] = fma(beta, s[q], w[q]);
+      x[q] = fma(alpha, p[q], x[q]);
+      r[q] = fma(-alpha, s[q], r[q]);
+      a.u[g] = S[q] * r[q];
     }
-    const double beta = rz_new / rz_old;
-    rz_old = rz_new;
-    for (int64_t g = t0; g < n; g += stride) a.p[g] = a.z[g] + beta * a.p[g];
-    if (!grid_barrier(a.ctl, gen, gridDim.x + a.phantom_blocks)) return;
+    gam_old = G;
+    alpha_old = alpha;
   }
-  if (lead) {
-    a.ctl[2] = CS_NOTCONV;
-    a.ctl[3] = a.maxit;
+}
+
+template <int NS>
+static const void* coarse_kernel(int rpt) {
+  switch (rpt) {
+    case 1: return (const void*)k_coarse_pcg<NS, 1>;
+    case 2: return (const void*)k_coarse_pcg<NS, 2>;
+    case 4: return (const void*)k_coarse_pcg<NS, 4>;
+    default: return (const void*)k_coarse_pcg<NS, 8>;
   }
+}
+
+static int coarse_rpt(int64_t n, int grid) {
+  const int64_t threads = (int64_t)grid * kCoarseThreads;
+  const int64_t need = (n + threads - 1) / threads;
+  return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 0;
 }
 
 int coarse_pcg_grid(int64_t n) {
@@ -821,18 +907,24 @@ int coarse_pcg_grid(int64_t n) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_pcg, kCoarseThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_pcg<0, 8>, kCoarseThreads, 0);
     cached = sms * (per_sm > 0 ? 1 : 0);
   }
   const int64_t need = (n + kCoarseThreads - 1) / kCoarseThreads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(cached, need));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cached, need));
+  return coarse_rpt(n, grid) > 0 ? grid : 0;   // 0: too large to keep in registers
 }
 
 bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err) {
   CoarseCG arg = a;
   void* params[] = {&arg};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_coarse_pcg, dim3(grid), dim3(kCoarseThreads),
-                                              params, 0, s);
+  const int rpt = coarse_rpt(a.n, grid);
+  if (rpt == 0 || grid <= 0) {
+    if (err) *err = cudaErrorInvalidConfiguration;
+    return false;
+  }
+  const void* fn = a.nslot == 27 ? coarse_kernel<27>(rpt) : coarse_kernel<0>(rpt);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoarseThreads), params, 0, s);
   count();
   if (err) *err = e;
   return e == cudaSuccess;

@@ -1,0 +1,283 @@
+// Element operator for polynomial order N = 7 (8 GLL points per direction), the
+// order of the finest p-multigrid level.
+//
+// Same operator as k_sem_ax (Sec. 1, Eq. 1.3: y_e = sum_m Dhat_m^T sum_n G_mn Dhat_n u_e,
+// then direct-stiffness summation), organised for GB300:
+//
+// * Line passes.  64 threads per element; in each of the six 1-D contractions a thread owns
+//   one whole grid line (a column along t, a row along r, a line along s), loads its 8 values
+//   once and produces 8 outputs, so one shared-memory load feeds 8 FMAs.  The t-direction
+//   line stays in registers.
+// * Even-odd factorisation.  The GLL derivative matrix is centro-antisymmetric,
+//   D[7-i][7-l] = -D[i][l], so (D u)[i] = E_i.(u_l + u_{7-l}) + O_i.(u_l - u_{7-l}) and
+//   (D u)[7-i] = O_i.(...) - E_i.(...) with 4x4 blocks E, O: 48 instead of 64 operations per
+//   line, which matters for the FP64 form (GB300 issues few FP64 FMAs per clock).
+// * Geometric factors by TMA.  G is stored [E][6][512], so the EB elements of a block are
+//   one contiguous span; a single elected thread issues one cp.async.bulk into shared memory
+//   at kernel start, completion tracked by an mbarrier, and the block overlaps it with the
+//   gather and the first three contractions.  The wait is bounded: on timeout the block
+//   records an error flag and skips its stores instead of hanging.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace chebmg {
+
+namespace {
+
+// even-odd blocks: [0] E of D, [1] O of D, [2] E of D^T, [3] O of D^T, each [i][l], i,l < 4
+__constant__ float c_eo_f[4][4][4];
+__constant__ double c_eo_d[4][4][4];
+
+template <typename T, int EB_ = 2>
+struct Ax8 {
+  static constexpr int EB = EB_;                       // elements per block
+  static constexpr int R = sizeof(T) == 4 ? 12 : 10;   // padded row stride (16-B aligned rows)
+  static constexpr int P = sizeof(T) == 4 ? 104 : 88;  // padded plane stride (bank spread)
+  static constexpr int STAGE = 8 * P;
+  static constexpr int GELEM = 6 * 512;
+  static size_t smem_bytes() { return sizeof(T) * (size_t)EB * (GELEM + 3 * STAGE); }
+};
+
+template <typename T>
+__device__ __forceinline__ T eo(int w, int i, int l);
+template <>
+__device__ __forceinline__ float eo<float>(int w, int i, int l) { return c_eo_f[w][i][l]; }
+template <>
+__device__ __forceinline__ double eo<double>(int w, int i, int l) { return c_eo_d[w][i][l]; }
+
+// o = D u (W = 0) or o = D^T u (W = 1) along one line of 8 points.
+template <typename T, int W>
+__device__ __forceinline__ void line8(const T (&u)[8], T (&o)[8]) {
+  T ue[4], uo[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    ue[l] = u[l] + u[7 - l];
+    uo[l] = u[l] - u[7 - l];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    T se = eo<T>(2 * W, i, 0) * ue[0];
+    T so = eo<T>(2 * W + 1, i, 0) * uo[0];
+#pragma unroll
+    for (int l = 1; l < 4; ++l) {
+      se = fma(eo<T>(2 * W, i, l), ue[l], se);
+      so = fma(eo<T>(2 * W + 1, i, l), uo[l], so);
+    }
+    o[i] = se + so;
+    o[7 - i] = so - se;
+  }
+}
+
+__device__ __forceinline__ void ld_row(const float* p, float (&v)[8]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void st_row(float* p, const float (&v)[8]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void ld_row(const double* p, double (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 a = reinterpret_cast<const double2*>(p)[q];
+    v[2 * q] = a.x;
+    v[2 * q + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void st_row(double* p, const double (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+template <typename T, int EB_>
+__global__ void __launch_bounds__(64 * EB_)
+k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G, const T* __restrict__ u,
+          T* __restrict__ y, unsigned* __restrict__ err) {
+  using C = Ax8<T, EB_>;
+  constexpr int EB = C::EB, R = C::R, P = C::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* sG = reinterpret_cast<T*>(smem_raw);
+  T* sU = sG + EB * C::GELEM;
+  T* sR = sU + EB * C::STAGE;
+  T* sS = sR + EB * C::STAGE;
+
+  const int tid = threadIdx.x;
+  const int le = tid >> 6, t = tid & 63, a = t & 7, b = t >> 3;
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((E - e0) < EB ? (E - e0) : EB);
+  const bool valid = le < nvalid;
+  const int64_t e = e0 + le;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t bytes = (uint32_t)(nvalid * C::GELEM * sizeof(T));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sG)),
+        "l"(G + e0 * C::GELEM), "r"(bytes), "r"(smem_addr(&bar))
+        : "memory");
+  }
+
+  T* su = sU + le * C::STAGE;
+  T* sr = sR + le * C::STAGE;
+  T* ss = sS + le * C::STAGE;
+
+  // gather: thread (i = a, j = b) owns the column along t
+  uint32_t g[8];
+  T col[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    g[k] = valid ? gid[e * 512 + k * 64 + b * 8 + a] : kGidDirichlet;
+    col[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
+    su[k * P + b * R + a] = col[k];
+  }
+  T ut[8];
+  line8<T, 0>(col, ut);
+  __syncthreads();
+  {
+    T v[8], o[8];
+    // r: thread (j = a, k = b) owns the row along i
+    ld_row(su + b * P + a * R, v);
+    line8<T, 0>(v, o);
+    st_row(sr + b * P + a * R, o);
+    // s: thread (i = a, k = b) owns the line along j
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = su[b * P + j * R + a];
+    line8<T, 0>(v, o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ss[b * P + j * R + a] = o[j];
+  }
+  // geometric factors must have landed
+  bool ok = false;
+  for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(&bar, 0)) {
+      ok = true;
+      break;
+    }
+  // every thread takes the same branch: the block agrees on the outcome
+  if (!__syncthreads_and(ok ? 1 : 0)) {
+    if (tid == 0) atomicExch(err, 1u);
+    for (uint32_t it = 0; it < kWaitLimit; ++it)   // let the copy in flight finish before leaving
+      if (mbar_try_wait(&bar, 0)) break;
+    return;
+  }
+  T wt[8];
+  const T* gG = sG + le * C::GELEM;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int p = k * 64 + b * 8 + a;
+    const int q = k * P + b * R + a;
+    const T ur = sr[q], us = ss[q], utk = ut[k];
+    const T g00 = gG[p], g01 = gG[512 + p], g02 = gG[1024 + p];
+    const T g11 = gG[1536 + p], g12 = gG[2048 + p], g22 = gG[2560 + p];
+    sr[q] = g00 * ur + g01 * us + g02 * utk;
+    ss[q] = g01 * ur + g11 * us + g12 * utk;
+    wt[k] = g02 * ur + g12 * us + g22 * utk;
+  }
+  T yt[8];
+  line8<T, 1>(wt, yt);
+  __syncthreads();
+  {
+    T v[8], o[8];
+    ld_row(sr + b * P + a * R, v);          // transposed r, thread (j = a, k = b)
+    line8<T, 1>(v, o);
+    st_row(su + b * P + a * R, o);
+  }
+  __syncthreads();
+  {
+    T v[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = ss[b * P + j * R + a];   // transposed s, thread (i = a, k = b)
+    line8<T, 1>(v, o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) su[b * P + j * R + a] += o[j];
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const T v = su[k * P + b * R + a] + yt[k];
+      if (!(g[k] & kGidDirichlet)) atomicAdd(&y[g[k] & kGidMask], v);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t sem_ax8_set_D(const double* D) {
+  // symmetrised even-odd blocks of D and D^T (D[7-i][7-l] = -D[i][l] exactly)
+  double S[8][8];
+  for (int i = 0; i < 8; ++i)
+    for (int l = 0; l < 8; ++l) S[i][l] = 0.5 * (D[i * 8 + l] - D[(7 - i) * 8 + (7 - l)]);
+  double h[4][4][4];
+  float f[4][4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int l = 0; l < 4; ++l) {
+      h[0][i][l] = 0.5 * (S[i][l] + S[i][7 - l]);
+      h[1][i][l] = 0.5 * (S[i][l] - S[i][7 - l]);
+      h[2][i][l] = 0.5 * (S[l][i] + S[7 - l][i]);
+      h[3][i][l] = 0.5 * (S[l][i] - S[7 - l][i]);
+    }
+  for (int w = 0; w < 4; ++w)
+    for (int i = 0; i < 4; ++i)
+      for (int l = 0; l < 4; ++l) f[w][i][l] = (float)h[w][i][l];
+  cudaError_t e = cudaMemcpyToSymbol(c_eo_d, h, sizeof(h));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_eo_f, f, sizeof(f));
+}
+
+template <typename T, int EB>
+static void launch_ax8(int64_t E, const uint32_t* gid, const T* G, const T* u, T* y, unsigned* err,
+                       cudaStream_t s) {
+  using C = Ax8<T, EB>;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_sem_ax8<T, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes());
+    configured = true;
+  }
+  const unsigned blocks = (unsigned)((E + EB - 1) / EB);
+  k_sem_ax8<T, EB><<<blocks, 64 * EB, C::smem_bytes(), s>>>(E, gid, G, u, y, err);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+template <typename T>
+void sem_ax8(int64_t E, const uint32_t* gid, const T* G, const T* u, T* y, unsigned* err, int eb, cudaStream_t s) {
+  switch (eb) {
+    case 1: launch_ax8<T, 1>(E, gid, G, u, y, err, s); break;
+    case 4: launch_ax8<T, 4>(E, gid, G, u, y, err, s); break;
+    default: launch_ax8<T, 2>(E, gid, G, u, y, err, s); break;
+  }
+}
+
+template void sem_ax8<float>(int64_t, const uint32_t*, const float*, const float*, float*, unsigned*, int,
+                             cudaStream_t);
+template void sem_ax8<double>(int64_t, const uint32_t*, const double*, const double*, double*, unsigned*, int,
+                              cudaStream_t);
+
+}  // namespace chebmg
