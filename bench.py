@@ -146,12 +146,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ne", type=int, default=NE,
                     help="elements per direction (profiling runs only; the benchmark uses 32)")
+    ap.add_argument("--profile-smoother", choices=["mixed", "fp64"], default=None,
+                    help="set up, then run one order-9 fine-level smoother application inside the NVTX "
+                         "range 'smooth' and exit")
+    ap.add_argument("--tile", type=int, default=None,
+                    help="profiling runs only: force this order-7 kernel variant on the fine level")
     ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
                     help="set up, warm up, run one solve inside the NVTX range 'solve' and exit "
                          "(for ncu --nvtx-include solve/)")
     args = ap.parse_args()
 
-    if args.profile_solve:
+    if args.profile_solve or args.profile_smoother:
         NE = args.ne
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,6 +219,26 @@ def main():
         code, it, rel, _ = cm.chebmg_pcg_solve(s.ctx, b, u, RTOL, 500)
         assert code == cm.CHEBMG_OK and rel <= RTOL, (code, it, rel)
         return it
+
+    if args.profile_smoother:
+        s = s32 if args.profile_smoother == "mixed" else s64
+        f32 = args.profile_smoother == "mixed"
+        dt = cm.CHEBMG_F32 if f32 else cm.CHEBMG_F64
+        xb = torch.zeros(n, device="cuda", dtype=torch.float32 if f32 else torch.float64)
+        bb = xb.clone().uniform_(-1, 1)
+        if args.tile is not None:
+            cm.chebmg_set_tile_choice(s.ctx, 0, dt, args.tile)
+        cm.chebmg_smooth(s.ctx, 0, dt, bb, xb, 9, True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("smooth")
+        cm.chebmg_smooth(s.ctx, 0, dt, bb, xb, 9, True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_smoother": args.profile_smoother,
+                          "elements_per_block": cm.chebmg_tile_choice(s.ctx, 0, dt)}))
+        s32.close()
+        s64.close()
+        return 0
 
     if args.profile_solve:
         s = s32 if args.profile_solve == "mixed" else s64

@@ -108,9 +108,14 @@ int chebmg_level_size(const chebmg_ctx* ctx, int level, int64_t* n);
 int chebmg_lambda_max(const chebmg_ctx* ctx, int level, double* out);
 /* Kernel launches issued by this library in this process (ctx unused; for accounting). */
 int chebmg_launch_count(const chebmg_ctx* ctx, int64_t* count);
-/* Elements per thread block chosen by the setup-time autotuner for the order-7 element
- * operator on `level` in `dtype` (0 if the level does not use that kernel). */
+/* Variant chosen by the setup-time autotuner for the order-7 element operator on `level`
+ * in `dtype`: 1, 2 or 4 elements per thread block, or 12 / 14 for the persistent pipelined
+ * kernel with 2 / 4 elements per block; +100 when global ids are computed from the box
+ * lattice instead of read from the element-to-global map (0 if the level does not use
+ * that kernel). */
 int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* elements_per_block);
+/* Overrides that choice (same codes); EINVAL for other levels or codes. */
+int chebmg_set_tile_choice(chebmg_ctx* ctx, int level, int dtype, int variant);
 
 /* ---- per-level operators (device vectors, dtype as above) ---------------- */
 

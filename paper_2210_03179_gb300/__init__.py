@@ -79,6 +79,7 @@ _SIGNATURES = {
     "chebmg_lambda_max": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "chebmg_launch_count": (c_int, [c_void_p, POINTER(c_int64)]),
     "chebmg_tile_choice": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
+    "chebmg_set_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int]),
     "chebmg_apply_A": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "chebmg_inv_diagonal": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "chebmg_smooth": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_int]),
@@ -209,6 +210,10 @@ def chebmg_tile_choice(ctx, level, dtype) -> int:
     v = c_int()
     _check(lib().chebmg_tile_choice(ctx, int(level), int(dtype), byref(v)), "chebmg_tile_choice")
     return v.value
+
+
+def chebmg_set_tile_choice(ctx, level, dtype, variant):
+    _check(lib().chebmg_set_tile_choice(ctx, int(level), int(dtype), int(variant)), "chebmg_set_tile_choice")
 
 
 def chebmg_apply_A(ctx, level, dtype, x, y):

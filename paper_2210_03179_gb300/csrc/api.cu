@@ -91,7 +91,8 @@ struct Level {
   void* D[2] = {nullptr, nullptr};
   void* Jn[2] = {nullptr, nullptr};   // interpolation from level+1 to this level, [Qf][Qc]
   void* v[2][NV] = {{nullptr}};
-  int eb[2] = {2, 2};   // elements per block of the order-7 operator, per dtype (autotuned)
+  int eb[2] = {2, 2};   // variant of the order-7 operator, per dtype (autotuned)
+  Lattice lat = {0, 0, 0, 0, 0, 0};
 };
 
 }  // namespace chebmg
@@ -195,7 +196,7 @@ void apply_into(chebmg_ctx* c, int j, const T* x, T* y) {
   const int dt = dt_of<T>();
   if (L.type == TYPE_SEM) {
     if (L.Q == 8)
-      sem_ax8<T>(L.E, L.gid, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s);
+      sem_ax8<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s);
     else
       sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s);
   } else {
@@ -546,7 +547,8 @@ void autotune_ax8(chebmg_ctx* c, int j) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_eb = 2;
-  for (int eb : {1, 2, 4}) {
+  for (int eb : {1, 2, 4, 12, 14, 101, 102, 104, 112, 114}) {
+    if (!sem_ax8_variant_fits<T>(eb)) continue;
     L.eb[dt] = eb;
     apply_into<T>(c, j, x, y);   // warm-up / first-launch configuration
     float t_min = 1e30f;
@@ -768,6 +770,7 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
         L.type = TYPE_SEM;
         L.N = h.N;
         L.Q = h.NQ;
+        L.lat = {nex, ney, nez, (int)(nex * h.N + 1), (int)(ney * h.N + 1), (int)(nez * h.N + 1)};
         L.NP = h.NP;
         L.E = h.E;
         L.n = h.n;
@@ -840,6 +843,20 @@ int chebmg_tile_choice(const chebmg_ctx* c, int level, int dtype, int* elements_
     return CHEBMG_EINVAL;
   const Level& L = c->L[level];
   *elements_per_block = (L.type == TYPE_SEM && L.Q == 8) ? L.eb[dtype] : 0;
+  return CHEBMG_OK;
+}
+
+int chebmg_set_tile_choice(chebmg_ctx* c, int level, int dtype, int variant) {
+  if (!c || level < 0 || level >= (int)c->L.size() || (dtype != 0 && dtype != 1)) return CHEBMG_EINVAL;
+  Level& L = c->L[level];
+  if (L.type != TYPE_SEM || L.Q != 8) return CHEBMG_EINVAL;
+  const int base = variant % 100;
+  if ((variant != base && variant != base + 100) ||
+      (base != 1 && base != 2 && base != 4 && base != 12 && base != 14))
+    return CHEBMG_EINVAL;
+  const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(variant) : sem_ax8_variant_fits<float>(variant);
+  if (!fits) return CHEBMG_EINVAL;
+  L.eb[dtype] = variant;
   return CHEBMG_OK;
 }
 

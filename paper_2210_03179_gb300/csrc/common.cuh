@@ -49,10 +49,20 @@ void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t
 // Order-7 element operator (line passes, even-odd D, TMA-staged geometric factors).
 // sem_ax8_set_D uploads the even-odd blocks of the 8x8 GLL derivative matrix (row-major).
 cudaError_t sem_ax8_set_D(const double* D);
-// eb = elements per thread block (1, 2 or 4), chosen per level by a setup-time autotuner.
+// Box lattice of an order-7 level (element counts and global node counts per direction).
+struct Lattice {
+  int nex, ney, nez;
+  int NX, NY, NZ;
+};
+// variant chosen per level by a setup-time autotuner: 1, 2 or 4 elements per thread block,
+// or 12 / 14 for the persistent software-pipelined kernel with 2 / 4 elements; +100 computes
+// global ids from the box lattice instead of reading the element-to-global map.
 template <typename T>
-void sem_ax8(int64_t E, const uint32_t* gid, const T* G, const T* u, T* y, unsigned* err, int eb,
-             cudaStream_t s);
+void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+             unsigned* err, int variant, cudaStream_t s);
+// Whether variant `eb` fits the device's per-block shared-memory limit.
+template <typename T>
+bool sem_ax8_variant_fits(int eb);
 
 // ---- FD kernels ----
 template <typename T>

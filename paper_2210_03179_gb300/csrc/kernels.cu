@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "common.cuh"
 
@@ -368,17 +369,57 @@ __global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__
   }
 }
 
+// Vector type of 16 bytes for T (float4 / double2) and its lane count.
 template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int L = 4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int L = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T c1, T c2) {
+  const T dv = d;
+  const T rv = r - y;
+  x += beta * dv;
+  r = rv;
+  d = c1 * dv + c2 * s * rv;
+  y = T(0);
+}
+
+// x += beta d; r -= y; d = c1 d + c2 S r; y = 0 -- 16-byte vector accesses over the aligned
+// body (every pointer comes from a 256-byte aligned allocation), scalar tail.
+template <typename T, bool VEC>
 __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
                              T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const T dv = d[g];
-    const T rv = r[g] - y[g];
-    x[g] += beta * dv;
-    r[g] = rv;
-    d[g] = c1 * dv + c2 * invD[g] * rv;
-    y[g] = T(0);
+  using VT = typename V16<T>::type;
+  constexpr int L = V16<T>::L;
+  const int64_t nv = VEC ? n / L : 0;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = tid; q < nv; q += stride) {
+    VT xv = reinterpret_cast<VT*>(x)[q], rv = reinterpret_cast<VT*>(r)[q], dv = reinterpret_cast<VT*>(d)[q];
+    VT yv = reinterpret_cast<VT*>(y)[q];
+    const VT sv = reinterpret_cast<const VT*>(invD)[q];
+    T* xs = reinterpret_cast<T*>(&xv);
+    T* rs = reinterpret_cast<T*>(&rv);
+    T* ds = reinterpret_cast<T*>(&dv);
+    T* ys = reinterpret_cast<T*>(&yv);
+    const T* ss = reinterpret_cast<const T*>(&sv);
+#pragma unroll
+    for (int l = 0; l < L; ++l) cheb4_one(xs[l], rs[l], ds[l], ys[l], ss[l], beta, c1, c2);
+    reinterpret_cast<VT*>(x)[q] = xv;
+    reinterpret_cast<VT*>(r)[q] = rv;
+    reinterpret_cast<VT*>(d)[q] = dv;
+    reinterpret_cast<VT*>(y)[q] = yv;
   }
+  for (int64_t g = nv * L + tid; g < n; g += stride) cheb4_one(x[g], r[g], d[g], y[g], invD[g], beta, c1, c2);
 }
 
 template <typename T>
@@ -449,7 +490,13 @@ void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, do
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
                 cudaStream_t s) {
-  k_cheb4_step<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2);
+  const uintptr_t align = (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
+  if (align % 16 == 0)
+    k_cheb4_step<T, true><<<grid_for(n / V16<T>::L + 1, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD,
+                                                                                          (T)beta, (T)c1, (T)c2);
+  else
+    k_cheb4_step<T, false><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)beta, (T)c1,
+                                                                           (T)c2);
   count();
 }
 template <typename T>

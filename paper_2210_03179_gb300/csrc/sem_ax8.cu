@@ -108,10 +108,45 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 constexpr uint32_t kWaitLimit = 1u << 22;
 
-template <typename T, int EB_>
+// Global ids (with the Dirichlet flag) of the column (i = a, j = b, k = 0..7) of element e:
+// read from the element-to-global map, or (IMPLICIT) computed from the box lattice, which the
+// library's meshes always have -- connectivity of a box, arbitrary vertex positions.  32-bit
+// arithmetic (n < 2^30), one division pair per element.
+template <bool IMPLICIT>
+__device__ __forceinline__ void column_ids(const uint32_t* __restrict__ gid, const Lattice& L, int64_t e,
+                                           bool valid, int a, int b, uint32_t (&g)[8]) {
+  if (!valid) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] = kGidDirichlet;
+    return;
+  }
+  if constexpr (IMPLICIT) {
+    const uint32_t ee = (uint32_t)e;
+    const uint32_t exy = (uint32_t)L.nex * (uint32_t)L.ney;
+    const uint32_t ez = ee / exy;
+    const uint32_t rem = ee - ez * exy;
+    const uint32_t ey = rem / (uint32_t)L.nex;
+    const uint32_t ex = rem - ey * (uint32_t)L.nex;
+    const uint32_t gx = ex * 7 + a, gy = ey * 7 + b;
+    const bool side = gx == 0 || gx == (uint32_t)L.NX - 1 || gy == 0 || gy == (uint32_t)L.NY - 1;
+    const uint32_t plane = (uint32_t)L.NX * (uint32_t)L.NY;
+    const uint32_t g0 = (ez * 7 * (uint32_t)L.NY + gy) * (uint32_t)L.NX + gx;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t gz = ez * 7 + k;
+      const bool bnd = side || gz == 0 || gz == (uint32_t)L.NZ - 1;
+      g[k] = (g0 + k * plane) | (bnd ? kGidDirichlet : 0u);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] = gid[e * 512 + k * 64 + b * 8 + a];
+  }
+}
+
+template <typename T, int EB_, bool IMPLICIT>
 __global__ void __launch_bounds__(64 * EB_)
-k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G, const T* __restrict__ u,
-          T* __restrict__ y, unsigned* __restrict__ err) {
+k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
+          const T* __restrict__ u, T* __restrict__ y, unsigned* __restrict__ err) {
   using C = Ax8<T, EB_>;
   constexpr int EB = C::EB, R = C::R, P = C::P;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -151,9 +186,9 @@ k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G, 
   // gather: thread (i = a, j = b) owns the column along t
   uint32_t g[8];
   T col[8];
+  column_ids<IMPLICIT>(gid, lat, e, valid, a, b, g);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    g[k] = valid ? gid[e * 512 + k * 64 + b * 8 + a] : kGidDirichlet;
     col[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
     su[k * P + b * R + a] = col[k];
   }
@@ -228,6 +263,149 @@ k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G, 
   }
 }
 
+// Persistent, software-pipelined variant: each block walks batches of EB elements
+// (blockIdx.x, blockIdx.x + gridDim.x, ...).  While it computes batch i, the TMA copy of
+// batch i+1's geometric factors runs into the second buffer and batch i+1's gather
+// (element-to-global ids and u values) is already in flight into registers.  Waits on the
+// copies are bounded like in k_sem_ax8.
+template <typename T, int EB, bool IMPLICIT>
+__global__ void __launch_bounds__(64 * EB)
+k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
+           const T* __restrict__ u, T* __restrict__ y, unsigned* __restrict__ err) {
+  using C = Ax8<T, EB>;
+  constexpr int R = C::R, P = C::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  T* sG = reinterpret_cast<T*>(smem_raw);                 // [2][EB * GELEM]
+  T* sU = sG + 2 * EB * C::GELEM;
+  T* sR = sU + EB * C::STAGE;
+  T* sS = sR + EB * C::STAGE;
+  const int tid = threadIdx.x;
+  const int le = tid >> 6, t = tid & 63, a = t & 7, b = t >> 3;
+  const int64_t nbatch = (E + EB - 1) / EB;
+  int64_t batch = blockIdx.x;
+  if (batch >= nbatch) return;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t bt, int buf) {
+    const int64_t e0 = bt * EB;
+    const int nv = (int)((E - e0) < EB ? (E - e0) : EB);
+    const uint32_t bytes = (uint32_t)(nv * C::GELEM * sizeof(T));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[buf])), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sG + buf * EB * C::GELEM)),
+        "l"(G + e0 * C::GELEM), "r"(bytes), "r"(smem_addr(&bar[buf]))
+        : "memory");
+  };
+  auto gather = [&](int64_t bt, uint32_t (&g)[8], T (&v)[8]) {
+    const int64_t e = bt * EB + le;
+    const bool valid = bt < nbatch && e < E;
+    column_ids<IMPLICIT>(gid, lat, e, valid, a, b, g);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
+  };
+  if (tid == 0) issue(batch, 0);
+  uint32_t g[8];
+  T col[8];
+  gather(batch, g, col);
+  uint32_t phase = 0;   // bit `buf`: parity of the next wait on bar[buf]
+  T* su = sU + le * C::STAGE;
+  T* sr = sR + le * C::STAGE;
+  T* ss = sS + le * C::STAGE;
+  for (int it = 0; batch < nbatch; ++it, batch += gridDim.x) {
+    const int buf = it & 1;
+    const int64_t next = batch + gridDim.x;
+    if (tid == 0 && next < nbatch) issue(next, buf ^ 1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) su[k * P + b * R + a] = col[k];
+    T ut[8];
+    line8<T, 0>(col, ut);
+    uint32_t gn[8];
+    T cn[8];
+    gather(next, gn, cn);        // next batch's loads overlap this batch's work
+    __syncthreads();
+    {
+      T v[8], o[8];
+      ld_row(su + b * P + a * R, v);
+      line8<T, 0>(v, o);
+      st_row(sr + b * P + a * R, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = su[b * P + j * R + a];
+      line8<T, 0>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ss[b * P + j * R + a] = o[j];
+    }
+    bool ok = false;
+    const uint32_t par = (phase >> buf) & 1u;
+    for (uint32_t w = 0; w < kWaitLimit; ++w)
+      if (mbar_try_wait(&bar[buf], par)) {
+        ok = true;
+        break;
+      }
+    phase ^= 1u << buf;
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      if (tid == 0) atomicExch(err, 1u);
+      // let copies still in flight finish before the block leaves
+      for (uint32_t w = 0; w < kWaitLimit; ++w)
+        if (mbar_try_wait(&bar[buf], par)) break;
+      if (next < nbatch)
+        for (uint32_t w = 0; w < kWaitLimit; ++w)
+          if (mbar_try_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u)) break;
+      return;
+    }
+    T wt[8];
+    const T* gG = sG + buf * EB * C::GELEM + le * C::GELEM;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int p = k * 64 + b * 8 + a;
+      const int q = k * P + b * R + a;
+      const T ur = sr[q], us = ss[q], utk = ut[k];
+      const T g00 = gG[p], g01 = gG[512 + p], g02 = gG[1024 + p];
+      const T g11 = gG[1536 + p], g12 = gG[2048 + p], g22 = gG[2560 + p];
+      sr[q] = g00 * ur + g01 * us + g02 * utk;
+      ss[q] = g01 * ur + g11 * us + g12 * utk;
+      wt[k] = g02 * ur + g12 * us + g22 * utk;
+    }
+    T yt[8];
+    line8<T, 1>(wt, yt);
+    __syncthreads();
+    {
+      T v[8], o[8];
+      ld_row(sr + b * P + a * R, v);
+      line8<T, 1>(v, o);
+      st_row(su + b * P + a * R, o);
+    }
+    __syncthreads();
+    {
+      T v[8], o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = ss[b * P + j * R + a];
+      line8<T, 1>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) su[b * P + j * R + a] += o[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const T v = su[k * P + b * R + a] + yt[k];
+      if (!(g[k] & kGidDirichlet)) atomicAdd(&y[g[k] & kGidMask], v);
+    }
+    __syncthreads();             // stage buffers and this G buffer are free for reuse
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      g[k] = gn[k];
+      col[k] = cn[k];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t sem_ax8_set_D(const double* D) {
@@ -252,32 +430,85 @@ cudaError_t sem_ax8_set_D(const double* D) {
   return cudaMemcpyToSymbol(c_eo_f, f, sizeof(f));
 }
 
-template <typename T, int EB>
-static void launch_ax8(int64_t E, const uint32_t* gid, const T* G, const T* u, T* y, unsigned* err,
-                       cudaStream_t s) {
+template <typename T, int EB, bool IM>
+static void launch_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                       unsigned* err, cudaStream_t s) {
   using C = Ax8<T, EB>;
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_sem_ax8<T, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes());
+    cudaFuncSetAttribute(k_sem_ax8<T, EB, IM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes());
     configured = true;
   }
   const unsigned blocks = (unsigned)((E + EB - 1) / EB);
-  k_sem_ax8<T, EB><<<blocks, 64 * EB, C::smem_bytes(), s>>>(E, gid, G, u, y, err);
+  k_sem_ax8<T, EB, IM><<<blocks, 64 * EB, C::smem_bytes(), s>>>(E, gid, lat, G, u, y, err);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+template <typename T, int EB, bool IM>
+static void launch_ax8p(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                        unsigned* err, cudaStream_t s) {
+  using C = Ax8<T, EB>;
+  const size_t smem = sizeof(T) * (size_t)EB * (2 * C::GELEM + 3 * C::STAGE);
+  static int grid = 0;
+  if (grid == 0) {
+    cudaFuncSetAttribute(k_sem_ax8p<T, EB, IM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_ax8p<T, EB, IM>, 64 * EB, smem);
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int64_t nbatch = (E + EB - 1) / EB;
+  const unsigned blocks = (unsigned)(nbatch < grid ? nbatch : grid);
+  k_sem_ax8p<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y, err);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 template <typename T>
-void sem_ax8(int64_t E, const uint32_t* gid, const T* G, const T* u, T* y, unsigned* err, int eb, cudaStream_t s) {
+size_t sem_ax8_smem(int eb) {
+  eb %= 100;
   switch (eb) {
-    case 1: launch_ax8<T, 1>(E, gid, G, u, y, err, s); break;
-    case 4: launch_ax8<T, 4>(E, gid, G, u, y, err, s); break;
-    default: launch_ax8<T, 2>(E, gid, G, u, y, err, s); break;
+    case 1: return sizeof(T) * 1 * (Ax8<T, 1>::GELEM + 3 * Ax8<T, 1>::STAGE);
+    case 2: return sizeof(T) * 2 * (Ax8<T, 2>::GELEM + 3 * Ax8<T, 2>::STAGE);
+    case 4: return sizeof(T) * 4 * (Ax8<T, 4>::GELEM + 3 * Ax8<T, 4>::STAGE);
+    case 12: return sizeof(T) * 2 * (2 * Ax8<T, 2>::GELEM + 3 * Ax8<T, 2>::STAGE);
+    case 14: return sizeof(T) * 4 * (2 * Ax8<T, 4>::GELEM + 3 * Ax8<T, 4>::STAGE);
+    default: return ~size_t(0);
   }
 }
 
-template void sem_ax8<float>(int64_t, const uint32_t*, const float*, const float*, float*, unsigned*, int,
-                             cudaStream_t);
-template void sem_ax8<double>(int64_t, const uint32_t*, const double*, const double*, double*, unsigned*, int,
-                              cudaStream_t);
+template <typename T>
+bool sem_ax8_variant_fits(int eb) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return sem_ax8_smem<T>(eb) + 256 <= (size_t)optin;   // + static shared (mbarriers)
+}
+
+template <typename T, bool IM>
+static void dispatch_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                         unsigned* err, int eb, cudaStream_t s) {
+  switch (eb) {
+    case 1: launch_ax8<T, 1, IM>(E, gid, lat, G, u, y, err, s); break;
+    case 4: launch_ax8<T, 4, IM>(E, gid, lat, G, u, y, err, s); break;
+    case 12: launch_ax8p<T, 2, IM>(E, gid, lat, G, u, y, err, s); break;
+    case 14: launch_ax8p<T, 4, IM>(E, gid, lat, G, u, y, err, s); break;
+    default: launch_ax8<T, 2, IM>(E, gid, lat, G, u, y, err, s); break;
+  }
+}
+
+template <typename T>
+void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y, unsigned* err,
+             int variant, cudaStream_t s) {
+  if (variant >= 100) dispatch_ax8<T, true>(E, gid, lat, G, u, y, err, variant - 100, s);
+  else dispatch_ax8<T, false>(E, gid, lat, G, u, y, err, variant, s);
+}
+
+template bool sem_ax8_variant_fits<float>(int);
+template bool sem_ax8_variant_fits<double>(int);
+template void sem_ax8<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
+                             unsigned*, int, cudaStream_t);
+template void sem_ax8<double>(int64_t, const uint32_t*, const Lattice&, const double*, const double*, double*,
+                              unsigned*, int, cudaStream_t);
 
 }  // namespace chebmg

@@ -154,3 +154,17 @@ def test_zero_rhs_and_errors():
     with pytest.raises(cm.ChebmgError):
         cm.chebmg_apply_A(s.ctx, 0, F32, empty(225, True), empty(225, True))  # FP64-only context
     s.close()
+
+
+def test_smoother_accepts_unaligned_caller_vectors():
+    # caller vectors that are views at an odd offset take the scalar path of the update kernels
+    H, s = make(63, kind="opt4th")
+    L = H.levels[0]
+    b = W.fd_rhs(63, seed=8)
+    ref = oracle_smooth(L, b, 4, "opt4th", L.lmax, 0.1, x0=None)
+    big = torch.zeros(L.n + 1, device="cuda:0", dtype=torch.float64)
+    x = big[1:]
+    assert x.data_ptr() % 16 != 0
+    cm.chebmg_smooth(s.ctx, 0, F64, T(b), x, 4, True)
+    assert relerr(N(x), ref) < 1e-12
+    s.close()

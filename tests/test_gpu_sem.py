@@ -215,3 +215,31 @@ def test_bounded_barrier_wait_reports_timeout_and_context_survives(verts):
     cm.chebmg_coarse_solve(s.ctx, T(r), z)
     assert np.linalg.norm(r - Lc.apply_A(N(z))) <= 1.01e-10 * np.linalg.norm(r)
     s.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2, 4, 12, 14, 101, 102, 104, 112, 114])
+def test_every_order7_kernel_variant(verts, variant):
+    # the setup autotuner may pick any of these; each must match the oracle
+    L = SemLevel(verts, 7)
+    s = solver(verts, (7, 3, 1), prec="mixed", lmax=[1.0, 1.0])
+    assert cm.chebmg_tile_choice(s.ctx, 0, F64) % 100 in (1, 2, 4, 12, 14)
+    x = np.where(L.dirichlet, 0.0, np.random.default_rng(variant).uniform(-1, 1, L.n))
+    ref = L.apply_A(x)
+    for dt, tol in ((F64, 1e-12), (F32, 2e-5)):
+        if dt == F64 and variant % 100 == 14:
+            # needs 264 KB of shared memory in FP64: rejected, and never picked by the autotuner
+            with pytest.raises(cm.ChebmgError):
+                cm.chebmg_set_tile_choice(s.ctx, 0, dt, variant)
+            continue
+        cm.chebmg_set_tile_choice(s.ctx, 0, dt, variant)
+        if dt == F64:
+            xt, y = T(x), empty(L.n)
+            ref_d = ref
+        else:
+            xt, y = T(x, torch.float32), empty(L.n, True)
+            ref_d = L.apply_A(x.astype(np.float32).astype(np.float64))
+        cm.chebmg_apply_A(s.ctx, 0, dt, xt, y)
+        assert relerr(N(y), ref_d) < tol, (variant, dt)
+    with pytest.raises(cm.ChebmgError):
+        cm.chebmg_set_tile_choice(s.ctx, 1, F64, 2)   # level 1 is order 3
+    s.close()
