@@ -47,6 +47,22 @@ def peaks():
         return {}
 
 
+def recorded_traffic(variant=None):
+    """DRAM bytes per fine step from profiles/roofline_traffic.json, or None if the kernels
+    that make up the step changed since those counters were taken (or another variant runs)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if variant is not None and variant != rec.get("variant"):
+            return None
+        return rec["traffic_bytes_per_step"] if h.hexdigest() == rec["source_sha256"] else None
+    except Exception:
+        return None
+
+
 def config(extra=None):
     c = {"workload": f"SEM Poisson E={NE}^3 N={NORDER}, p-MG {ORDERS}, {KIND} Chebyshev one-sided "
                      f"({2 * K_ORDER},0), FCG to 1e-8",
@@ -308,11 +324,14 @@ def main():
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     achieved = alg_bytes32 / step32 / 1e9
-    roofline = {"bound": "hbm", "kernel": "fine FP32 Chebyshev step: k_sem_ax<float,8> + k_cheb4_step<float>",
+    roofline = {"bound": "hbm",
+                "kernel": "fine FP32 Chebyshev step: k_sem_ax8p (element Ax + gather-scatter) + k_cheb4_step",
                 "achieved": achieved, "peak": hbm if hbm else 6800.0, "unit": "GB/s",
                 "frac": achieved / (hbm if hbm else 6800.0),
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
-                "traffic": None, "alg_bytes_per_step": alg_bytes32, "step_us": step32 * 1e6}
+                "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "of fallback",
+                "traffic": recorded_traffic(cm.chebmg_tile_choice(s32.ctx, 0, 1)),
+                "alg_bytes_per_step": alg_bytes32, "step_us": step32 * 1e6,
+                "elements_per_block_variant": cm.chebmg_tile_choice(s32.ctx, 0, 1)}
     flops64 = 111 * L + 8 * n
     fp64_alu = {"bound": "alu", "kernel": "fine FP64 Chebyshev step", "achieved": flops64 / step64 / 1e12,
                 "peak": 1.25, "unit": "TFLOP/s", "frac": flops64 / step64 / 1e12 / 1.25,
