@@ -115,6 +115,11 @@ int chebmg_launch_count(const chebmg_ctx* ctx, int64_t* count);
  * that kernel). */
 int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* elements_per_block);
 /* Overrides that choice (same codes); EINVAL for other levels or codes. */
+/* SEM coarse solver: PCG whose preconditioner is Algorithm 2 (4th kind, beta = 1) of
+ * `degree` applied from zero with Jacobi scaling (degree 1 = Jacobi-PCG), chosen at setup
+ * by timing; lmax = lambda_max of S A on the coarse level (FP64 Lanczos). */
+int chebmg_coarse_info(const chebmg_ctx* ctx, int* degree, double* lmax);
+int chebmg_set_coarse_degree(chebmg_ctx* ctx, int degree);
 int chebmg_set_tile_choice(chebmg_ctx* ctx, int level, int dtype, int variant);
 
 /* ---- per-level operators (device vectors, dtype as above) ---------------- */
@@ -139,8 +144,8 @@ int chebmg_restrict(chebmg_ctx* ctx, int level, int dtype, const void* rf, void*
 int chebmg_prolong(chebmg_ctx* ctx, int level, int dtype, const void* zc, void* zf,
                    int accumulate);
 
-/* z = A_l^{-1} r on the coarsest level: FD dense Cholesky; SEM Jacobi-PCG to
- * coarse_rtol (iters may be NULL).  FP64 device vectors. */
+/* z = A_l^{-1} r on the coarsest level: FD dense Cholesky; SEM preconditioned CG to
+ * coarse_rtol (see chebmg_coarse_info; iters may be NULL).  FP64 device vectors. */
 int chebmg_coarse_solve(chebmg_ctx* ctx, const double* r, double* z, int* iters);
 
 /* ---- solver --------------------------------------------------------------- */

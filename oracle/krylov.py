@@ -10,6 +10,8 @@ Test infrastructure only (see ``oracle/__init__``).
   ||r||_2 / ||b||_2 <= rtol (the 1e-8 relative residual of Sec. 5.1).
   Iterations = number of x updates = number of preconditioner applications.
 * ``pcg_jacobi``: Jacobi-preconditioned CG, used for the p = 1 coarse problem.
+* ``pcg_cheb4``: CG preconditioned by one degree-m application of Algorithm 2 (the same
+  coarse solver with a polynomial preconditioner; m = 1 reduces to Jacobi-PCG).
 * ``lanczos_lmax``: lambda_max of S A (Sec. 2: lambda_max is the largest
   eigenvalue of S_j A_j; the paper does not say how it is estimated).  Plain
   Lanczos on the symmetric S^{1/2} A S^{1/2}, start vector from SplitMix64, the
@@ -78,6 +80,38 @@ def pcg_jacobi(apply_A, Sdiag, b, rtol: float = 1e-10, maxit: int = 2000):
         p = z + (rz_new / rz) * p
         rz = rz_new
     raise NotConverged(f"coarse PCG did not reach {rtol} in {maxit} iterations")
+
+
+def pcg_cheb4(apply_A, Sdiag, b, lmax: float, degree: int, rtol: float = 1e-10, maxit: int = 2000):
+    """PCG whose preconditioner is one application of Algorithm 2 (4th kind, beta = 1) of the
+    given degree from a zero guess: M^{-1} = q(S A) S with q(l) = (1 - W_m(1 - 2 l/lmax)/(2m+1)) / l,
+    positive on (0, lmax], so M^{-1} is SPD.  degree = 1 is Jacobi-PCG (a scaled S).
+    Returns (x, iterations)."""
+    from .chebyshev import chebyshev_4th
+
+    def precond(r):
+        return chebyshev_4th(apply_A, Sdiag, r, degree, lmax)
+
+    x = np.zeros_like(b)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0
+    r = b.copy()
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, maxit + 1):
+        q = apply_A(p)
+        alpha = rz / (p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        if np.linalg.norm(r) / bnorm <= rtol:
+            return x, it
+        z = precond(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    raise NotConverged(f"polynomial PCG did not reach {rtol} in {maxit} iterations")
 
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)

@@ -80,6 +80,8 @@ _SIGNATURES = {
     "chebmg_launch_count": (c_int, [c_void_p, POINTER(c_int64)]),
     "chebmg_tile_choice": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
     "chebmg_set_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "chebmg_coarse_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
+    "chebmg_set_coarse_degree": (c_int, [c_void_p, c_int]),
     "chebmg_apply_A": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "chebmg_inv_diagonal": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "chebmg_smooth": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_int]),
@@ -210,6 +212,17 @@ def chebmg_tile_choice(ctx, level, dtype) -> int:
     v = c_int()
     _check(lib().chebmg_tile_choice(ctx, int(level), int(dtype), byref(v)), "chebmg_tile_choice")
     return v.value
+
+
+def chebmg_coarse_info(ctx):
+    """(degree of the coarse CG's polynomial preconditioner, lambda_max of the coarse level)."""
+    m, l = c_int(), c_double()
+    _check(lib().chebmg_coarse_info(ctx, byref(m), byref(l)), "chebmg_coarse_info")
+    return m.value, l.value
+
+
+def chebmg_set_coarse_degree(ctx, degree):
+    _check(lib().chebmg_set_coarse_degree(ctx, int(degree)), "chebmg_set_coarse_degree")
 
 
 def chebmg_set_tile_choice(ctx, level, dtype, variant):

@@ -125,8 +125,13 @@ struct chebmg_ctx {
   bool coop_ok = false;
   unsigned* cctl = nullptr;     // [5] control words of the persistent kernel
   unsigned* hcctl = nullptr;    // pinned host copy
-  double* cpart = nullptr;      // [2][3 * coarse_grid]
-  double* cvec[1] = {nullptr};  // u = M r of the persistent coarse CG
+  double* cpart = nullptr;      // [3 * coarse_grid + 3]
+  double* cxbuf[2] = {nullptr, nullptr};   // exchange buffers of the persistent coarse CG
+  unsigned* cflag = nullptr;    // [coarse_grid] exchange flags
+  int coarse_rows_per_block = 0;
+  int coarse_halo = 0;
+  int coarse_degree = 1;        // 4th-kind polynomial preconditioner degree (autotuned)
+  double coarse_lmax = 0.0;
   unsigned* dstat = nullptr;    // [4] device-side error flags of the operator kernels
   unsigned* hdstat = nullptr;
 };
@@ -288,14 +293,26 @@ CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
   a.invD = static_cast<const double*>(C.invD[CHEBMG_F64]);
   a.b = b;
   a.x = x;
-  a.u = c->cvec[0];
+  a.xbuf[0] = c->cxbuf[0];
+  a.xbuf[1] = c->cxbuf[1];
+  a.flag = c->cflag;
+  a.rows_per_block = c->coarse_rows_per_block;
+  a.halo = c->coarse_halo;
   a.part = c->cpart;
   a.tot = c->cpart + 3 * std::max(1, c->coarse_grid);
   a.ctl = c->cctl;
   a.rtol = c->o.coarse_rtol;
   a.maxit = c->o.coarse_maxit;
+  a.degree = c->coarse_degree;
+  a.lmax = c->coarse_lmax > 0.0 ? c->coarse_lmax : 1.0;
   a.phantom_blocks = 0;
   return a;
+}
+
+// Resets the control words and exchange flags of the persistent coarse kernel.
+void coarse_reset(chebmg_ctx* c) {
+  CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 4, c->s));
+  CK(cudaMemsetAsync(c->cflag, 0, sizeof(unsigned) * std::max(1, c->coarse_grid), c->s));
 }
 
 // FP64 coarse solve on the last level: FD dense inverse, SEM Jacobi-PCG.
@@ -311,9 +328,9 @@ int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {
   const double* S = static_cast<const double*>(C.invD[CHEBMG_F64]);
   double *r = c->cr, *z = c->cz, *p = c->cp, *q = c->cq;
   if (c->coop_ok) {
-    // whole Jacobi-PCG in one cooperative launch; no host round trip.  Status and
-    // iterations land in cctl[2..3], errors also in the sticky cctl[4].
-    CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 4, c->s));
+    // whole PCG in one cooperative launch; no host round trip.  Status and iterations
+    // land in cctl[2..3], errors also in the sticky cctl[4].
+    coarse_reset(c);
     CoarseCG a = coarse_args(c, b, x);
     a.phantom_blocks = 0;
     cudaError_t e = cudaSuccess;
@@ -512,15 +529,20 @@ void common_alloc(chebmg_ctx* c) {
   if (c->ell_col) {
     int coop = 0;
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev));
-    c->coarse_grid = coarse_pcg_grid(nc);
-    c->coop_ok = coop != 0 && c->coarse_grid > 0;
+    int grid = 0, rb = 0;
+    coarse_pcg_shape(nc, &grid, &rb);
+    c->coarse_grid = grid;
+    c->coarse_rows_per_block = rb;
+    c->coop_ok = coop != 0 && grid > 0;
     c->cctl = dalloc<unsigned>(c, 5);
     CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 5, c->s));
     CK(cudaMallocHost(&h, sizeof(unsigned) * 5));
     c->hcctl = static_cast<unsigned*>(h);
     std::memset(c->hcctl, 0, sizeof(unsigned) * 5);
-    c->cpart = dalloc<double>(c, 3 * std::max(1, c->coarse_grid) + 3);
-    c->cvec[0] = dalloc<double>(c, nc);
+    c->cpart = dalloc<double>(c, 3 * std::max(1, grid) + 3);
+    c->cxbuf[0] = dalloc<double>(c, nc);
+    c->cxbuf[1] = dalloc<double>(c, nc);
+    c->cflag = dalloc<unsigned>(c, std::max(1, grid));
   }
 }
 
@@ -572,6 +594,45 @@ void autotune_ax8(chebmg_ctx* c, int j) {
   CK(cudaMemsetAsync(y, 0, sizeof(T) * L.n, c->s));
 }
 
+// Picks the degree of the coarse CG's polynomial preconditioner by timing full coarse solves
+// of a seeded right-hand side (degree 1 = Jacobi-PCG).
+void autotune_coarse_degree(chebmg_ctx* c) {
+  Level& C = c->L.back();
+  const int64_t n = C.n;
+  double* b = vec<double>(C, VB);
+  double* x = vec<double>(C, VX);
+  splitmix_fill(n, 7ull, static_cast<const double*>(C.invD[CHEBMG_F64]), b, c->s);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_m = 1;
+  for (int m : {1, 2, 4, 8, 12, 16}) {
+    c->coarse_degree = m;
+    float t_min = 1e30f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      CK(cudaEventRecord(e0, c->s));
+      if (coarse_solve64(c, b, x) != CHEBMG_OK) ok = false;
+      CK(cudaEventRecord(e1, c->s));
+      CK(cudaEventSynchronize(e1));
+      read_scal(c);
+      if (c->hcctl[2] != CS_OK) ok = false;
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      t_min = std::min(t_min, ms);
+    }
+    if (ok && t_min < best) {
+      best = t_min;
+      best_m = m;
+    }
+  }
+  c->coarse_degree = best_m;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaMemsetAsync(c->cctl + 4, 0, sizeof(unsigned), c->s));
+}
+
 void finish_setup(chebmg_ctx* c) {
   const int nl = (int)c->L.size();
   for (int j = 0; j < nl; ++j) {
@@ -586,6 +647,11 @@ void finish_setup(chebmg_ctx* c) {
     else lm = c->o.lmax_scale * lanczos(c, j, c->o.lanczos_steps);
     if (!(lm > 0.0) || !std::isfinite(lm)) throw Error(CHEBMG_EBREAKDOWN, "non-positive lambda_max");
     c->L[j].lmax = lm;
+  }
+  if (c->coop_ok) {
+    // lambda_max of S A on the coarse level (same Lanczos), then the preconditioner degree
+    c->coarse_lmax = lanczos(c, nl - 1, c->o.lanczos_steps);
+    autotune_coarse_degree(c);
   }
   CK(cudaStreamSynchronize(c->s));
 }
@@ -799,6 +865,16 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
           std::vector<int> col;
           std::vector<double> val;
           assemble_ell(h, c->nslot, col, val);
+          int grid = 0, rb = 0;
+          coarse_pcg_shape(h.n, &grid, &rb);
+          int halo = 0;
+          if (rb > 0)
+            for (int64_t g = 0; g < h.n; ++g)
+              for (int k = 0; k < c->nslot; ++k) {
+                const int64_t cc = col[(size_t)k * h.n + g];
+                halo = std::max<int>(halo, (int)std::llabs(cc / rb - g / rb));
+              }
+          c->coarse_halo = halo;
           c->ell_col = dalloc<int>(c, (int64_t)col.size());
           CK(cudaMemcpy(c->ell_col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
           c->ell_val = upload<double>(c, val);
@@ -843,6 +919,19 @@ int chebmg_tile_choice(const chebmg_ctx* c, int level, int dtype, int* elements_
     return CHEBMG_EINVAL;
   const Level& L = c->L[level];
   *elements_per_block = (L.type == TYPE_SEM && L.Q == 8) ? L.eb[dtype] : 0;
+  return CHEBMG_OK;
+}
+
+int chebmg_coarse_info(const chebmg_ctx* c, int* degree, double* lmax) {
+  if (!c || !degree || !lmax) return CHEBMG_EINVAL;
+  *degree = (c->coop_ok && c->L.back().type == TYPE_SEM) ? c->coarse_degree : 1;
+  *lmax = c->coarse_lmax;
+  return CHEBMG_OK;
+}
+
+int chebmg_set_coarse_degree(chebmg_ctx* c, int degree) {
+  if (!c || degree < 1 || degree > 64) return CHEBMG_EINVAL;
+  c->coarse_degree = degree;
   return CHEBMG_OK;
 }
 
@@ -1061,7 +1150,8 @@ int chebmg_selftest_coarse_timeout(chebmg_ctx* c, int* status) {
     if (!c->cctl || !c->coop_ok) throw Error(CHEBMG_EINVAL, "no persistent coarse solver in this context");
     Level& C = c->L.back();
     const int64_t n = C.n;
-    CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 5, c->s));
+    coarse_reset(c);
+    CK(cudaMemsetAsync(c->cctl + 4, 0, sizeof(unsigned), c->s));
     CoarseCG a = coarse_args(c, c->cb, c->cx);
     a.phantom_blocks = 1;    // one arrival that never comes: every barrier wait runs out
     cudaError_t e = cudaSuccess;

@@ -129,19 +129,26 @@ struct CoarseCG {
   const double* invD;
   const double* b;
   double* x;
-  double* u;             // u = M r, exchanged between blocks once per iteration
-  double* part;          // [3 * gridDim] block partials of (r, u), (A u, u), (r, r)
+  double* xbuf[2];       // vector exchanged for the next product, double-buffered by generation parity
+  unsigned* flag;        // [gridDim] last generation each block has published
+  int rows_per_block;    // block q owns rows [q * rows_per_block, (q + 1) * rows_per_block)
+  int halo;              // block q reads rows owned by blocks q - halo .. q + halo (symmetric)
+  double* part;          // [3 * gridDim] block partials
   double* tot;           // [3] their totals, published by the last block to reach the barrier
   unsigned* ctl;         // [5], ctl[0..1] zero at launch
   double rtol;
   int maxit;
+  int degree;            // degree of the 4th-kind Chebyshev preconditioner (1 = Jacobi)
+  double lmax;           // lambda_max of S A on the coarse level
   unsigned phantom_blocks;   // self-test only: barrier also waits for this many blocks that never come
 };
 // Rows per thread the persistent coarse kernel can keep in registers.
 constexpr int kCoarseMaxRowsPerThread = 8;
+constexpr int kCoarseThreadsPerBlock = 256;
 // Returns false (nothing launched) if a cooperative launch is not possible.
 bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err);
-int coarse_pcg_grid(int64_t n);
+// Grid size (blocks) and rows per block for a coarse problem of n rows; grid 0 = not possible.
+void coarse_pcg_shape(int64_t n, int* grid, int* rows_per_block);
 
 // ---- Lanczos helpers ----
 void splitmix_fill(int64_t n, uint64_t seed, const double* invD, double* v, cudaStream_t s);

@@ -833,103 +833,205 @@ __device__ __forceinline__ bool barrier_reduce3(unsigned* ctl, unsigned& gen, un
   return s_ok != 0;
 }
 
-// Persistent Jacobi-preconditioned CG in the Chronopoulos-Gear form: one reduction per
-// iteration (gamma = (r, u), delta = (A u, u), rho = (r, r) with u = M r) and two grid
-// barriers -- after u is published for the neighbours' product, and after the product and
-// the partial sums (that one also forms the totals).  Each thread owns up to RPT rows whose
-// x, r, s, p, w stay in registers for the whole solve; the ELL matrix is read through the
-// read-only cache path.
+// Exchange of one vector with the neighbouring blocks (the rows a product reads): each block
+// writes its rows into the buffer of the new generation's parity, fences, raises its flag,
+// and waits -- bounded -- until every block within `halo` has raised the same generation.
+// Because the neighbourhood is symmetric, a block can only reuse a buffer parity after all
+// its readers have published the next generation, i.e. finished reading the old one.
+__device__ __forceinline__ void publish_rows(const CoarseCG& a, unsigned gen, const double* v, int rpt,
+                                             int64_t base) {
+  double* buf = a.xbuf[gen & 1u];
+  for (int q = 0; q < rpt; ++q) {
+    const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
+    if (g < a.n && g < base + a.rows_per_block) buf[g] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(&a.flag[blockIdx.x], gen);
+  }
+}
+
+__device__ __forceinline__ bool wait_neighbours(const CoarseCG& a, unsigned gen) {
+  const int lo = max(0, (int)blockIdx.x - a.halo);
+  const int hi = min((int)gridDim.x - 1, (int)blockIdx.x + a.halo);
+  int ok = 1;
+  if ((int)threadIdx.x <= hi - lo) {
+    const unsigned* f = &a.flag[lo + threadIdx.x];
+    unsigned spins = 0;
+    while (*(volatile const unsigned*)f < gen) {
+      if (++spins > kSpinLimit) {
+        atomicMax((int*)&a.ctl[4], (int)CS_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// y = A v for the owned rows, v read from the exchange buffer of generation gen.
 template <int NS, int RPT>
-__global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
+__device__ __forceinline__ void coarse_spmv(const CoarseCG& a, unsigned gen, int64_t base, double (&y)[RPT]) {
+  const double* v = a.xbuf[gen & 1u];
   const int64_t n = a.n;
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const unsigned expected = gridDim.x + a.phantom_blocks;
-  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   const int ns = NS > 0 ? NS : a.nslot;
-  unsigned gen = 0;
-  double x[RPT], r[RPT], s[RPT], p[RPT], w[RPT], S[RPT];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
-    const int64_t g = t0 + q * stride;
-    const bool live = g < n;
-    S[q] = live ? __ldg(&a.invD[g]) : 0.0;
-    r[q] = (live && S[q] != 0.0) ? a.b[g] : 0.0;
-    x[q] = s[q] = p[q] = w[q] = 0.0;
-    if (live) a.u[g] = S[q] * r[q];
-  }
-  double gam_old = 0.0, alpha_old = 0.0, bb = 0.0, tol2 = 0.0;
-  for (int it = 0;; ++it) {
-    if (!grid_barrier(a.ctl, gen, expected)) return;
-    // w = A u for the owned rows, and this block's partial sums
-    double gam = 0.0, del = 0.0, rho = 0.0;
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      const int64_t g = t0 + q * stride;
-      if (g >= n) continue;
-      double acc = 0.0;
+    const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
+    double acc = 0.0;
+    if (g < n && g < base + a.rows_per_block) {
       if (NS > 0) {
 #pragma unroll
         for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
-          acc += __ldg(&a.val[k * n + g]) * __ldcg(&a.u[__ldg(&a.col[k * n + g])]);
+          acc += __ldg(&a.val[k * n + g]) * __ldcg(&v[__ldg(&a.col[k * n + g])]);
       } else {
-#pragma unroll 9
-        for (int k = 0; k < ns; ++k) acc += __ldg(&a.val[k * n + g]) * __ldcg(&a.u[__ldg(&a.col[k * n + g])]);
+        for (int k = 0; k < ns; ++k) acc += __ldg(&a.val[k * n + g]) * __ldcg(&v[__ldg(&a.col[k * n + g])]);
       }
-      w[q] = acc;
-      const double uq = S[q] * r[q];
-      gam += r[q] * uq;
-      del += acc * uq;
-      rho += r[q] * r[q];
     }
-    block_sum3(gam, del, rho);
-    if (threadIdx.x == 0) {
-      a.part[3 * blockIdx.x] = gam;
-      a.part[3 * blockIdx.x + 1] = del;
-      a.part[3 * blockIdx.x + 2] = rho;
-    }
-    double G, Dl, Rh;
-    if (!barrier_reduce3(a.ctl, gen, expected, a.part, a.tot, G, Dl, Rh)) return;
-    int status = 0;
-    if (it == 0) {
-      bb = Rh;
-      tol2 = a.rtol * a.rtol * bb;
-      if (!(bb > 0.0)) status = bb == 0.0 ? CS_OK : CS_BREAKDOWN;
-    }
-    if (!status && !(Rh == Rh)) status = CS_BREAKDOWN;
-    if (!status && Rh <= tol2) status = CS_OK;
-    if (!status && it >= a.maxit) status = CS_NOTCONV;
-    const double beta = it == 0 ? 0.0 : G / gam_old;
-    const double den = it == 0 ? Dl : Dl - beta * G / alpha_old;
-    if (!status && (!(den > 0.0) || !(G > 0.0))) status = CS_BREAKDOWN;
-    if (status) {
-      // x holds the iterate after `it` updates
+    y[q] = acc;
+  }
+}
+
+// Persistent preconditioned CG on the assembled coarse operator.  The preconditioner is one
+// application of Algorithm 2 (4th kind, beta = 1) of degree m from a zero guess, Jacobi-
+// scaled -- SPD for every m, and for m = 1 simply Jacobi.  Per CG iteration: m products,
+// each needing only the neighbouring blocks' rows (flag exchange), and two grid-wide
+// reductions (reduce-then-release barrier).  Owned rows live in registers.
+template <int NS, int RPT>
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
+  const int64_t n = a.n;
+  const int64_t base = (int64_t)blockIdx.x * a.rows_per_block;
+  const unsigned expected = gridDim.x + a.phantom_blocks;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned gb = 0, gx = 0;   // generations: grid barrier, neighbour exchange
+  double x[RPT], r[RPT], p[RPT], z[RPT], S[RPT], d[RPT], rp[RPT], y[RPT];
+  bool live[RPT];
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int64_t g = t0 + q * stride;
-        if (g < n) a.x[g] = x[q];
-      }
-      if (lead) {
-        a.ctl[2] = (unsigned)status;
-        a.ctl[3] = (unsigned)it;
-        if (status == CS_BREAKDOWN) atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
-      }
-      return;
-    }
-    const double alpha = G / den;
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
+    live[q] = g < n && g < base + a.rows_per_block;
+    S[q] = live[q] ? __ldg(&a.invD[g]) : 0.0;
+    r[q] = (live[q] && S[q] != 0.0) ? a.b[g] : 0.0;
+    x[q] = p[q] = 0.0;
+  }
+  const double c0 = 4.0 / (3.0 * a.lmax);
+  // z = M r: Algorithm 2 from a zero guess; returns false on a failed exchange
+  auto precond = [&]() -> bool {
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-      const int64_t g = t0 + q * stride;
-      if (g >= n) continue;
-      p[q] = fma(beta, p[q], S[q] * r[q]);
-      s[q] = fma(beta, s[q], w[q]);
-      x[q] = fma(alpha, p[q], x[q]);
-      r[q] = fma(-alpha, s[q], r[q]);
-      a.u[g] = S[q] * r[q];
+      rp[q] = r[q];
+      d[q] = c0 * S[q] * rp[q];
+      z[q] = 0.0;
     }
-    gam_old = G;
-    alpha_old = alpha;
+    for (int i = 1; i < a.degree; ++i) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) z[q] += d[q];
+      publish_rows(a, ++gx, d, RPT, base);
+      if (!wait_neighbours(a, gx)) return false;
+      coarse_spmv<NS, RPT>(a, gx, base, y);
+      const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0), c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        rp[q] -= y[q];
+        d[q] = c1 * d[q] + c2 * S[q] * rp[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) z[q] += d[q];
+    return true;
+  };
+  auto finish = [&](int status, int it) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
+      if (live[q]) a.x[g] = x[q];
+    }
+    if (lead) {
+      a.ctl[2] = (unsigned)status;
+      a.ctl[3] = (unsigned)it;
+      if (status == CS_BREAKDOWN) atomicMax((int*)&a.ctl[4], (int)CS_BREAKDOWN);
+    }
+  };
+  if (!precond()) return;
+  double rz = 0.0, rr = 0.0, zero = 0.0;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    p[q] = z[q];
+    rz += r[q] * z[q];
+    rr += r[q] * r[q];
   }
+  block_sum3(rz, rr, zero);
+  if (threadIdx.x == 0) {
+    a.part[3 * blockIdx.x] = rz;
+    a.part[3 * blockIdx.x + 1] = rr;
+    a.part[3 * blockIdx.x + 2] = 0.0;
+  }
+  double gam, bb, unused;
+  if (!barrier_reduce3(a.ctl, gb, expected, a.part, a.tot, gam, bb, unused)) return;
+  if (!(bb > 0.0) || !(gam >= 0.0)) {
+    finish(bb == 0.0 ? CS_OK : CS_BREAKDOWN, 0);
+    return;
+  }
+  const double tol2 = a.rtol * a.rtol * bb;
+  publish_rows(a, ++gx, p, RPT, base);
+  for (int it = 1; it <= a.maxit; ++it) {
+    if (!wait_neighbours(a, gx)) return;
+    coarse_spmv<NS, RPT>(a, gx, base, y);
+    double pq = 0.0, z1 = 0.0, z2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) pq += p[q] * y[q];
+    block_sum3(pq, z1, z2);
+    if (threadIdx.x == 0) {
+      a.part[3 * blockIdx.x] = pq;
+      a.part[3 * blockIdx.x + 1] = 0.0;
+      a.part[3 * blockIdx.x + 2] = 0.0;
+    }
+    double pq_tot;
+    if (!barrier_reduce3(a.ctl, gb, expected, a.part, a.tot, pq_tot, z1, z2)) return;
+    if (!(pq_tot > 0.0)) {
+      finish(CS_BREAKDOWN, it);
+      return;
+    }
+    const double alpha = gam / pq_tot;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      x[q] = fma(alpha, p[q], x[q]);
+      r[q] = fma(-alpha, y[q], r[q]);
+    }
+    if (!precond()) return;
+    double rz2 = 0.0, rr2 = 0.0;
+    z1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      rz2 += r[q] * z[q];
+      rr2 += r[q] * r[q];
+    }
+    block_sum3(rz2, rr2, z1);
+    if (threadIdx.x == 0) {
+      a.part[3 * blockIdx.x] = rz2;
+      a.part[3 * blockIdx.x + 1] = rr2;
+      a.part[3 * blockIdx.x + 2] = 0.0;
+    }
+    double gam_new, rr_tot;
+    if (!barrier_reduce3(a.ctl, gb, expected, a.part, a.tot, gam_new, rr_tot, z1)) return;
+    if (!(rr_tot == rr_tot)) {
+      finish(CS_BREAKDOWN, it);
+      return;
+    }
+    if (rr_tot <= tol2) {
+      finish(CS_OK, it);
+      return;
+    }
+    const double beta = gam_new / gam;
+    gam = gam_new;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) p[q] = fma(beta, p[q], z[q]);
+    publish_rows(a, ++gx, p, RPT, base);
+  }
+  finish(CS_NOTCONV, a.maxit);
 }
 
 template <int NS>
@@ -942,31 +1044,32 @@ static const void* coarse_kernel(int rpt) {
   }
 }
 
-static int coarse_rpt(int64_t n, int grid) {
-  const int64_t threads = (int64_t)grid * kCoarseThreads;
-  const int64_t need = (n + threads - 1) / threads;
-  return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 0;
-}
-
-int coarse_pcg_grid(int64_t n) {
-  static int cached = -1;
-  if (cached < 0) {
-    int dev = 0, sms = 0, per_sm = 0;
+void coarse_pcg_shape(int64_t n, int* grid, int* rows_per_block) {
+  static int sms = -1;
+  if (sms < 0) {
+    int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_pcg<0, 8>, kCoarseThreads, 0);
-    cached = sms * (per_sm > 0 ? 1 : 0);
   }
-  const int64_t need = (n + kCoarseThreads - 1) / kCoarseThreads;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cached, need));
-  return coarse_rpt(n, grid) > 0 ? grid : 0;   // 0: too large to keep in registers
+  const int64_t per_block_min = (n + sms - 1) / sms;
+  int rpt = 1;
+  while ((int64_t)rpt * kCoarseThreads < per_block_min && rpt < kCoarseMaxRowsPerThread) rpt *= 2;
+  const int64_t rb = (int64_t)rpt * kCoarseThreads;
+  const int64_t g = (n + rb - 1) / rb;
+  if (g > sms) {
+    *grid = 0;
+    *rows_per_block = 0;
+    return;
+  }
+  *grid = (int)std::max<int64_t>(1, g);
+  *rows_per_block = (int)rb;
 }
 
 bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err) {
   CoarseCG arg = a;
   void* params[] = {&arg};
-  const int rpt = coarse_rpt(a.n, grid);
-  if (rpt == 0 || grid <= 0) {
+  const int rpt = a.rows_per_block / kCoarseThreads;
+  if (grid <= 0 || rpt < 1) {
     if (err) *err = cudaErrorInvalidConfiguration;
     return false;
   }

@@ -110,15 +110,23 @@ def test_coarse_cg_and_lanczos(verts):
     for j, L in enumerate(H.levels[:-1]):
         assert abs(s.lambda_max(j) / L.lmax - 1) < 1e-10
     Lc = H.levels[-1]
+    m, lc = cm.chebmg_coarse_info(s.ctx)
+    assert 1 <= m <= 16
+    assert abs(lc / K.lanczos_lmax(Lc.apply_A, Lc.invD, 30) - 1) < 1e-10
     r = np.random.default_rng(9).uniform(-1, 1, Lc.n)
     r[Lc.dirichlet] = 0
-    z = empty(Lc.n)
-    iters = cm.chebmg_coarse_solve(s.ctx, T(r), z)
-    zz = N(z)
-    assert np.linalg.norm(r - Lc.apply_A(zz)) <= 1.01e-10 * np.linalg.norm(r)
-    x_ref, it_ref = K.pcg_jacobi(Lc.apply_A, Lc.invD, r, 1e-10)
-    assert abs(iters - it_ref) <= 1
-    assert relerr(zz, x_ref) < 1e-8
+    # the autotuned degree, plain Jacobi (degree 1) and a high degree, each against the oracle
+    for deg in (m, 1, 8):
+        cm.chebmg_set_coarse_degree(s.ctx, deg)
+        z = empty(Lc.n)
+        iters = cm.chebmg_coarse_solve(s.ctx, T(r), z)
+        zz = N(z)
+        assert np.linalg.norm(r - Lc.apply_A(zz)) <= 1.01e-10 * np.linalg.norm(r)
+        x_ref, it_ref = K.pcg_cheb4(Lc.apply_A, Lc.invD, r, lc, deg, 1e-10)
+        assert abs(iters - it_ref) <= 1, (deg, iters, it_ref)
+        assert relerr(zz, x_ref) < 1e-8
+        if deg == 1:
+            assert abs(iters - K.pcg_jacobi(Lc.apply_A, Lc.invD, r, 1e-10)[1]) <= 1
     s.close()
 
 

@@ -71,3 +71,32 @@ def test_not_converged_raises():
     A = laplacian_5pt(30, 30, 1 / 31, 1 / 31)
     with pytest.raises(K.NotConverged):
         K.pcg_jacobi(lambda v: A @ v, 1 / A.diagonal(), np.ones(900), 1e-12, maxit=3)
+
+
+def test_polynomial_pcg_degree_one_is_jacobi_pcg_and_higher_degrees_cut_iterations():
+    m = 31
+    A = laplacian_5pt(m, m, 1 / (m + 1), 1 / (m + 1))
+    S = 1 / A.diagonal()
+    b = np.random.default_rng(5).uniform(-1, 1, m * m)
+    lmax = K.lanczos_lmax(lambda v: A @ v, S, steps=60) * 1.01
+    xj, itj = K.pcg_jacobi(lambda v: A @ v, S, b, 1e-10)
+    x1, it1 = K.pcg_cheb4(lambda v: A @ v, S, b, lmax, 1, 1e-10)
+    assert it1 == itj
+    np.testing.assert_allclose(x1, xj, rtol=1e-8, atol=1e-12)
+    xd = np.linalg.solve(A.toarray(), b)
+    prev = itj
+    for deg in (2, 4, 8):
+        x, it = K.pcg_cheb4(lambda v: A @ v, S, b, lmax, deg, 1e-10)
+        assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b) * 1.01
+        np.testing.assert_allclose(x, xd, rtol=1e-7, atol=1e-10)
+        assert it < prev
+        prev = it
+    # the degree-m preconditioner is SPD: its dense matrix is symmetric positive definite
+    from oracle.chebyshev import chebyshev_4th
+    n = 64
+    A2 = laplacian_5pt(8, 8, 1 / 9, 1 / 9)
+    S2 = 1 / A2.diagonal()
+    l2 = K.lanczos_lmax(lambda v: A2 @ v, S2, steps=64)
+    M = np.stack([chebyshev_4th(lambda v: A2 @ v, S2, np.eye(n)[i], 6, l2) for i in range(n)], axis=1)
+    assert np.abs(M - M.T).max() < 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
