@@ -262,7 +262,10 @@ void restrict_to(chebmg_ctx* c, int j, const T* rf, T* rc) {
   const int dt = dt_of<T>();
   if (F.type == TYPE_SEM) {
     zero<T>(c, rc, C.n);
-    sem_restrict<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), rf, rc, c->s);
+    if (transfer_box_supported(F.Q, C.Q))
+      restrict_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, rf, rc, c->s);
+    else
+      sem_restrict<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), rf, rc, c->s);
   } else {
     fd_restrict<T>(F.mx, F.my, C.mx, C.my, F.c_next, rf, rc, c->s);
   }
@@ -276,7 +279,10 @@ void prolong_to(chebmg_ctx* c, int j, const T* zc, T* zf, int accumulate) {
   Level& C = c->L[j + 1];
   const int dt = dt_of<T>();
   if (F.type == TYPE_SEM) {
-    sem_prolong<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), zc, zf, accumulate, c->s);
+    if (transfer_box_supported(F.Q, C.Q))
+      prolong_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, zc, zf, accumulate, c->s);
+    else
+      sem_prolong<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), zc, zf, accumulate, c->s);
   } else {
     fd_prolong<T>(F.mx, F.my, C.mx, C.my, F.c_next, zc, zf, accumulate, c->s);
   }
@@ -858,6 +864,7 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
         if (j + 1 < nlevels) {
           std::vector<double> J;
           lagrange_interp(H[j + 1].x, h.x, J);
+          if (transfer_box_supported(h.NQ, H[j + 1].NQ)) CK(transfer_box_set_J(h.NQ, H[j + 1].NQ, J.data()));
           L.Jn[CHEBMG_F64] = upload<double>(c, J);
           if (c->fp32) L.Jn[CHEBMG_F32] = upload<float>(c, J);
         }

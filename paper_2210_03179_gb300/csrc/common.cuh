@@ -64,6 +64,16 @@ void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, con
 template <typename T>
 bool sem_ax8_variant_fits(int eb);
 
+// p-multigrid transfers on the box lattice for the order pairs (7,3) and (3,1) (Q 8->4, 4->2).
+cudaError_t transfer_box_set_J(int Qf, int Qc, const double* J);
+bool transfer_box_supported(int Qf, int Qc);
+template <typename T>
+void restrict_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* rf, T* rc,
+                  cudaStream_t s);
+template <typename T>
+void prolong_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* zc, T* zf,
+                 int accumulate, cudaStream_t s);
+
 // ---- FD kernels ----
 template <typename T>
 void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s);
