@@ -166,6 +166,66 @@ int chebmg_pcg_solve(chebmg_ctx* ctx, const double* b, double* u, double rtol, i
 int chebmg_pcg_solve_host(chebmg_ctx* ctx, const double* b_host, double* u_host, double rtol,
                           int maxit, int* iters, double* relres);
 
+/* ---- batches of right-hand sides ------------------------------------------------ */
+
+/* The problem statement (Sec. 1) is a sequence of Poisson problems A u = b with one
+ * operator: setup is amortised over many right-hand sides.  These calls solve several of
+ * them at once. */
+typedef struct chebmg_group chebmg_group;
+
+/* flags: capture each Krylov half-iteration as a CUDA graph and replay it (needs a coarse
+ * solve without host decisions: FD, or an SEM coarsest level of at most 3072 nodes;
+ * otherwise the flag is ignored and the same kernels are launched one by one). */
+#define CHEBMG_BATCH_GRAPH 1
+
+/* nrhs independent chebmg_pcg_solve problems in one pass: every operator, transfer,
+ * smoother and reduction kernel processes all right-hand sides in one launch (the order-7
+ * operator stages each element's geometric factors once for several right-hand sides), each
+ * right-hand side with its own FCG scalars and stopping test; one that has converged is
+ * frozen while the others iterate, so iterations and results equal those of separate
+ * solves up to rounding.  B, U: FP64 device arrays [nrhs][n] (right-hand side q at q*n).
+ * iters, relres: host arrays of nrhs entries (may be NULL).  1 <= nrhs <= 65535.  The
+ * first call for a batch size allocates nrhs copies of the work vectors and times the
+ * batched kernel variants on the context's data (autotuning).  Returns the worst status
+ * over the batch: EBREAKDOWN before ENOTCONV before OK; ETIMEOUT if a bounded device wait
+ * gave up. */
+int chebmg_pcg_solve_batched(chebmg_ctx* ctx, int nrhs, const double* B, double* U, double rtol,
+                             int maxit, int flags, int* iters, double* relres);
+
+/* Y = A X on `level` for nrhs vectors at once: X, Y device arrays [nrhs][n] of the dtype,
+ * vector q at q*n.  Same kernels as the batched solve. */
+int chebmg_apply_A_batched(chebmg_ctx* ctx, int level, int dtype, int nrhs, const void* X, void* Y);
+
+/* Z = B R: one V-cycle (Eq. 2.2) for each of nrhs FP64 vectors, R, Z device arrays
+ * [nrhs][n] of the finest level. */
+int chebmg_vcycle_batched(chebmg_ctx* ctx, int nrhs, const double* R, double* Z);
+
+/* Autotuned choices for batches of nrhs (allocating and tuning as the first batched solve
+ * would): *variant = 1000 * right-hand sides per block + (100 if global ids come from the
+ * box lattice) + elements per block of the batched order-7 operator on `level` (0 for other
+ * levels or nrhs = 1); *coarse_degree = degree of the Algorithm 2 preconditioner of the
+ * per-right-hand-side coarse CG (0 if the coarsest level is not solved that way). */
+int chebmg_batch_info(chebmg_ctx* ctx, int nrhs, int level, int dtype, int* variant,
+                      int* coarse_degree);
+
+/* Overrides the autotuned batched order-7 variant (encoding as in chebmg_batch_info) for
+ * batches of nrhs >= 2 on `level`; EINVAL for other levels or a variant that does not fit. */
+int chebmg_set_batch_tile_choice(chebmg_ctx* ctx, int nrhs, int level, int dtype, int variant);
+
+/* A group of contexts on one device -- meshes of different sizes and polynomial orders --
+ * each solving one right-hand side per chebmg_group_pcg_solve call.  Every context runs on
+ * its own stream; with CHEBMG_BATCH_GRAPH each Krylov half-iteration of all of them is one
+ * captured CUDA graph (fork/join over the streams), so the meshes' kernels overlap on the
+ * GPU.  The contexts stay owned by the caller and must outlive the group; the group keeps
+ * no reference to B or U.  Contexts must be distinct.  While a group call runs, its
+ * contexts must not be used otherwise. */
+int chebmg_group_create(chebmg_ctx* const* ctxs, int nctx, chebmg_group** group);
+/* B[k], U[k]: FP64 device vectors of context k's finest level.  iters, relres: host arrays
+ * of nctx entries (may be NULL).  Status as chebmg_pcg_solve_batched. */
+int chebmg_group_pcg_solve(chebmg_group* group, const double* const* B, double* const* U,
+                           double rtol, int maxit, int flags, int* iters, double* relres);
+void chebmg_group_destroy(chebmg_group* group);
+
 /* ---- self-test -------------------------------------------------------------- */
 
 /* Failure-path self-test of the persistent SEM coarse solver (not part of the paper's

@@ -95,6 +95,16 @@ _SIGNATURES = {
                                       POINTER(c_int), POINTER(c_double)]),
     "chebmg_fd_smooth_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_int, c_double, c_double, c_void_p,
                                          c_void_p, c_int, c_void_p]),
+    "chebmg_pcg_solve_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_int,
+                                         POINTER(c_int), POINTER(c_double)]),
+    "chebmg_apply_A_batched": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "chebmg_vcycle_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "chebmg_batch_info": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_int), POINTER(c_int)]),
+    "chebmg_set_batch_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
+    "chebmg_group_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
+    "chebmg_group_pcg_solve": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_double, c_int, c_int,
+                                       POINTER(c_int), POINTER(c_double)]),
+    "chebmg_group_destroy": (None, [c_void_p]),
     "chebmg_selftest_coarse_timeout": (c_int, [c_void_p, POINTER(c_int)]),
     "chebmg_strerror": (ctypes.c_char_p, [c_int]),
     "chebmg_last_error": (ctypes.c_char_p, []),
@@ -294,6 +304,82 @@ def chebmg_pcg_solve_host(ctx, b_host: np.ndarray, u_host: np.ndarray, rtol=1e-8
                                               byref(it), byref(rel)),
                   "chebmg_pcg_solve_host", allow=(CHEBMG_ENOTCONV,))
     return code, it.value, rel.value
+
+
+CHEBMG_BATCH_GRAPH = 1
+
+
+def chebmg_pcg_solve_batched(ctx, B, U, rtol=1e-8, maxit=500, graph=True):
+    """B, U: contiguous FP64 CUDA tensors of shape (nrhs, n).  Returns (status, iterations[nrhs],
+    relres[nrhs]); raises on errors other than ENOTCONV."""
+    torch = _torch()
+    n = chebmg_level_size(ctx, 0)
+    if not isinstance(B, torch.Tensor) or B.dim() != 2 or B.shape[1] != n:
+        raise ValueError(f"B must have shape (nrhs, {n})")
+    nrhs = B.shape[0]
+    its, rel = (c_int * nrhs)(), (c_double * nrhs)()
+    code = _check(lib().chebmg_pcg_solve_batched(ctx, nrhs, _ptr(B, nrhs * n, CHEBMG_F64, "B"),
+                                                 _ptr(U, nrhs * n, CHEBMG_F64, "U"), float(rtol), int(maxit),
+                                                 CHEBMG_BATCH_GRAPH if graph else 0, its, rel),
+                  "chebmg_pcg_solve_batched", allow=(CHEBMG_ENOTCONV,))
+    return code, list(its), list(rel)
+
+
+def chebmg_apply_A_batched(ctx, level, dtype, X, Y):
+    """X, Y: contiguous CUDA tensors of shape (nrhs, n) of the dtype."""
+    n = chebmg_level_size(ctx, level)
+    if X.dim() != 2 or X.shape[1] != n:
+        raise ValueError(f"X must have shape (nrhs, {n})")
+    nrhs = X.shape[0]
+    _check(lib().chebmg_apply_A_batched(ctx, int(level), int(dtype), nrhs, _ptr(X, nrhs * n, dtype, "X"),
+                                        _ptr(Y, nrhs * n, dtype, "Y")), "chebmg_apply_A_batched")
+
+
+def chebmg_vcycle_batched(ctx, R, Z):
+    """R, Z: contiguous FP64 CUDA tensors of shape (nrhs, n)."""
+    n = chebmg_level_size(ctx, 0)
+    if R.dim() != 2 or R.shape[1] != n:
+        raise ValueError(f"R must have shape (nrhs, {n})")
+    nrhs = R.shape[0]
+    _check(lib().chebmg_vcycle_batched(ctx, nrhs, _ptr(R, nrhs * n, CHEBMG_F64, "R"),
+                                       _ptr(Z, nrhs * n, CHEBMG_F64, "Z")), "chebmg_vcycle_batched")
+
+
+def chebmg_batch_info(ctx, nrhs, level=0, dtype=CHEBMG_F64):
+    """(batched order-7 variant, coarse preconditioner degree) autotuned for batches of nrhs."""
+    v, m = c_int(), c_int()
+    _check(lib().chebmg_batch_info(ctx, int(nrhs), int(level), int(dtype), byref(v), byref(m)), "chebmg_batch_info")
+    return v.value, m.value
+
+
+def chebmg_set_batch_tile_choice(ctx, nrhs, level, dtype, variant):
+    _check(lib().chebmg_set_batch_tile_choice(ctx, int(nrhs), int(level), int(dtype), int(variant)),
+           "chebmg_set_batch_tile_choice")
+
+
+def chebmg_group_create(ctxs) -> c_void_p:
+    arr = (c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    g = c_void_p()
+    _check(lib().chebmg_group_create(arr, len(ctxs), byref(g)), "chebmg_group_create")
+    return g
+
+
+def chebmg_group_pcg_solve(group, ctxs, B, U, rtol=1e-8, maxit=500, graph=True):
+    """One right-hand side per context: B[k], U[k] FP64 CUDA vectors of context k's fine size."""
+    k = len(ctxs)
+    if len(B) != k or len(U) != k:
+        raise ValueError("one B and one U per context")
+    bp = (c_void_p * k)(*[_ptr(B[q], chebmg_level_size(ctxs[q], 0), CHEBMG_F64, "B").value for q in range(k)])
+    up = (c_void_p * k)(*[_ptr(U[q], chebmg_level_size(ctxs[q], 0), CHEBMG_F64, "U").value for q in range(k)])
+    its, rel = (c_int * k)(), (c_double * k)()
+    code = _check(lib().chebmg_group_pcg_solve(group, bp, up, float(rtol), int(maxit),
+                                               CHEBMG_BATCH_GRAPH if graph else 0, its, rel),
+                  "chebmg_group_pcg_solve", allow=(CHEBMG_ENOTCONV,))
+    return code, list(its), list(rel)
+
+
+def chebmg_group_destroy(group):
+    lib().chebmg_group_destroy(group)
 
 
 def chebmg_selftest_coarse_timeout(ctx) -> int:

@@ -92,7 +92,9 @@ struct Level {
   void* Jn[2] = {nullptr, nullptr};   // interpolation from level+1 to this level, [Qf][Qc]
   void* v[2][NV] = {{nullptr}};
   int eb[2] = {2, 2};   // variant of the order-7 operator, per dtype (autotuned)
+  int beb[2] = {2002, 2002};   // variant of the batched order-7 operator (autotuned per batch size)
   Lattice lat = {0, 0, 0, 0, 0, 0};
+  int64_t ld = 0;       // leading dimension of batched vectors: n rounded up to 64
 };
 
 }  // namespace chebmg
@@ -132,8 +134,26 @@ struct chebmg_ctx {
   int coarse_halo = 0;
   int coarse_degree = 1;        // 4th-kind polynomial preconditioner degree (autotuned)
   double coarse_lmax = 0.0;
-  unsigned* dstat = nullptr;    // [4] device-side error flags of the operator kernels
+  unsigned* dstat = nullptr;    // [4] device-side error flags: [0] operator wait, [1] batched coarse
   unsigned* hdstat = nullptr;
+  // ---- batches of right-hand sides ----
+  int nb = 1;                   // right-hand sides of the operation in progress
+  bool batched = false;         // inside a batched or grouped solve (device-side decisions only)
+  int64_t gen = 0;              // bumped whenever captured graphs of this context go stale
+  int bcap = 1;                 // capacity of the work vectors (right-hand sides)
+  int btuned = 0;               // batch size the batched variants were tuned for
+  double* kx = nullptr;         // batched FCG solution
+  double* bpart = nullptr;      // batched reduction partials
+  double* bscal = nullptr;      // [bcap][S_NSLOTS]
+  int* bstat = nullptr;         // [bcap][4]
+  double* hbscal = nullptr;
+  int* hbstat = nullptr;
+  unsigned* bcstat = nullptr;   // [bcap][2] batched coarse status
+  int bcoarse_degree = 1;
+  cudaStream_t gs = nullptr;    // private stream for graph capture
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int gexec_nb = 0;
+  int64_t glaunches[2] = {0, 0};   // kernels per replay of each graph
 };
 
 namespace {
@@ -160,6 +180,10 @@ template <typename T>
 const T* invD_of(const Level& L) {
   return static_cast<const T*>(L.invD[dt_of<T>()]);
 }
+
+// Leading dimension and total length of a level's work vectors for the current batch.
+int64_t ldv(const chebmg_ctx* c, const Level& L) { return c->nb > 1 ? L.ld : L.n; }
+int64_t span(const chebmg_ctx* c, const Level& L) { return c->nb > 1 ? (int64_t)c->nb * L.ld : L.n; }
 
 template <typename T>
 Stencil9<T> stencil(const Level& L) {
@@ -196,18 +220,28 @@ void read_cscal(chebmg_ctx* c) {
 
 // y = A x on level j; for SEM y must be zero on entry (element contributions accumulate).
 template <typename T>
-void apply_into(chebmg_ctx* c, int j, const T* x, T* y) {
+void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld) {
   Level& L = c->L[j];
   const int dt = dt_of<T>();
   if (L.type == TYPE_SEM) {
-    if (L.Q == 8)
+    if (L.Q == 8 && nb > 1)
+      sem_ax8_batched<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.beb[dt], nb, ld,
+                         c->s);
+    else if (L.Q == 8)
       sem_ax8<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s);
     else
-      sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s);
+      sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s, nb,
+                ld);
   } else {
-    fd_apply<T>(L.mx, L.my, stencil<T>(L), x, y, c->s);
+    fd_apply<T>(L.mx, L.my, stencil<T>(L), x, y, c->s, nb, ld);
   }
   check_launch();
+}
+
+// y = A x on level j for the current batch (y zero on entry for SEM).
+template <typename T>
+void apply_into(chebmg_ctx* c, int j, const T* x, T* y) {
+  apply_into_ld<T>(c, j, x, y, c->nb, ldv(c, c->L[j]));
 }
 
 template <typename T>
@@ -220,36 +254,38 @@ template <typename T>
 void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
   Level& L = c->L[j];
   const int64_t n = L.n;
+  const int nb = c->nb;
+  const int64_t ld = ldv(c, L);
   T* r = vec<T>(L, VR);
   T* d = vec<T>(L, VD);
   T* y = vec<T>(L, VY);
   const T* S = invD_of<T>(L);
   const double lmax = L.lmax;
-  zero<T>(c, y, n);
+  zero<T>(c, y, span(c, L));
   if (!x_zero) apply_into<T>(c, j, x, y);
   if (c->o.kind == CHEBMG_CHEB_1ST) {
     const double lmin = c->o.lmin_ratio * lmax;
     const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
     const double sigma = theta / delta;
     double rho = 1.0 / sigma;
-    cheb1_init<T>(n, b, x, r, d, y, S, 1.0 / theta, x_zero ? 1 : 0, c->s);
+    cheb1_init<T>(n, b, x, r, d, y, S, 1.0 / theta, x_zero ? 1 : 0, c->s, nb, ld);
     for (int i = 1; i < order; ++i) {
       apply_into<T>(c, j, d, y);
       const double rho_new = 1.0 / (2.0 * sigma - rho);
-      cheb1_step<T>(n, x, r, d, y, S, rho_new * rho, 2.0 * rho_new / delta, c->s);
+      cheb1_step<T>(n, x, r, d, y, S, rho_new * rho, 2.0 * rho_new / delta, c->s, nb, ld);
       rho = rho_new;
     }
-    axpy<T>(n, 1.0, d, x, c->s);
+    axpy<T>(n, 1.0, d, x, c->s, nb, ld);
   } else {
     const double* beta = (c->o.kind == CHEBMG_CHEB_4TH_OPT) ? kBeta[order - 1] : nullptr;
-    cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), x_zero ? 1 : 0, c->s);
+    cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), x_zero ? 1 : 0, c->s, nb, ld);
     for (int i = 1; i < order; ++i) {
       apply_into<T>(c, j, d, y);
       const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0);
       const double c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lmax);
-      cheb4_step<T>(n, x, r, d, y, S, beta ? beta[i - 1] : 1.0, c1, c2, c->s);
+      cheb4_step<T>(n, x, r, d, y, S, beta ? beta[i - 1] : 1.0, c1, c2, c->s, nb, ld);
     }
-    axpy<T>(n, beta ? beta[order - 1] : 1.0, d, x, c->s);
+    axpy<T>(n, beta ? beta[order - 1] : 1.0, d, x, c->s, nb, ld);
   }
   check_launch();
 }
@@ -260,14 +296,16 @@ void restrict_to(chebmg_ctx* c, int j, const T* rf, T* rc) {
   Level& F = c->L[j];
   Level& C = c->L[j + 1];
   const int dt = dt_of<T>();
+  const int nb = c->nb;
+  const int64_t ldf = ldv(c, F), ldc = ldv(c, C);
   if (F.type == TYPE_SEM) {
-    zero<T>(c, rc, C.n);
+    zero<T>(c, rc, span(c, C));
     if (transfer_box_supported(F.Q, C.Q))
-      restrict_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, rf, rc, c->s);
+      restrict_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, rf, rc, c->s, nb, ldf, ldc);
     else
-      sem_restrict<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), rf, rc, c->s);
+      sem_restrict<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), rf, rc, c->s, nb, ldf, ldc);
   } else {
-    fd_restrict<T>(F.mx, F.my, C.mx, C.my, F.c_next, rf, rc, c->s);
+    fd_restrict<T>(F.mx, F.my, C.mx, C.my, F.c_next, rf, rc, c->s, nb, ldf, ldc);
   }
   check_launch();
 }
@@ -278,13 +316,16 @@ void prolong_to(chebmg_ctx* c, int j, const T* zc, T* zf, int accumulate) {
   Level& F = c->L[j];
   Level& C = c->L[j + 1];
   const int dt = dt_of<T>();
+  const int nb = c->nb;
+  const int64_t ldf = ldv(c, F), ldc = ldv(c, C);
   if (F.type == TYPE_SEM) {
     if (transfer_box_supported(F.Q, C.Q))
-      prolong_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, zc, zf, accumulate, c->s);
+      prolong_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, zc, zf, accumulate, c->s, nb, ldf, ldc);
     else
-      sem_prolong<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), zc, zf, accumulate, c->s);
+      sem_prolong<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), zc, zf, accumulate, c->s, nb,
+                     ldf, ldc);
   } else {
-    fd_prolong<T>(F.mx, F.my, C.mx, C.my, F.c_next, zc, zf, accumulate, c->s);
+    fd_prolong<T>(F.mx, F.my, C.mx, C.my, F.c_next, zc, zf, accumulate, c->s, nb, ldf, ldc);
   }
   check_launch();
 }
@@ -374,15 +415,61 @@ int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {
   return CHEBMG_ENOTCONV;
 }
 
+// Whether the coarse solve of a batch runs without host decisions (so it can be captured).
+bool coarse_batch_capturable(const chebmg_ctx* c) {
+  const Level& C = c->L.back();
+  return C.type == TYPE_FD || (c->ell_col && coarse_block_supported(C.n));
+}
+
+// FP64 coarse solve of the current batch (c->nb right-hand sides at the coarse leading dimension).
+int coarse_solve64_batched(chebmg_ctx* c, const double* b, double* x) {
+  Level& C = c->L.back();
+  const int64_t ld = ldv(c, C);
+  if (C.type == TYPE_FD) {
+    dense_matvec((int)C.n, c->cinv, b, x, c->s, c->nb, ld);
+    check_launch();
+    return CHEBMG_OK;
+  }
+  if (coarse_block_supported(C.n)) {
+    CoarseBlock a;
+    a.n = C.n;
+    a.nslot = c->nslot;
+    a.col = c->ell_col;
+    a.val = c->ell_val;
+    a.invD = static_cast<const double*>(C.invD[CHEBMG_F64]);
+    a.b = b;
+    a.x = x;
+    a.ld = ld;
+    a.rtol = c->o.coarse_rtol;
+    a.maxit = c->o.coarse_maxit;
+    a.degree = c->bcoarse_degree;
+    a.lmax = c->coarse_lmax > 0.0 ? c->coarse_lmax : 1.0;
+    a.stat = c->bcstat;
+    a.sticky = c->dstat + 1;
+    if (!coarse_block_launch(a, c->nb, c->s)) throw Error(CHEBMG_ECUDA, "batched coarse launch failed");
+    check_launch();
+    return CHEBMG_OK;
+  }
+  // larger coarse problems: one persistent solve per right-hand side
+  const int nb = c->nb;
+  c->nb = 1;
+  int rc = CHEBMG_OK;
+  for (int q = 0; q < nb && (rc == CHEBMG_OK || rc == CHEBMG_ENOTCONV); ++q)
+    rc = coarse_solve64(c, b + q * ld, x + q * ld);
+  c->nb = nb;
+  return rc;
+}
+
 template <typename T>
 int coarse(chebmg_ctx* c, const T* b, T* x) {
   if constexpr (sizeof(T) == 8) {
-    return coarse_solve64(c, b, x);
+    return c->batched ? coarse_solve64_batched(c, b, x) : coarse_solve64(c, b, x);
   } else {
     Level& C = c->L.back();
-    cast<float, double>(C.n, b, c->cb, c->s);
-    int rc = coarse_solve64(c, c->cb, c->cx);
-    cast<double, float>(C.n, c->cx, x, c->s);
+    const int64_t ld = ldv(c, C);
+    cast<float, double>(C.n, b, c->cb, c->s, c->nb, ld, ld);
+    int rc = c->batched ? coarse_solve64_batched(c, c->cb, c->cx) : coarse_solve64(c, c->cb, c->cx);
+    cast<double, float>(C.n, c->cx, x, c->s, c->nb, ld, ld);
     check_launch();
     return rc;
   }
@@ -397,13 +484,13 @@ int vcycle_level(chebmg_ctx* c, int j, const T* b, T* x) {
   if (c->pre > 0) {
     smooth<T>(c, j, b, x, c->pre, true);
   } else {
-    zero<T>(c, x, L.n);
+    zero<T>(c, x, span(c, L));
   }
   T* y = vec<T>(L, VY);
   T* r = vec<T>(L, VR);
-  zero<T>(c, y, L.n);
+  zero<T>(c, y, span(c, L));
   apply_into<T>(c, j, x, y);
-  residual<T>(L.n, b, y, r, c->s);
+  residual<T>(L.n, b, y, r, c->s, c->nb, ldv(c, L));
   restrict_to<T>(c, j, r, vec<T>(C, VB));
   int rc = vcycle_level<T>(c, j + 1, vec<T>(C, VB), vec<T>(C, VX));
   if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
@@ -414,14 +501,15 @@ int vcycle_level(chebmg_ctx* c, int j, const T* b, T* x) {
 }
 
 int vcycle_top(chebmg_ctx* c, const double* r, double* z) {
-  if (c->L.size() == 1) return coarse_solve64(c, r, z);
+  if (c->L.size() == 1) return coarse<double>(c, r, z);
   if (!c->fp32) return vcycle_level<double>(c, 0, r, z);
   Level& L = c->L[0];
   float* b32 = vec<float>(L, VB);
   float* x32 = vec<float>(L, VX);
-  cast<double, float>(L.n, r, b32, c->s);
+  const int64_t ld = ldv(c, L);
+  cast<double, float>(L.n, r, b32, c->s, c->nb, ld, ld);
   int rc = vcycle_level<float>(c, 0, b32, x32);
-  cast<float, double>(L.n, x32, z, c->s);
+  cast<float, double>(L.n, x32, z, c->s, c->nb, ld, ld);
   check_launch();
   return rc;
 }
@@ -497,9 +585,9 @@ double lanczos(chebmg_ctx* c, int j, int steps) {
 }
 
 void alloc_vectors(chebmg_ctx* c, Level& L, bool with32) {
-  for (int w = 0; w < NV; ++w) L.v[CHEBMG_F64][w] = dalloc<double>(c, L.n);
+  for (int w = 0; w < NV; ++w) L.v[CHEBMG_F64][w] = dalloc<double>(c, L.ld);
   if (with32)
-    for (int w = 0; w < NV; ++w) L.v[CHEBMG_F32][w] = dalloc<float>(c, L.n);
+    for (int w = 0; w < NV; ++w) L.v[CHEBMG_F32][w] = dalloc<float>(c, L.ld);
 }
 
 void common_alloc(chebmg_ctx* c) {
@@ -654,10 +742,10 @@ void finish_setup(chebmg_ctx* c) {
     if (!(lm > 0.0) || !std::isfinite(lm)) throw Error(CHEBMG_EBREAKDOWN, "non-positive lambda_max");
     c->L[j].lmax = lm;
   }
-  if (c->coop_ok) {
+  if (c->ell_col) {
     // lambda_max of S A on the coarse level (same Lanczos), then the preconditioner degree
-    c->coarse_lmax = lanczos(c, nl - 1, c->o.lanczos_steps);
-    autotune_coarse_degree(c);
+    c->coarse_lmax = lanczos(c, nl - 1, c->o.lanczos_steps >= 1 ? c->o.lanczos_steps : 30);
+    if (c->coop_ok) autotune_coarse_degree(c);
   }
   CK(cudaStreamSynchronize(c->s));
 }
@@ -707,6 +795,11 @@ void destroy_ctx(chebmg_ctx* c) {
   if (c->hcscal) cudaFreeHost(c->hcscal);
   if (c->hcctl) cudaFreeHost(c->hcctl);
   if (c->hdstat) cudaFreeHost(c->hdstat);
+  if (c->hbscal) cudaFreeHost(c->hbscal);
+  if (c->hbstat) cudaFreeHost(c->hbstat);
+  for (auto& g : c->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  if (c->gs) cudaStreamDestroy(c->gs);
   delete c;
 }
 
@@ -739,6 +832,497 @@ void check_dtype(chebmg_ctx* c, int dtype) {
 void enter(chebmg_ctx* c) {
   if (!c) throw Error(CHEBMG_EINVAL, "ctx is NULL");
   CK(cudaSetDevice(c->dev));
+}
+
+// ===========================================================================
+// Batches of right-hand sides
+// ===========================================================================
+void replace_alloc(chebmg_ctx* c, void*& p, size_t bytes) {
+  if (p) {
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    CK(cudaFree(p));
+    p = nullptr;
+  }
+  CK(cudaMalloc(&p, std::max<size_t>(bytes, 8)));
+  c->allocs.push_back(p);
+}
+template <typename T>
+void replace_vec(chebmg_ctx* c, T*& p, int64_t count) {
+  void* v = p;
+  replace_alloc(c, v, sizeof(T) * (size_t)count);
+  p = static_cast<T*>(v);
+}
+
+void drop_graphs(chebmg_ctx* c) {
+  for (auto& g : c->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  c->gexec_nb = 0;
+  ++c->gen;
+}
+
+// Grows every work vector to `nrhs` right-hand sides at the levels' leading dimensions and
+// allocates the per-right-hand-side scalars and status words.
+void reserve_batch(chebmg_ctx* c, int nrhs) {
+  if (nrhs <= c->bcap && c->bscal) return;
+  const int cap = std::max(nrhs, c->bcap);
+  CK(cudaStreamSynchronize(c->s));
+  drop_graphs(c);
+  if (cap > c->bcap) {
+    for (Level& L : c->L)
+      for (int dt = 0; dt < 2; ++dt)
+        for (int w = 0; w < NV; ++w)
+          if (L.v[dt][w]) replace_alloc(c, L.v[dt][w], (dt == CHEBMG_F64 ? 8 : 4) * (size_t)cap * L.ld);
+    const int64_t ld0 = c->L[0].ld, ldc = c->L.back().ld;
+    for (double** p : {&c->kr, &c->kz, &c->kp, &c->kq, &c->kro}) replace_vec(c, *p, (int64_t)cap * ld0);
+    for (double** p : {&c->cb, &c->cx}) replace_vec(c, *p, (int64_t)cap * ldc);
+  }
+  const int64_t ld0 = c->L[0].ld;
+  replace_vec(c, c->kx, (int64_t)cap * ld0);
+  replace_vec(c, c->bpart, 2 * (int64_t)cap * std::max(bred_blocks(c->L[0].n), bred_blocks(c->L.back().n)));
+  replace_vec(c, c->bscal, (int64_t)cap * S_NSLOTS);
+  replace_vec(c, c->bstat, (int64_t)cap * 4);
+  replace_vec(c, c->bcstat, (int64_t)cap * 2);
+  CK(cudaMemsetAsync(c->bscal, 0, sizeof(double) * cap * S_NSLOTS, c->s));
+  CK(cudaMemsetAsync(c->bstat, 0, sizeof(int) * cap * 4, c->s));
+  CK(cudaMemsetAsync(c->bcstat, 0, sizeof(unsigned) * cap * 2, c->s));
+  if (c->hbscal) cudaFreeHost(c->hbscal);
+  if (c->hbstat) cudaFreeHost(c->hbstat);
+  c->hbscal = nullptr;
+  c->hbstat = nullptr;
+  void* h = nullptr;
+  CK(cudaMallocHost(&h, sizeof(double) * cap * S_NSLOTS));
+  c->hbscal = static_cast<double*>(h);
+  CK(cudaMallocHost(&h, sizeof(int) * cap * 4));
+  c->hbstat = static_cast<int*>(h);
+  c->bcap = cap;
+  CK(cudaStreamSynchronize(c->s));
+}
+
+// Times the batched order-7 variants (elements per block x right-hand sides per block x id
+// source) and the batched coarse preconditioner degree on the context's own data for a batch
+// of nrhs right-hand sides -- run once per batch size.
+void autotune_batch(chebmg_ctx* c, int nrhs) {
+  if (c->btuned == nrhs) return;
+  drop_graphs(c);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& fn, int reps) {
+    fn();
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      CK(cudaEventRecord(e0, c->s));
+      fn();
+      CK(cudaEventRecord(e1, c->s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  const int saved_nb = c->nb;
+  const bool saved_batched = c->batched;
+  c->nb = nrhs;
+  c->batched = true;
+  if (nrhs > 1) {
+    for (int j = 0; j < (int)c->L.size(); ++j) {
+      Level& L = c->L[j];
+      if (L.type != TYPE_SEM || L.Q != 8) continue;
+      for (int dt = 0; dt < 2; ++dt) {
+        if (!L.G[dt]) continue;
+        void* x = L.v[dt][VB];
+        void* y = L.v[dt][VY];
+        const size_t es = dt == CHEBMG_F64 ? 8 : 4;
+        CK(cudaMemsetAsync(x, 0, es * (size_t)nrhs * L.ld, c->s));
+        float best = 1e30f;
+        int best_v = L.beb[dt];
+        for (int rb : {1, 2, 4, 8, 16}) {
+          if (rb > nrhs) break;
+          for (int eb : {1, 2, 4, 101, 102, 104}) {
+            const int v = 1000 * rb + eb;
+            if (dt == CHEBMG_F64 ? !sem_ax8_variant_fits<double>(eb % 100) : !sem_ax8_variant_fits<float>(eb % 100))
+              continue;
+            L.beb[dt] = v;
+            const float t = time_it(
+                [&]() {
+                  if (dt == CHEBMG_F64) apply_into<double>(c, j, static_cast<double*>(x), static_cast<double*>(y));
+                  else apply_into<float>(c, j, static_cast<float*>(x), static_cast<float*>(y));
+                },
+                2);
+            if (t < best) {
+              best = t;
+              best_v = v;
+            }
+          }
+        }
+        L.beb[dt] = best_v;
+        CK(cudaMemsetAsync(y, 0, es * (size_t)nrhs * L.ld, c->s));
+      }
+    }
+  }
+  Level& C = c->L.back();
+  if (C.type == TYPE_SEM && c->ell_col && coarse_block_supported(C.n)) {
+    const int64_t ldc = ldv(c, C);
+    splitmix_fill(C.n, 7ull, static_cast<const double*>(C.invD[CHEBMG_F64]), c->cb, c->s);
+    for (int q = 1; q < nrhs; ++q)
+      CK(cudaMemcpyAsync(c->cb + q * ldc, c->cb, sizeof(double) * C.n, cudaMemcpyDeviceToDevice, c->s));
+    std::vector<unsigned> st(2 * (size_t)nrhs);
+    float best = 1e30f;
+    int best_m = 1;
+    for (int m : {1, 2, 4, 8, 12, 16}) {
+      c->bcoarse_degree = m;
+      const float t = time_it([&]() { coarse_solve64_batched(c, c->cb, c->cx); }, 2);
+      CK(cudaMemcpy(st.data(), c->bcstat, sizeof(unsigned) * st.size(), cudaMemcpyDeviceToHost));
+      bool ok = true;
+      for (int q = 0; q < nrhs; ++q) ok = ok && st[2 * q] == CS_OK;
+      if (ok && t < best) {
+        best = t;
+        best_m = m;
+      }
+    }
+    c->bcoarse_degree = best_m;
+    CK(cudaMemsetAsync(c->dstat + 1, 0, sizeof(unsigned), c->s));
+  }
+  c->nb = saved_nb;
+  c->batched = saved_batched;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaStreamSynchronize(c->s));
+  c->btuned = nrhs;
+}
+
+// ---- batched flexible CG, split into launch sequences without host decisions ----
+void bfcg_start(chebmg_ctx* c, const double* B, int64_t ldb, double rtol) {
+  Level& L = c->L[0];
+  const int nb = c->nb;
+  const int64_t n = L.n, ld = ldv(c, L);
+  const double* S = static_cast<const double*>(L.invD[CHEBMG_F64]);
+  CK(cudaMemsetAsync(c->dstat, 0, sizeof(unsigned) * 2, c->s));
+  masked_copy(n, B, S, c->kr, c->s, nb, ldb, ld);
+  zero<double>(c, c->kx, span(c, L));
+  bdot2(n, ld, nb, c->kr, c->kr, nullptr, nullptr, BPOST_INIT, rtol, c->bpart, c->bscal, c->bstat, c->s);
+  const int rc = vcycle_top(c, c->kr, c->kz);
+  if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) throw Error(rc, "V-cycle failed");
+  CK(cudaMemcpyAsync(c->kp, c->kz, sizeof(double) * span(c, L), cudaMemcpyDeviceToDevice, c->s));
+  bdot2(n, ld, nb, c->kz, c->kr, nullptr, nullptr, BPOST_SET_RZ, 0.0, c->bpart, c->bscal, c->bstat, c->s);
+  check_launch();
+}
+
+// q = A p; alpha; x += alpha p; r -= alpha q; convergence test
+void bfcg_body1(chebmg_ctx* c) {
+  Level& L = c->L[0];
+  const int nb = c->nb;
+  const int64_t n = L.n, ld = ldv(c, L);
+  zero<double>(c, c->kq, span(c, L));
+  apply_into<double>(c, 0, c->kp, c->kq);
+  bdot2(n, ld, nb, c->kp, c->kq, nullptr, nullptr, BPOST_ALPHA, 0.0, c->bpart, c->bscal, c->bstat, c->s);
+  bfcg_update_xr(n, ld, nb, c->kx, c->kr, c->kro, c->kp, c->kq, c->bpart, c->bscal, c->bstat, c->s);
+  check_launch();
+}
+
+// z = V-cycle(r); Polak-Ribiere beta; p = z + beta p
+void bfcg_body2(chebmg_ctx* c) {
+  Level& L = c->L[0];
+  const int nb = c->nb;
+  const int64_t n = L.n, ld = ldv(c, L);
+  const int rc = vcycle_top(c, c->kr, c->kz);
+  if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) throw Error(rc, "V-cycle failed");
+  bdot2(n, ld, nb, c->kz, c->kr, c->kz, c->kro, BPOST_BETA, 0.0, c->bpart, c->bscal, c->bstat, c->s);
+  bupdate_p(n, ld, nb, c->kz, c->kp, c->bscal, c->s);
+  check_launch();
+}
+
+// Queues the read-back of the status words (and device error flags) on stream s.
+void bfcg_queue_read(chebmg_ctx* c, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->hbstat, c->bstat, sizeof(int) * 4 * c->nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->hdstat, c->dstat, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, s));
+}
+
+int bfcg_active(const chebmg_ctx* c) {
+  int a = 0;
+  for (int q = 0; q < c->nb; ++q) a += c->hbstat[4 * q] != 0;
+  return a;
+}
+
+// Copies the solutions out and fills the per-right-hand-side results; returns the worst status.
+int bfcg_finish(chebmg_ctx* c, double* U, int64_t ldu, int* iters, double* relres) {
+  Level& L = c->L[0];
+  cast<double, double>(L.n, c->kx, U, c->s, c->nb, ldv(c, L), ldu);
+  CK(cudaMemcpyAsync(c->hbscal, c->bscal, sizeof(double) * S_NSLOTS * c->nb, cudaMemcpyDeviceToHost, c->s));
+  bfcg_queue_read(c, c->s);
+  CK(cudaStreamSynchronize(c->s));
+  check_launch();
+  int worst = CHEBMG_OK;
+  for (int q = 0; q < c->nb; ++q) {
+    const double* sc = c->hbscal + q * S_NSLOTS;
+    const int* st = c->hbstat + 4 * q;
+    if (iters) iters[q] = st[1];
+    if (relres) relres[q] = sc[S_BB] > 0.0 ? std::sqrt(sc[S_RR] / sc[S_BB]) : 0.0;
+    int rc = CHEBMG_OK;
+    if (st[2] == BS_BREAKDOWN) rc = CHEBMG_EBREAKDOWN;
+    else if (st[0] != 0 || st[2] != BS_OK) rc = CHEBMG_ENOTCONV;
+    if (rc == CHEBMG_EBREAKDOWN || (rc == CHEBMG_ENOTCONV && worst == CHEBMG_OK)) worst = rc;
+  }
+  if (c->hdstat[0]) return CHEBMG_ETIMEOUT;
+  if (c->hdstat[1] == CS_BREAKDOWN) return CHEBMG_EBREAKDOWN;
+  return worst;
+}
+
+// Captures fn (a launch sequence on c->s) into an executable graph; launches counted per replay.
+template <typename F>
+cudaGraphExec_t capture(chebmg_ctx* c, F&& fn, int64_t* launches) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+  const int64_t l0 = g_launches.load();
+  try {
+    fn();
+  } catch (...) {
+    cudaStreamEndCapture(c->s, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  const int64_t l1 = g_launches.load();
+  CK(cudaStreamEndCapture(c->s, &g));
+  g_launches.fetch_sub(l1 - l0);
+  *launches = l1 - l0;
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) throw Error(CHEBMG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return ex;
+}
+
+void replay(chebmg_ctx* c, int k) {
+  CK(cudaGraphLaunch(c->gexec[k], c->s));
+  g_launches.fetch_add(c->glaunches[k]);
+}
+
+// Runs on the context's private stream (needed for capture) and restores the caller's stream.
+struct PrivateStream {
+  chebmg_ctx* c;
+  cudaStream_t saved;
+  explicit PrivateStream(chebmg_ctx* cc) : c(cc), saved(cc->s) {
+    if (!c->gs) CK(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(saved));
+    c->s = c->gs;
+  }
+  ~PrivateStream() {
+    cudaStreamSynchronize(c->gs);
+    c->s = saved;
+  }
+};
+
+struct BatchScope {
+  chebmg_ctx* c;
+  BatchScope(chebmg_ctx* cc, int nb) : c(cc) {
+    c->nb = nb;
+    c->batched = true;
+  }
+  ~BatchScope() {
+    c->nb = 1;
+    c->batched = false;
+  }
+};
+
+int pcg_batched(chebmg_ctx* c, int nrhs, const double* B, int64_t ldb, double* U, int64_t ldu, double rtol,
+                int maxit, int* iters, double* relres, bool graphs) {
+  reserve_batch(c, nrhs);
+  autotune_batch(c, nrhs);
+  PrivateStream ps(c);
+  BatchScope bs(c, nrhs);
+  const bool use_graph = graphs && coarse_batch_capturable(c);
+  bfcg_start(c, B, ldb, rtol);
+  bfcg_queue_read(c, c->s);
+  CK(cudaStreamSynchronize(c->s));
+  if (bfcg_active(c) == 0 || maxit == 0) return bfcg_finish(c, U, ldu, iters, relres);
+  if (use_graph && c->gexec_nb != nrhs) {
+    drop_graphs(c);
+    // first iteration eagerly (first-launch configuration happens outside capture)
+    bfcg_body1(c);
+    bfcg_queue_read(c, c->s);
+    CK(cudaStreamSynchronize(c->s));
+    if (bfcg_active(c) == 0 || maxit == 1) return bfcg_finish(c, U, ldu, iters, relres);
+    bfcg_body2(c);
+    c->gexec[0] = capture(c, [&]() { bfcg_body1(c); }, &c->glaunches[0]);
+    c->gexec[1] = capture(c, [&]() { bfcg_body2(c); }, &c->glaunches[1]);
+    c->gexec_nb = nrhs;
+    for (int it = 2; it <= maxit; ++it) {
+      replay(c, 0);
+      bfcg_queue_read(c, c->s);
+      CK(cudaStreamSynchronize(c->s));
+      if (bfcg_active(c) == 0 || c->hdstat[0]) break;
+      if (it < maxit) replay(c, 1);
+    }
+    return bfcg_finish(c, U, ldu, iters, relres);
+  }
+  for (int it = 1; it <= maxit; ++it) {
+    if (use_graph) replay(c, 0);
+    else bfcg_body1(c);
+    bfcg_queue_read(c, c->s);
+    CK(cudaStreamSynchronize(c->s));
+    if (bfcg_active(c) == 0 || c->hdstat[0]) break;
+    if (it < maxit) {
+      if (use_graph) replay(c, 1);
+      else bfcg_body2(c);
+    }
+  }
+  return bfcg_finish(c, U, ldu, iters, relres);
+}
+
+}  // namespace
+
+// A fixed set of contexts (meshes of different sizes and orders) solved together: one
+// right-hand side each, every context on its own stream, each Krylov half-iteration of all
+// of them captured as one CUDA graph (fork/join over the contexts' streams).
+struct chebmg_group {
+  std::vector<chebmg_ctx*> c;
+  int dev = 0;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t g[2] = {nullptr, nullptr};
+  int64_t launches[2] = {0, 0};
+  std::vector<int64_t> gens;   // contexts' graph generations when captured
+};
+
+namespace {
+
+void group_drop(chebmg_group* g) {
+  for (auto& x : g->g)
+    if (x) {
+      cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+  g->gens.clear();
+}
+
+// Every context on its private stream in batched mode with one right-hand side; restored on exit.
+struct GroupScope {
+  chebmg_group* g;
+  std::vector<cudaStream_t> saved;
+  explicit GroupScope(chebmg_group* gg) : g(gg) {
+    for (chebmg_ctx* c : g->c) {
+      if (!c->gs) CK(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
+      CK(cudaStreamSynchronize(c->s));
+      saved.push_back(c->s);
+      c->s = c->gs;
+      c->nb = 1;
+      c->batched = true;
+    }
+  }
+  ~GroupScope() {
+    for (size_t k = 0; k < saved.size(); ++k) {
+      chebmg_ctx* c = g->c[k];
+      cudaStreamSynchronize(c->gs);
+      c->s = saved[k];
+      c->nb = 1;
+      c->batched = false;
+    }
+  }
+};
+
+template <typename F>
+cudaGraphExec_t group_capture(chebmg_group* g, F&& body, int64_t* launches) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
+  const int64_t l0 = g_launches.load();
+  try {
+    CK(cudaEventRecord(g->fork, g->s));
+    for (size_t k = 0; k < g->c.size(); ++k) {
+      chebmg_ctx* c = g->c[k];
+      CK(cudaStreamWaitEvent(c->s, g->fork, 0));
+      body(c);
+      CK(cudaEventRecord(g->join[k], c->s));
+      CK(cudaStreamWaitEvent(g->s, g->join[k], 0));
+    }
+  } catch (...) {
+    cudaStreamEndCapture(g->s, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  const int64_t l1 = g_launches.load();
+  CK(cudaStreamEndCapture(g->s, &graph));
+  g_launches.fetch_sub(l1 - l0);
+  *launches = l1 - l0;
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) throw Error(CHEBMG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return ex;
+}
+
+int group_active(chebmg_group* g, cudaStream_t s) {
+  for (chebmg_ctx* c : g->c) bfcg_queue_read(c, s ? s : c->s);
+  if (s) CK(cudaStreamSynchronize(s));
+  else
+    for (chebmg_ctx* c : g->c) CK(cudaStreamSynchronize(c->s));
+  int a = 0;
+  for (chebmg_ctx* c : g->c) {
+    if (c->hdstat[0]) return 0;
+    a += bfcg_active(c);
+  }
+  return a;
+}
+
+int group_solve(chebmg_group* g, const double* const* B, double* const* U, double rtol, int maxit, bool graphs,
+                int* iters, double* relres) {
+  for (chebmg_ctx* c : g->c) {
+    reserve_batch(c, 1);
+    autotune_batch(c, 1);
+  }
+  bool use_graph = graphs;
+  for (chebmg_ctx* c : g->c) use_graph = use_graph && coarse_batch_capturable(c);
+  if (use_graph && !g->gens.empty())
+    for (size_t k = 0; k < g->c.size(); ++k)
+      if (g->gens[k] != g->c[k]->gen) group_drop(g);
+  GroupScope scope(g);
+  auto finish = [&]() {
+    int worst = CHEBMG_OK;
+    for (size_t k = 0; k < g->c.size(); ++k) {
+      const int rc = bfcg_finish(g->c[k], U[k], g->c[k]->L[0].n, iters ? iters + k : nullptr,
+                                 relres ? relres + k : nullptr);
+      if (rc == CHEBMG_ETIMEOUT || rc == CHEBMG_EBREAKDOWN) worst = rc;
+      else if (rc != CHEBMG_OK && worst == CHEBMG_OK) worst = rc;
+    }
+    return worst;
+  };
+  for (size_t k = 0; k < g->c.size(); ++k) bfcg_start(g->c[k], B[k], g->c[k]->L[0].n, rtol);
+  if (group_active(g, nullptr) == 0 || maxit == 0) return finish();
+  int it = 1;
+  if (use_graph && !g->g[0]) {
+    for (chebmg_ctx* c : g->c) bfcg_body1(c);   // first iteration eagerly
+    if (group_active(g, nullptr) == 0 || maxit == 1) return finish();
+    for (chebmg_ctx* c : g->c) bfcg_body2(c);
+    for (chebmg_ctx* c : g->c) CK(cudaStreamSynchronize(c->s));
+    g->g[0] = group_capture(g, [](chebmg_ctx* c) { bfcg_body1(c); }, &g->launches[0]);
+    g->g[1] = group_capture(g, [](chebmg_ctx* c) { bfcg_body2(c); }, &g->launches[1]);
+    g->gens.clear();
+    for (chebmg_ctx* c : g->c) g->gens.push_back(c->gen);
+    it = 2;
+  }
+  for (; it <= maxit; ++it) {
+    if (use_graph) {
+      CK(cudaGraphLaunch(g->g[0], g->s));
+      g_launches.fetch_add(g->launches[0]);
+      if (group_active(g, g->s) == 0) break;
+      if (it < maxit) {
+        CK(cudaGraphLaunch(g->g[1], g->s));
+        g_launches.fetch_add(g->launches[1]);
+      }
+    } else {
+      for (chebmg_ctx* c : g->c) bfcg_body1(c);
+      if (group_active(g, nullptr) == 0) break;
+      if (it < maxit)
+        for (chebmg_ctx* c : g->c) bfcg_body2(c);
+    }
+  }
+  if (use_graph) CK(cudaStreamSynchronize(g->s));
+  return finish();
 }
 
 }  // namespace
@@ -789,6 +1373,7 @@ int chebmg_setup_fd2d(int m, double Lx, double Ly, int coarsening, int coarsest,
         L.type = TYPE_FD;
         L.mx = L.my = sizes[j];
         L.n = (int64_t)sizes[j] * sizes[j];
+        L.ld = (L.n + 63) / 64 * 64;
         L.c_next = coarsening;
         std::memcpy(L.st, st, sizeof(st));
         std::vector<double> invd((size_t)L.n, 1.0 / st[4]);
@@ -846,6 +1431,7 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
         L.NP = h.NP;
         L.E = h.E;
         L.n = h.n;
+        L.ld = (L.n + 63) / 64 * 64;
         L.gid = dalloc<uint32_t>(c, (int64_t)h.gid.size());
         CK(cudaMemcpy(L.gid, h.gid.data(), sizeof(uint32_t) * h.gid.size(), cudaMemcpyHostToDevice));
         std::vector<double> invd((size_t)h.n, 0.0);
@@ -939,6 +1525,8 @@ int chebmg_coarse_info(const chebmg_ctx* c, int* degree, double* lmax) {
 int chebmg_set_coarse_degree(chebmg_ctx* c, int degree) {
   if (!c || degree < 1 || degree > 64) return CHEBMG_EINVAL;
   c->coarse_degree = degree;
+  c->bcoarse_degree = degree;
+  drop_graphs(c);
   return CHEBMG_OK;
 }
 
@@ -953,6 +1541,7 @@ int chebmg_set_tile_choice(chebmg_ctx* c, int level, int dtype, int variant) {
   const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(variant) : sem_ax8_variant_fits<float>(variant);
   if (!fits) return CHEBMG_EINVAL;
   L.eb[dtype] = variant;
+  drop_graphs(c);
   return CHEBMG_OK;
 }
 
@@ -1148,6 +1737,145 @@ int chebmg_pcg_solve_host(chebmg_ctx* c, const double* b_host, double* u_host, d
     CK(cudaStreamSynchronize(c->s));
     return rc;
   });
+}
+
+int chebmg_pcg_solve_batched(chebmg_ctx* c, int nrhs, const double* B, double* U, double rtol, int maxit,
+                             int flags, int* iters, double* relres) {
+  return guard([&]() -> int {
+    enter(c);
+    if (!B || !U || nrhs < 1 || nrhs > 65535 || maxit < 0 || !(rtol > 0.0) || (flags & ~CHEBMG_BATCH_GRAPH))
+      throw Error(CHEBMG_EINVAL, "bad batched solve arguments");
+    const int64_t n = c->L[0].n;
+    return pcg_batched(c, nrhs, B, n, U, n, rtol, maxit, iters, relres, (flags & CHEBMG_BATCH_GRAPH) != 0);
+  });
+}
+
+int chebmg_apply_A_batched(chebmg_ctx* c, int level, int dtype, int nrhs, const void* X, void* Y) {
+  return guard([&]() -> int {
+    enter(c);
+    Level& L = level_checked(c, level);
+    check_dtype(c, dtype);
+    if (!X || !Y || nrhs < 1 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "bad batched apply arguments");
+    if (dtype == CHEBMG_F32 && !L.G[CHEBMG_F32] && L.type == TYPE_SEM)
+      throw Error(CHEBMG_EINVAL, "no FP32 data on this level");
+    if (nrhs > 1) {
+      reserve_batch(c, nrhs);
+      autotune_batch(c, nrhs);
+    }
+    const size_t es = dtype == CHEBMG_F64 ? 8 : 4;
+    CK(cudaMemsetAsync(Y, 0, es * (size_t)nrhs * L.n, c->s));
+    if (dtype == CHEBMG_F64)
+      apply_into_ld<double>(c, level, static_cast<const double*>(X), static_cast<double*>(Y), nrhs, L.n);
+    else
+      apply_into_ld<float>(c, level, static_cast<const float*>(X), static_cast<float*>(Y), nrhs, L.n);
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_vcycle_batched(chebmg_ctx* c, int nrhs, const double* R, double* Z) {
+  return guard([&]() -> int {
+    enter(c);
+    if (!R || !Z || nrhs < 1 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "bad batched V-cycle arguments");
+    reserve_batch(c, nrhs);
+    autotune_batch(c, nrhs);
+    Level& L = c->L[0];
+    BatchScope bs(c, nrhs);
+    CK(cudaMemsetAsync(c->dstat, 0, sizeof(unsigned) * 2, c->s));
+    cast<double, double>(L.n, R, c->kr, c->s, nrhs, L.n, L.ld);
+    int rc = vcycle_top(c, c->kr, c->kz);
+    cast<double, double>(L.n, c->kz, Z, c->s, nrhs, L.ld, L.n);
+    check_launch();
+    CK(cudaMemcpyAsync(c->hdstat, c->dstat, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (c->hdstat[0]) return CHEBMG_ETIMEOUT;
+    if (c->hdstat[1] == CS_BREAKDOWN) return CHEBMG_EBREAKDOWN;
+    return rc == CHEBMG_ENOTCONV ? CHEBMG_OK : rc;
+  });
+}
+
+int chebmg_batch_info(chebmg_ctx* c, int nrhs, int level, int dtype, int* variant, int* coarse_degree) {
+  return guard([&]() -> int {
+    enter(c);
+    Level& L = level_checked(c, level);
+    check_dtype(c, dtype);
+    if (!variant || !coarse_degree || nrhs < 1 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "bad arguments");
+    reserve_batch(c, nrhs);
+    autotune_batch(c, nrhs);
+    *variant = (L.type == TYPE_SEM && L.Q == 8 && nrhs > 1) ? L.beb[dtype] : 0;
+    *coarse_degree = (c->ell_col && coarse_block_supported(c->L.back().n)) ? c->bcoarse_degree : 0;
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_set_batch_tile_choice(chebmg_ctx* c, int nrhs, int level, int dtype, int variant) {
+  return guard([&]() -> int {
+    enter(c);
+    Level& L = level_checked(c, level);
+    check_dtype(c, dtype);
+    if (L.type != TYPE_SEM || L.Q != 8 || nrhs < 2 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "no batched variant");
+    const int rb = variant / 1000, rest = variant % 1000, eb = rest % 100;
+    if (rb < 1 || rb > 64 || (rest != eb && rest != eb + 100) || (eb != 1 && eb != 2 && eb != 4))
+      throw Error(CHEBMG_EINVAL, "bad batched variant");
+    const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(eb) : sem_ax8_variant_fits<float>(eb);
+    if (!fits || (dtype == CHEBMG_F32 && !L.G[CHEBMG_F32])) throw Error(CHEBMG_EINVAL, "variant not available");
+    reserve_batch(c, nrhs);
+    autotune_batch(c, nrhs);
+    L.beb[dtype] = variant;
+    drop_graphs(c);
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_group_create(chebmg_ctx* const* ctxs, int nctx, chebmg_group** out) {
+  return guard([&]() -> int {
+    if (!out) throw Error(CHEBMG_EINVAL, "group output is NULL");
+    *out = nullptr;
+    if (!ctxs || nctx < 1) throw Error(CHEBMG_EINVAL, "no contexts");
+    for (int k = 0; k < nctx; ++k) {
+      if (!ctxs[k]) throw Error(CHEBMG_EINVAL, "NULL context");
+      if (ctxs[k]->dev != ctxs[0]->dev) throw Error(CHEBMG_EINVAL, "contexts on different devices");
+      for (int q = 0; q < k; ++q)
+        if (ctxs[q] == ctxs[k]) throw Error(CHEBMG_EINVAL, "a context appears twice");
+    }
+    CK(cudaSetDevice(ctxs[0]->dev));
+    chebmg_group* g = new chebmg_group();
+    g->dev = ctxs[0]->dev;
+    g->c.assign(ctxs, ctxs + nctx);
+    g->join.assign(nctx, nullptr);
+    cudaError_t e = cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+    for (int k = 0; k < nctx && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&g->join[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      chebmg_group_destroy(g);
+      throw Error(CHEBMG_ECUDA, std::string("group resources: ") + cudaGetErrorString(e));
+    }
+    *out = g;
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_group_pcg_solve(chebmg_group* g, const double* const* B, double* const* U, double rtol, int maxit,
+                           int flags, int* iters, double* relres) {
+  return guard([&]() -> int {
+    if (!g || !B || !U || maxit < 0 || !(rtol > 0.0) || (flags & ~CHEBMG_BATCH_GRAPH))
+      throw Error(CHEBMG_EINVAL, "bad group solve arguments");
+    for (size_t k = 0; k < g->c.size(); ++k)
+      if (!B[k] || !U[k]) throw Error(CHEBMG_EINVAL, "NULL vector");
+    CK(cudaSetDevice(g->dev));
+    return group_solve(g, B, U, rtol, maxit, (flags & CHEBMG_BATCH_GRAPH) != 0, iters, relres);
+  });
+}
+
+void chebmg_group_destroy(chebmg_group* g) {
+  if (!g) return;
+  cudaSetDevice(g->dev);
+  if (g->s) cudaStreamSynchronize(g->s);
+  group_drop(g);
+  for (cudaEvent_t e : g->join)
+    if (e) cudaEventDestroy(e);
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->s) cudaStreamDestroy(g->s);
+  delete g;
 }
 
 int chebmg_selftest_coarse_timeout(chebmg_ctx* c, int* status) {

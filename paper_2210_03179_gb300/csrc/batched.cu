@@ -1,0 +1,417 @@
+// Batched Krylov kernels: the outer flexible CG (Polak-Ribiere) and the coarse-grid PCG run
+// on nb right-hand sides at once, each with its own scalars (Sec. 1: a sequence of Poisson
+// problems with the same operator, setup amortised over them).
+//
+// Layout: vector q of a batch starts at q * ld.  Per right-hand side the device keeps a row
+// of FP64 scalars (the Slot enum) and four status words: active, iterations, status, spare.
+// A right-hand side that has converged (or broken down) is frozen: its step length is zero,
+// so x and r no longer change while the others iterate, and the iteration counts equal those
+// of separate solves.  All decisions are taken on the device, so one Krylov iteration is a
+// fixed sequence of launches that a CUDA graph can capture.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "common.cuh"
+
+namespace chebmg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of two values over a block of kThreads; result in thread 0.
+__device__ __forceinline__ void bsum2(double& a, double& b) {
+  __shared__ double sa[kThreads / 32], sb[kThreads / 32];
+  a = wsum(a);
+  b = wsum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = l < kThreads / 32 ? sa[l] : 0.0;
+    b = l < kThreads / 32 ? sb[l] : 0.0;
+    a = wsum(a);
+    b = wsum(b);
+  }
+}
+
+__device__ __forceinline__ bool finite(double v) { return v == v && fabs(v) <= 1.79769313486231570e308; }
+
+// grid (nblk, nb): partial sums of (a0, b0) and (a1, b1) of right-hand side blockIdx.y
+__global__ void __launch_bounds__(kThreads)
+k_bdot2_partial(int64_t n, int64_t ld, int nblk, const double* __restrict__ a0, const double* __restrict__ b0,
+                const double* __restrict__ a1, const double* __restrict__ b1, double* __restrict__ part) {
+  const int64_t off = (int64_t)blockIdx.y * ld;
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)kThreads + threadIdx.x; g < n; g += (int64_t)nblk * kThreads) {
+    s0 += a0[off + g] * b0[off + g];
+    if (a1) s1 += a1[off + g] * b1[off + g];
+  }
+  bsum2(s0, s1);
+  if (threadIdx.x == 0) {
+    part[(2 * (int64_t)blockIdx.y) * nblk + blockIdx.x] = s0;
+    part[(2 * (int64_t)blockIdx.y + 1) * nblk + blockIdx.x] = s1;
+  }
+}
+
+__device__ void bpost(int post, double s0, double s1, double* sc, int* st, double rtol) {
+  switch (post) {
+    case BPOST_INIT:   // s0 = (b, b)
+      sc[S_BB] = s0;
+      sc[S_RR] = s0;
+      sc[S_T0] = rtol * rtol * s0;
+      st[1] = 0;
+      if (!finite(s0)) {
+        st[0] = 0;
+        st[2] = BS_BREAKDOWN;
+      } else if (s0 == 0.0) {
+        st[0] = 0;
+        st[2] = BS_OK;
+      } else {
+        st[0] = 1;
+        st[2] = BS_RUNNING;
+      }
+      break;
+    case BPOST_SET_RZ:   // s0 = (z, r)
+      sc[S_ZR] = s0;
+      sc[S_RZ] = s0;
+      break;
+    case BPOST_ALPHA: {   // s0 = (p, A p)
+      sc[S_PQ] = s0;
+      double alpha = 0.0;
+      if (st[0]) {
+        if (s0 > 0.0 && finite(s0)) {
+          alpha = sc[S_RZ] / s0;
+        } else {
+          st[0] = 0;
+          st[2] = BS_BREAKDOWN;
+          st[1] += 1;
+        }
+      }
+      sc[S_ALPHA] = alpha;
+      break;
+    }
+    case BPOST_CHECK:   // s0 = (r, r) after the update
+      if (st[0]) {
+        sc[S_RR] = s0;
+        st[1] += 1;
+        if (!finite(s0)) {
+          st[0] = 0;
+          st[2] = BS_BREAKDOWN;
+        } else if (s0 <= sc[S_T0]) {
+          st[0] = 0;
+          st[2] = BS_OK;
+        }
+      }
+      break;
+    case BPOST_BETA:   // s0 = (z, r_new), s1 = (z, r_old)
+      if (st[0]) {
+        sc[S_ZR] = s0;
+        sc[S_ZRO] = s1;
+        sc[S_BETA] = (s0 - s1) / sc[S_RZ];
+        sc[S_RZ] = s0;
+      } else {
+        sc[S_BETA] = 0.0;
+      }
+      break;
+    default: break;
+  }
+}
+
+// grid nb: fixed-order sum of the partials of right-hand side blockIdx.x, then the post-op
+__global__ void __launch_bounds__(kThreads)
+k_bdot2_finish(int nblk, int post, const double* __restrict__ part, double* __restrict__ scal,
+               int* __restrict__ stat, double rtol) {
+  const int64_t q = blockIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += kThreads) {
+    s0 += part[(2 * q) * nblk + k];
+    s1 += part[(2 * q + 1) * nblk + k];
+  }
+  bsum2(s0, s1);
+  if (threadIdx.x == 0) bpost(post, s0, s1, scal + q * S_NSLOTS, stat + q * 4, rtol);
+}
+
+// rold = r; x += alpha p; r -= alpha q; partial (r, r)   (alpha of each right-hand side)
+__global__ void __launch_bounds__(kThreads)
+k_bfcg_update_xr(int64_t n, int64_t ld, int nblk, double* __restrict__ x, double* __restrict__ r,
+                 double* __restrict__ rold, const double* __restrict__ p, const double* __restrict__ q,
+                 double* __restrict__ part, const double* __restrict__ scal) {
+  const int64_t off = (int64_t)blockIdx.y * ld;
+  const double alpha = scal[blockIdx.y * S_NSLOTS + S_ALPHA];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n; g += (int64_t)nblk * kThreads) {
+    const double rv = r[g];
+    rold[g] = rv;
+    x[g] += alpha * p[g];
+    const double rn = rv - alpha * q[g];
+    r[g] = rn;
+    s0 += rn * rn;
+  }
+  bsum2(s0, s1);
+  if (threadIdx.x == 0) {
+    part[(2 * (int64_t)blockIdx.y) * nblk + blockIdx.x] = s0;
+    part[(2 * (int64_t)blockIdx.y + 1) * nblk + blockIdx.x] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bupdate_p(int64_t n, int64_t ld, const double* __restrict__ z, double* __restrict__ p,
+            const double* __restrict__ scal) {
+  const int64_t off = (int64_t)blockIdx.y * ld;
+  const double beta = scal[blockIdx.y * S_NSLOTS + S_BETA];
+  for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n;
+       g += (int64_t)gridDim.x * kThreads)
+    p[g] = z[g] + beta * p[g];
+}
+
+// ---------------------------------------------------------------------------
+// Coarse PCG, one thread block per right-hand side.  The block keeps RPT rows per thread in
+// registers (rows tid, tid + blockDim, ...), the vector of each product in shared memory, and
+// reduces with warp shuffles; no grid-wide synchronisation, so any number of these blocks
+// (and other kernels) may run side by side.  Same method as the cooperative coarse kernel:
+// CG preconditioned by one degree-m application of Algorithm 2 (beta = 1) from a zero guess.
+// ---------------------------------------------------------------------------
+constexpr int kCBThreads = 512;
+constexpr int kCBMaxRows = 6;   // rows per thread (registers)
+
+// Sum of three values over the block; every thread gets the totals.
+__device__ __forceinline__ void cb_sum3(double& a, double& b, double& c) {
+  __shared__ double sh[3][kCBThreads / 32];
+  __shared__ double res[3];
+  a = wsum(a);
+  b = wsum(b);
+  c = wsum(c);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();   // previous readers of res are done
+  if (l == 0) {
+    sh[0][w] = a;
+    sh[1][w] = b;
+    sh[2][w] = c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double t0 = l < kCBThreads / 32 ? sh[0][l] : 0.0;
+    double t1 = l < kCBThreads / 32 ? sh[1][l] : 0.0;
+    double t2 = l < kCBThreads / 32 ? sh[2][l] : 0.0;
+    t0 = wsum(t0);
+    t1 = wsum(t1);
+    t2 = wsum(t2);
+    if (l == 0) {
+      res[0] = t0;
+      res[1] = t1;
+      res[2] = t2;
+    }
+  }
+  __syncthreads();
+  a = res[0];
+  b = res[1];
+  c = res[2];
+}
+
+template <int NS, int RPT>
+__device__ __forceinline__ void cb_spmv(const CoarseBlock& a, const double* sv, double (&y)[RPT]) {
+  const int64_t n = a.n;
+  const int ns = NS > 0 ? NS : a.nslot;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t g = threadIdx.x + (int64_t)q * kCBThreads;
+    double acc = 0.0;
+    if (g < n) {
+      if (NS > 0) {
+#pragma unroll
+        for (int k = 0; k < (NS > 0 ? NS : 1); ++k) acc += __ldg(&a.val[k * n + g]) * sv[__ldg(&a.col[k * n + g])];
+      } else {
+        for (int k = 0; k < ns; ++k) acc += __ldg(&a.val[k * n + g]) * sv[__ldg(&a.col[k * n + g])];
+      }
+    }
+    y[q] = acc;
+  }
+}
+
+template <int NS, int RPT>
+__global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
+  extern __shared__ double sv[];   // [n]: the vector of the current product
+  const int64_t n = a.n;
+  const int64_t off = (int64_t)blockIdx.x * a.ld;
+  const double* b = a.b + off;
+  double* xo = a.x + off;
+  double x[RPT], r[RPT], p[RPT], z[RPT], d[RPT], rp[RPT], y[RPT];
+  bool live[RPT];
+  // S = invD is re-read (L1) where needed instead of taking RPT more registers
+  auto Sv = [&](int q) { return live[q] ? __ldg(&a.invD[threadIdx.x + q * kCBThreads]) : 0.0; };
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t g = threadIdx.x + (int64_t)q * kCBThreads;
+    live[q] = g < n;
+    r[q] = (live[q] && Sv(q) != 0.0) ? b[g] : 0.0;
+    x[q] = p[q] = 0.0;
+  }
+  auto product = [&](const double (&v)[RPT]) {
+    __syncthreads();   // earlier readers of sv are done
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+      if (live[q]) sv[threadIdx.x + q * kCBThreads] = v[q];
+    __syncthreads();
+    cb_spmv<NS, RPT>(a, sv, y);
+  };
+  const double c0 = 4.0 / (3.0 * a.lmax);
+  auto precond = [&]() {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      rp[q] = r[q];
+      d[q] = c0 * Sv(q) * rp[q];
+      z[q] = 0.0;
+    }
+    for (int i = 1; i < a.degree; ++i) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) z[q] += d[q];
+      product(d);
+      const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0), c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        rp[q] -= y[q];
+        d[q] = c1 * d[q] + c2 * Sv(q) * rp[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) z[q] += d[q];
+  };
+  auto finish = [&](int status, int it) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+      if (live[q]) xo[threadIdx.x + q * kCBThreads] = x[q];
+    if (threadIdx.x == 0) {
+      a.stat[2 * blockIdx.x] = (unsigned)status;
+      a.stat[2 * blockIdx.x + 1] = (unsigned)it;
+      if (status == CS_BREAKDOWN) atomicMax((int*)a.sticky, (int)CS_BREAKDOWN);
+    }
+  };
+  precond();
+  double gam = 0.0, bb = 0.0, t = 0.0;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    p[q] = z[q];
+    gam += r[q] * z[q];
+    bb += r[q] * r[q];
+  }
+  cb_sum3(gam, bb, t);
+  if (!(bb > 0.0) || !(gam >= 0.0)) {
+    finish(bb == 0.0 ? CS_OK : CS_BREAKDOWN, 0);
+    return;
+  }
+  const double tol2 = a.rtol * a.rtol * bb;
+  for (int it = 1; it <= a.maxit; ++it) {
+    product(p);
+    double pq = 0.0, u1 = 0.0, u2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) pq += p[q] * y[q];
+    cb_sum3(pq, u1, u2);
+    if (!(pq > 0.0)) {
+      finish(CS_BREAKDOWN, it);
+      return;
+    }
+    const double alpha = gam / pq;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      x[q] = fma(alpha, p[q], x[q]);
+      r[q] = fma(-alpha, y[q], r[q]);
+    }
+    precond();
+    double gnew = 0.0, rr = 0.0;
+    u1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      gnew += r[q] * z[q];
+      rr += r[q] * r[q];
+    }
+    cb_sum3(gnew, rr, u1);
+    if (!(rr == rr)) {
+      finish(CS_BREAKDOWN, it);
+      return;
+    }
+    if (rr <= tol2) {
+      finish(CS_OK, it);
+      return;
+    }
+    const double beta = gnew / gam;
+    gam = gnew;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) p[q] = fma(beta, p[q], z[q]);
+  }
+  finish(CS_NOTCONV, a.maxit);
+}
+
+template <int NS>
+const void* cb_kernel(int rpt) {
+  switch (rpt) {
+    case 1: return (const void*)k_coarse_block<NS, 1>;
+    case 2: return (const void*)k_coarse_block<NS, 2>;
+    case 3: return (const void*)k_coarse_block<NS, 3>;
+    case 4: return (const void*)k_coarse_block<NS, 4>;
+    default: return (const void*)k_coarse_block<NS, 6>;
+  }
+}
+
+}  // namespace
+
+int bred_blocks(int64_t n) {
+  int64_t b = (n + 4095) / 4096;
+  if (b < 1) b = 1;
+  if (b > 256) b = 256;
+  return (int)b;
+}
+
+void bdot2(int64_t n, int64_t ld, int nb, const double* a0, const double* b0, const double* a1, const double* b1,
+           int post, double rtol, double* part, double* scal, int* stat, cudaStream_t s) {
+  const int nblk = bred_blocks(n);
+  k_bdot2_partial<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, a0, b0, a1, b1, part);
+  k_bdot2_finish<<<nb, kThreads, 0, s>>>(nblk, post, part, scal, stat, rtol);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+void bfcg_update_xr(int64_t n, int64_t ld, int nb, double* x, double* r, double* rold, const double* p,
+                    const double* q, double* part, double* scal, int* stat, cudaStream_t s) {
+  const int nblk = bred_blocks(n);
+  k_bfcg_update_xr<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, x, r, rold, p, q, part, scal);
+  k_bdot2_finish<<<nb, kThreads, 0, s>>>(nblk, BPOST_CHECK, part, scal, stat, 0.0);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+void bupdate_p(int64_t n, int64_t ld, int nb, const double* z, double* p, const double* scal, cudaStream_t s) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  if (g > 1024) g = 1024;
+  k_bupdate_p<<<dim3((unsigned)g, nb), kThreads, 0, s>>>(n, ld, z, p, scal);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+bool coarse_block_supported(int64_t n) { return n >= 1 && n <= (int64_t)kCBThreads * kCBMaxRows; }
+
+bool coarse_block_launch(const CoarseBlock& a, int nb, cudaStream_t s) {
+  if (!coarse_block_supported(a.n) || nb < 1) return false;
+  int rpt = (int)((a.n + kCBThreads - 1) / kCBThreads);
+  if (rpt > 4) rpt = 6;
+  const void* fn = a.nslot == 27 ? cb_kernel<27>(rpt) : cb_kernel<0>(rpt);
+  const size_t smem = sizeof(double) * (size_t)a.n;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return false;
+  }
+  CoarseBlock arg = a;
+  void* params[] = {&arg};
+  const cudaError_t e = cudaLaunchKernel(fn, dim3(nb), dim3(kCBThreads), params, smem, s);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e == cudaSuccess;
+}
+
+}  // namespace chebmg

@@ -36,15 +36,18 @@ struct Stencil9 {
 };
 
 // ---- SEM kernels (y must be zeroed by the caller; results accumulate) ----
+// Every operator, transfer and vector kernel also runs on a batch of nb right-hand sides:
+// vector b of the batch starts at offset b * ld (ld = 0 means n; per-node data shared).
 template <typename T>
 void sem_ax(int Q, int64_t E, const uint32_t* gid, const T* G, const T* D, const T* u, T* y,
-            cudaStream_t s);
+            cudaStream_t s, int nb = 1, int64_t ld = 0);
 template <typename T>
 void sem_restrict(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc,
-                  const T* J, const T* rf, T* rc, cudaStream_t s);
+                  const T* J, const T* rf, T* rc, cudaStream_t s, int nb = 1, int64_t ldf = 0, int64_t ldc = 0);
 template <typename T>
 void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc,
-                 const T* J, const T* zc, T* zf, int accumulate, cudaStream_t s);
+                 const T* J, const T* zc, T* zf, int accumulate, cudaStream_t s, int nb = 1, int64_t ldf = 0,
+                 int64_t ldc = 0);
 
 // Order-7 element operator (line passes, even-odd D, TMA-staged geometric factors).
 // sem_ax8_set_D uploads the even-odd blocks of the 8x8 GLL derivative matrix (row-major).
@@ -60,6 +63,12 @@ struct Lattice {
 template <typename T>
 void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
              unsigned* err, int variant, cudaStream_t s);
+// Batched form: nb right-hand sides at leading dimension ld.  variant = 1000 * RB + (100 if
+// implicit ids) + EB: a block stages the geometric factors of EB elements once and applies them
+// to RB right-hand sides.
+template <typename T>
+void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                     unsigned* err, int variant, int nb, int64_t ld, cudaStream_t s);
 // Whether variant `eb` fits the device's per-block shared-memory limit.
 template <typename T>
 bool sem_ax8_variant_fits(int eb);
@@ -69,48 +78,52 @@ cudaError_t transfer_box_set_J(int Qf, int Qc, const double* J);
 bool transfer_box_supported(int Qf, int Qc);
 template <typename T>
 void restrict_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* rf, T* rc,
-                  cudaStream_t s);
+                  cudaStream_t s, int nb = 1, int64_t ldf = 0, int64_t ldc = 0);
 template <typename T>
 void prolong_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* zc, T* zf,
-                 int accumulate, cudaStream_t s);
+                 int accumulate, cudaStream_t s, int nb = 1, int64_t ldf = 0, int64_t ldc = 0);
 
 // ---- FD kernels ----
 template <typename T>
-void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s);
+void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s, int nb = 1,
+              int64_t ld = 0);
 template <typename T>
-void fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* rf, T* rc, cudaStream_t s);
+void fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* rf, T* rc, cudaStream_t s, int nb = 1,
+                 int64_t ldf = 0, int64_t ldc = 0);
 template <typename T>
 void fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* zc, T* zf, int accumulate,
-                cudaStream_t s);
-void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s);
+                cudaStream_t s, int nb = 1, int64_t ldf = 0, int64_t ldc = 0);
+void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s, int nb = 1, int64_t ld = 0);
 
 // ---- Chebyshev recurrences (Algorithms 1 and 2), elementwise over n ----
 // 4th kind init: x_is_zero: x = 0, r = b; else r = b - y, y = 0.  d = c0 S r.
 template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0,
-                int x_is_zero, cudaStream_t s);
+                int x_is_zero, cudaStream_t s, int nb = 1, int64_t ld = 0);
 // 4th kind step: x += beta d; r -= y; d = c1 d + c2 S r; y = 0.
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1,
-                double c2, cudaStream_t s);
+                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0);
 // 1st kind init: r = S (b - y) (or S b), d = r / theta, y = 0 (x = 0 if x_is_zero).
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
-                int x_is_zero, cudaStream_t s);
+                int x_is_zero, cudaStream_t s, int nb = 1, int64_t ld = 0);
 // 1st kind step: x += d; r -= S y; d = c1 d + c2 r; y = 0.
 template <typename T>
 void cheb1_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double c1, double c2,
-                cudaStream_t s);
+                cudaStream_t s, int nb = 1, int64_t ld = 0);
 // x += a * d
 template <typename T>
-void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s);
+void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s, int nb = 1, int64_t ld = 0);
 // r = b - y; y = 0
 template <typename T>
-void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s);
+void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s, int nb = 1, int64_t ld = 0);
+// Batched forms: nb vectors at leading dimension ld (0 = n); per-node data (S) shared.
 template <typename Tin, typename Tout>
-void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s);
+void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s, int nb = 1, int64_t ldi = 0, int64_t ldo = 0);
 // out = mask(invD) ? in : 0   (mask: invD != 0)
-void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s);
+void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s, int nb = 1,
+                 int64_t ldi = 0, int64_t ldo = 0);
 
 // ---- FP64 reductions into scal[slot] (deterministic two-pass) ----
 // out slots: scal[slot0] = (a0, b0), scal[slot1] = (a1, b1) if a1 != nullptr; then post-op.
@@ -159,6 +172,48 @@ constexpr int kCoarseThreadsPerBlock = 256;
 bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err);
 // Grid size (blocks) and rows per block for a coarse problem of n rows; grid 0 = not possible.
 void coarse_pcg_shape(int64_t n, int* grid, int* rows_per_block);
+
+// ---- batched Krylov (batched.cu): nb right-hand sides at leading dimension ld ----
+// Per right-hand side: scal[q * S_NSLOTS + slot] and stat[q * 4 + {0 active, 1 iterations,
+// 2 status, 3 spare}].
+enum BatchStatus { BS_RUNNING = 0, BS_OK = 1, BS_NOTCONV = 2, BS_BREAKDOWN = 3 };
+enum BatchPost {
+  BPOST_NONE = 0,
+  BPOST_INIT,      // s0 = (b, b): BB, tolerance rtol^2 BB in S_T0, active unless b = 0
+  BPOST_SET_RZ,    // s0 = (z, r): ZR = RZ = s0
+  BPOST_ALPHA,     // s0 = (p, A p): ALPHA = RZ / PQ while active (breakdown freezes), else 0
+  BPOST_CHECK,     // s0 = (r, r): iteration count, converged when RR <= S_T0
+  BPOST_BETA       // s0 = (z, r), s1 = (z, r_old): Polak-Ribiere BETA while active, else 0
+};
+int bred_blocks(int64_t n);
+// part needs 2 * nb * bred_blocks(n) doubles
+void bdot2(int64_t n, int64_t ld, int nb, const double* a0, const double* b0, const double* a1, const double* b1,
+           int post, double rtol, double* part, double* scal, int* stat, cudaStream_t s);
+// rold = r; x += alpha p; r -= alpha q, then BPOST_CHECK on (r, r)
+void bfcg_update_xr(int64_t n, int64_t ld, int nb, double* x, double* r, double* rold, const double* p,
+                    const double* q, double* part, double* scal, int* stat, cudaStream_t s);
+// p = z + beta p
+void bupdate_p(int64_t n, int64_t ld, int nb, const double* z, double* p, const double* scal, cudaStream_t s);
+
+// Coarse PCG with one thread block per right-hand side (no grid-wide synchronisation).
+struct CoarseBlock {
+  int64_t n;
+  int nslot;
+  const int* col;        // ELL, slot-major
+  const double* val;
+  const double* invD;
+  const double* b;       // [nb][ld]
+  double* x;             // [nb][ld]
+  int64_t ld;
+  double rtol;
+  int maxit;
+  int degree;
+  double lmax;
+  unsigned* stat;        // [nb][2]: status (CoarseStatus), iterations
+  unsigned* sticky;      // worst error (atomicMax), reset by the caller
+};
+bool coarse_block_supported(int64_t n);
+bool coarse_block_launch(const CoarseBlock& a, int nb, cudaStream_t s);
 
 // ---- Lanczos helpers ----
 void splitmix_fill(int64_t n, uint64_t seed, const double* invD, double* v, cudaStream_t s);

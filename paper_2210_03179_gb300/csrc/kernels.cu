@@ -44,8 +44,10 @@ struct SemShape {
 template <typename T, int Q>
 __global__ void __launch_bounds__(SemShape<Q>::THREADS)
 k_sem_ax(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G,
-         const T* __restrict__ Dg, const T* __restrict__ u, T* __restrict__ y) {
+         const T* __restrict__ Dg, const T* __restrict__ u, T* __restrict__ y, int64_t ld) {
   constexpr int NP = SemShape<Q>::NP;
+  u += (int64_t)blockIdx.y * ld;   // right-hand side of a batch
+  y += (int64_t)blockIdx.y * ld;
   constexpr int EPB = SemShape<Q>::EPB;
   __shared__ T sD[Q * Q];
   __shared__ T s_u[EPB * NP];
@@ -98,26 +100,26 @@ k_sem_ax(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G,
 
 template <typename T, int Q>
 static void launch_sem_ax(int64_t E, const uint32_t* gid, const T* G, const T* D, const T* u, T* y,
-                          cudaStream_t s) {
+                          cudaStream_t s, int nb, int64_t ld) {
   using S = SemShape<Q>;
   const unsigned blocks = (unsigned)((E + S::EPB - 1) / S::EPB);
-  k_sem_ax<T, Q><<<blocks, S::THREADS, 0, s>>>(E, gid, G, D, u, y);
+  k_sem_ax<T, Q><<<dim3(blocks, nb), S::THREADS, 0, s>>>(E, gid, G, D, u, y, ld);
   count();
 }
 
 template <typename T>
 void sem_ax(int Q, int64_t E, const uint32_t* gid, const T* G, const T* D, const T* u, T* y,
-            cudaStream_t s) {
+            cudaStream_t s, int nb, int64_t ld) {
   switch (Q) {
-    case 2: launch_sem_ax<T, 2>(E, gid, G, D, u, y, s); break;
-    case 3: launch_sem_ax<T, 3>(E, gid, G, D, u, y, s); break;
-    case 4: launch_sem_ax<T, 4>(E, gid, G, D, u, y, s); break;
-    case 5: launch_sem_ax<T, 5>(E, gid, G, D, u, y, s); break;
-    case 6: launch_sem_ax<T, 6>(E, gid, G, D, u, y, s); break;
-    case 7: launch_sem_ax<T, 7>(E, gid, G, D, u, y, s); break;
-    case 8: launch_sem_ax<T, 8>(E, gid, G, D, u, y, s); break;
-    case 9: launch_sem_ax<T, 9>(E, gid, G, D, u, y, s); break;
-    case 10: launch_sem_ax<T, 10>(E, gid, G, D, u, y, s); break;
+    case 2: launch_sem_ax<T, 2>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 3: launch_sem_ax<T, 3>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 4: launch_sem_ax<T, 4>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 5: launch_sem_ax<T, 5>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 6: launch_sem_ax<T, 6>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 7: launch_sem_ax<T, 7>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 8: launch_sem_ax<T, 8>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 9: launch_sem_ax<T, 9>(E, gid, G, D, u, y, s, nb, ld); break;
+    case 10: launch_sem_ax<T, 10>(E, gid, G, D, u, y, s, nb, ld); break;
     default: break;
   }
 }
@@ -132,7 +134,9 @@ constexpr int kTransferThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(kTransferThreads)
 k_sem_restrict(int Qf, int Qc, const uint32_t* __restrict__ gidf, const uint32_t* __restrict__ gidc,
-               const T* __restrict__ J, const T* __restrict__ rf, T* __restrict__ rc) {
+               const T* __restrict__ J, const T* __restrict__ rf, T* __restrict__ rc, int64_t ldf, int64_t ldc) {
+  rf += (int64_t)blockIdx.y * ldf;
+  rc += (int64_t)blockIdx.y * ldc;
   extern __shared__ unsigned char smem_raw[];
   T* sJ = reinterpret_cast<T*>(smem_raw);      // [Qf][Qc]
   T* a = sJ + Qf * Qc;                         // [kf][jf][if]
@@ -172,7 +176,10 @@ k_sem_restrict(int Qf, int Qc, const uint32_t* __restrict__ gidf, const uint32_t
 template <typename T>
 __global__ void __launch_bounds__(kTransferThreads)
 k_sem_prolong(int Qf, int Qc, const uint32_t* __restrict__ gidf, const uint32_t* __restrict__ gidc,
-              const T* __restrict__ J, const T* __restrict__ zc, T* __restrict__ zf, int accumulate) {
+              const T* __restrict__ J, const T* __restrict__ zc, T* __restrict__ zf, int accumulate, int64_t ldf,
+              int64_t ldc) {
+  zf += (int64_t)blockIdx.y * ldf;
+  zc += (int64_t)blockIdx.y * ldc;
   extern __shared__ unsigned char smem_raw[];
   T* sJ = reinterpret_cast<T*>(smem_raw);      // [Qf][Qc]
   T* a = sJ + Qf * Qc;                         // [kc][jc][ic]
@@ -222,17 +229,17 @@ static size_t transfer_smem(int Qf, int Qc) {
 
 template <typename T>
 void sem_restrict(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc, const T* J,
-                  const T* rf, T* rc, cudaStream_t s) {
-  k_sem_restrict<T><<<(unsigned)E, kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(Qf, Qc, gidf, gidc,
-                                                                                   J, rf, rc);
+                  const T* rf, T* rc, cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
+  k_sem_restrict<T><<<dim3((unsigned)E, nb), kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(
+      Qf, Qc, gidf, gidc, J, rf, rc, ldf, ldc);
   count();
 }
 
 template <typename T>
 void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc, const T* J,
-                 const T* zc, T* zf, int accumulate, cudaStream_t s) {
-  k_sem_prolong<T><<<(unsigned)E, kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(
-      Qf, Qc, gidf, gidc, J, zc, zf, accumulate);
+                 const T* zc, T* zf, int accumulate, cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
+  k_sem_prolong<T><<<dim3((unsigned)E, nb), kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(
+      Qf, Qc, gidf, gidc, J, zc, zf, accumulate, ldf, ldc);
   count();
 }
 
@@ -240,7 +247,10 @@ void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t
 // FD kernels
 // ===========================================================================
 template <typename T>
-__global__ void k_fd_apply(int mx, int my, Stencil9<T> st, const T* __restrict__ u, T* __restrict__ y) {
+__global__ void k_fd_apply(int mx, int my, Stencil9<T> st, const T* __restrict__ u, T* __restrict__ y,
+                           int64_t ld) {
+  u += (int64_t)blockIdx.z * ld;   // right-hand side of a batch
+  y += (int64_t)blockIdx.z * ld;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= mx || j >= my) return;
@@ -260,17 +270,19 @@ __global__ void k_fd_apply(int mx, int my, Stencil9<T> st, const T* __restrict__
 }
 
 template <typename T>
-void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s) {
+void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s, int nb, int64_t ld) {
   dim3 bs(32, 8);
-  dim3 gs((mx + 31) / 32, (my + 7) / 8);
-  k_fd_apply<T><<<gs, bs, 0, s>>>(mx, my, st, u, y);
+  dim3 gs((mx + 31) / 32, (my + 7) / 8, nb);
+  k_fd_apply<T><<<gs, bs, 0, s>>>(mx, my, st, u, y, ld);
   count();
 }
 
 // rc(I,J) = sum_{|a|,|b| < c} w_a w_b rf(c(I+1)-1+b, c(J+1)-1+a), w_d = (c - |d|)/c
 template <typename T>
 __global__ void k_fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* __restrict__ rf,
-                              T* __restrict__ rc) {
+                              T* __restrict__ rc, int64_t ldf, int64_t ldc) {
+  rf += (int64_t)blockIdx.z * ldf;
+  rc += (int64_t)blockIdx.z * ldc;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int Jc = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mcx || Jc >= mcy) return;
@@ -294,7 +306,9 @@ __global__ void k_fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T
 
 template <typename T>
 __global__ void k_fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* __restrict__ zc,
-                             T* __restrict__ zf, int accumulate) {
+                             T* __restrict__ zf, int accumulate, int64_t ldf, int64_t ldc) {
+  zf += (int64_t)blockIdx.z * ldf;
+  zc += (int64_t)blockIdx.z * ldc;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= mfx || j >= mfy) return;
@@ -318,24 +332,27 @@ __global__ void k_fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T*
 }
 
 template <typename T>
-void fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* rf, T* rc, cudaStream_t s) {
+void fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* rf, T* rc, cudaStream_t s, int nb,
+                 int64_t ldf, int64_t ldc) {
   dim3 bs(16, 16);
-  dim3 gs((mcx + 15) / 16, (mcy + 15) / 16);
-  k_fd_restrict<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, rf, rc);
+  dim3 gs((mcx + 15) / 16, (mcy + 15) / 16, nb);
+  k_fd_restrict<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, rf, rc, ldf, ldc);
   count();
 }
 
 template <typename T>
 void fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* zc, T* zf, int accumulate,
-                cudaStream_t s) {
+                cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
   dim3 bs(32, 8);
-  dim3 gs((mfx + 31) / 32, (mfy + 7) / 8);
-  k_fd_prolong<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, zc, zf, accumulate);
+  dim3 gs((mfx + 31) / 32, (mfy + 7) / 8, nb);
+  k_fd_prolong<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, zc, zf, accumulate, ldf, ldc);
   count();
 }
 
 __global__ void k_dense_matvec(int n, const double* __restrict__ M, const double* __restrict__ x,
-                               double* __restrict__ y) {
+                               double* __restrict__ y, int64_t ld) {
+  x += (int64_t)blockIdx.y * ld;
+  y += (int64_t)blockIdx.y * ld;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double acc = 0.0;
@@ -343,8 +360,8 @@ __global__ void k_dense_matvec(int n, const double* __restrict__ M, const double
   y[i] = acc;
 }
 
-void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s) {
-  k_dense_matvec<<<(n + 127) / 128, 128, 0, s>>>(n, M, x, y);
+void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s, int nb, int64_t ld) {
+  k_dense_matvec<<<dim3((n + 127) / 128, nb), 128, 0, s>>>(n, M, x, y, ld);
   count();
 }
 
@@ -354,7 +371,8 @@ void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream
 template <typename T>
 __global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                              T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD, T c0,
-                             int x_is_zero) {
+                             int x_is_zero, int64_t ld) {
+  { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     T rv;
     if (x_is_zero) {
@@ -397,7 +415,8 @@ __device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T
 // body (every pointer comes from a 256-byte aligned allocation), scalar tail.
 template <typename T, bool VEC>
 __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
-                             T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2) {
+                             T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, int64_t ld) {
+  { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
   using VT = typename V16<T>::type;
   constexpr int L = V16<T>::L;
   const int64_t nv = VEC ? n / L : 0;
@@ -425,7 +444,8 @@ __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
 template <typename T>
 __global__ void k_cheb1_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                              T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD,
-                             T inv_theta, int x_is_zero) {
+                             T inv_theta, int x_is_zero, int64_t ld) {
+  { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     T rv;
     if (x_is_zero) {
@@ -442,7 +462,8 @@ __global__ void k_cheb1_init(int64_t n, const T* __restrict__ b, T* __restrict__
 
 template <typename T>
 __global__ void k_cheb1_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
-                             T* __restrict__ y, const T* __restrict__ invD, T c1, T c2) {
+                             T* __restrict__ y, const T* __restrict__ invD, T c1, T c2, int64_t ld) {
+  { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const T dv = d[g];
     const T rv = r[g] - invD[g] * y[g];
@@ -454,13 +475,15 @@ __global__ void k_cheb1_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
 }
 
 template <typename T>
-__global__ void k_axpy(int64_t n, T a, const T* __restrict__ d, T* __restrict__ x) {
+__global__ void k_axpy(int64_t n, T a, const T* __restrict__ d, T* __restrict__ x, int64_t ld) {
+  { const int64_t off_ = (int64_t)blockIdx.y * ld; d += off_; x += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     x[g] += a * d[g];
 }
 
 template <typename T>
-__global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y, T* __restrict__ r) {
+__global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y, T* __restrict__ r, int64_t ld) {
+  { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; y += off_; r += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     r[g] = b[g] - y[g];
     y[g] = T(0);
@@ -468,13 +491,17 @@ __global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y
 }
 
 template <typename Tin, typename Tout>
-__global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out) {
+__global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out, int64_t ldi, int64_t ldo) {
+  in += (int64_t)blockIdx.y * ldi;
+  out += (int64_t)blockIdx.y * ldo;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     out[g] = (Tout)in[g];
 }
 
 __global__ void k_masked_copy(int64_t n, const double* __restrict__ in, const double* __restrict__ invD,
-                              double* __restrict__ out) {
+                              double* __restrict__ out, int64_t ldi, int64_t ldo) {
+  in += (int64_t)blockIdx.y * ldi;
+  out += (int64_t)blockIdx.y * ldo;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     out[g] = invD[g] != 0.0 ? in[g] : 0.0;
 }
@@ -483,51 +510,58 @@ constexpr int kVecThreads = 256;
 
 template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0, int x_is_zero,
-                cudaStream_t s) {
-  k_cheb4_init<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)c0, x_is_zero);
+                cudaStream_t s, int nb, int64_t ld) {
+  k_cheb4_init<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)c0,
+                                                                             x_is_zero, ld ? ld : n);
   count();
 }
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
-                cudaStream_t s) {
+                cudaStream_t s, int nb, int64_t ld) {
+  if (!ld) ld = n;
   const uintptr_t align = (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
-  if (align % 16 == 0)
-    k_cheb4_step<T, true><<<grid_for(n / V16<T>::L + 1, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD,
-                                                                                          (T)beta, (T)c1, (T)c2);
+  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
+    k_cheb4_step<T, true><<<dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), kVecThreads, 0, s>>>(
+        n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, ld);
   else
-    k_cheb4_step<T, false><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)beta, (T)c1,
-                                                                           (T)c2);
+    k_cheb4_step<T, false><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)beta,
+                                                                                     (T)c1, (T)c2, ld);
   count();
 }
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
-                int x_is_zero, cudaStream_t s) {
-  k_cheb1_init<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)inv_theta,
-                                                                    x_is_zero);
+                int x_is_zero, cudaStream_t s, int nb, int64_t ld) {
+  k_cheb1_init<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)inv_theta,
+                                                                             x_is_zero, ld ? ld : n);
   count();
 }
 template <typename T>
-void cheb1_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double c1, double c2, cudaStream_t s) {
-  k_cheb1_step<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)c1, (T)c2);
+void cheb1_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double c1, double c2, cudaStream_t s, int nb,
+                int64_t ld) {
+  k_cheb1_step<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)c1, (T)c2,
+                                                                             ld ? ld : n);
   count();
 }
 template <typename T>
-void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s) {
-  k_axpy<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, (T)a, d, x);
+void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s, int nb, int64_t ld) {
+  k_axpy<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, (T)a, d, x, ld ? ld : n);
   count();
 }
 template <typename T>
-void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s) {
-  k_residual<T><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, b, y, r);
+void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s, int nb, int64_t ld) {
+  k_residual<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, y, r, ld ? ld : n);
   count();
 }
 template <typename Tin, typename Tout>
-void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s) {
-  k_cast<Tin, Tout><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, in, out);
+void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s, int nb, int64_t ldi, int64_t ldo) {
+  k_cast<Tin, Tout><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, in, out, ldi ? ldi : n,
+                                                                               ldo ? ldo : n);
   count();
 }
-void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s) {
-  k_masked_copy<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, in, invD, out);
+void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s, int nb, int64_t ldi,
+                 int64_t ldo) {
+  k_masked_copy<<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, in, invD, out, ldi ? ldi : n,
+                                                                           ldo ? ldo : n);
   count();
 }
 
@@ -1138,25 +1172,30 @@ void scale(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
 // explicit instantiations
 // ===========================================================================
 #define CHEBMG_INST(T)                                                                                \
-  template void sem_ax<T>(int, int64_t, const uint32_t*, const T*, const T*, const T*, T*, cudaStream_t); \
+  template void sem_ax<T>(int, int64_t, const uint32_t*, const T*, const T*, const T*, T*, cudaStream_t, int,  \
+                          int64_t);                                                                   \
   template void sem_restrict<T>(int, int, int64_t, const uint32_t*, const uint32_t*, const T*, const T*,  \
-                                T*, cudaStream_t);                                                     \
+                                T*, cudaStream_t, int, int64_t, int64_t);                              \
   template void sem_prolong<T>(int, int, int64_t, const uint32_t*, const uint32_t*, const T*, const T*,   \
-                               T*, int, cudaStream_t);                                                 \
-  template void fd_apply<T>(int, int, const Stencil9<T>&, const T*, T*, cudaStream_t);                  \
-  template void fd_restrict<T>(int, int, int, int, int, const T*, T*, cudaStream_t);                    \
-  template void fd_prolong<T>(int, int, int, int, int, const T*, T*, int, cudaStream_t);                \
-  template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t);  \
-  template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t); \
-  template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t);  \
-  template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t);         \
-  template void axpy<T>(int64_t, double, const T*, T*, cudaStream_t);                                   \
-  template void residual<T>(int64_t, const T*, T*, T*, cudaStream_t);
+                               T*, int, cudaStream_t, int, int64_t, int64_t);                          \
+  template void fd_apply<T>(int, int, const Stencil9<T>&, const T*, T*, cudaStream_t, int, int64_t);    \
+  template void fd_restrict<T>(int, int, int, int, int, const T*, T*, cudaStream_t, int, int64_t, int64_t); \
+  template void fd_prolong<T>(int, int, int, int, int, const T*, T*, int, cudaStream_t, int, int64_t,     \
+                              int64_t);                                                               \
+  template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
+                              int64_t);                                                                 \
+  template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t, int,   \
+                              int64_t);                                                                 \
+  template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
+                              int64_t);                                                                 \
+  template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t, int, int64_t); \
+  template void axpy<T>(int64_t, double, const T*, T*, cudaStream_t, int, int64_t);                     \
+  template void residual<T>(int64_t, const T*, T*, T*, cudaStream_t, int, int64_t);
 
 CHEBMG_INST(float)
 CHEBMG_INST(double)
-template void cast<double, float>(int64_t, const double*, float*, cudaStream_t);
-template void cast<float, double>(int64_t, const float*, double*, cudaStream_t);
-template void cast<double, double>(int64_t, const double*, double*, cudaStream_t);
+template void cast<double, float>(int64_t, const double*, float*, cudaStream_t, int, int64_t, int64_t);
+template void cast<float, double>(int64_t, const float*, double*, cudaStream_t, int, int64_t, int64_t);
+template void cast<double, double>(int64_t, const double*, double*, cudaStream_t, int, int64_t, int64_t);
 
 }  // namespace chebmg

@@ -406,6 +406,139 @@ k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
   }
 }
 
+// Batched variant: the block stages the geometric factors of its EB elements once (one TMA
+// copy) and applies the element operator to RB right-hand sides in turn, RHS q of the batch
+// at u + q * ld, y + q * ld.  The element-to-global ids are computed once per block, and the
+// gather of the next right-hand side is in flight while the current one is computed.
+template <typename T, int EB, bool IMPLICIT>
+__global__ void __launch_bounds__(64 * EB)
+k_sem_ax8b(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
+           const T* __restrict__ u, T* __restrict__ y, unsigned* __restrict__ err, int nb, int64_t ld, int rb) {
+  using C = Ax8<T, EB>;
+  constexpr int R = C::R, P = C::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* sG = reinterpret_cast<T*>(smem_raw);
+  T* sU = sG + EB * C::GELEM;
+  T* sR = sU + EB * C::STAGE;
+  T* sS = sR + EB * C::STAGE;
+  const int tid = threadIdx.x;
+  const int le = tid >> 6, t = tid & 63, a = t & 7, b = t >> 3;
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((E - e0) < EB ? (E - e0) : EB);
+  const bool valid = le < nvalid;
+  const int64_t e = e0 + le;
+  const int q0 = blockIdx.y * rb;
+  const int q1 = q0 + rb < nb ? q0 + rb : nb;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t bytes = (uint32_t)(nvalid * C::GELEM * sizeof(T));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sG)),
+        "l"(G + e0 * C::GELEM), "r"(bytes), "r"(smem_addr(&bar))
+        : "memory");
+  }
+  T* su = sU + le * C::STAGE;
+  T* sr = sR + le * C::STAGE;
+  T* ss = sS + le * C::STAGE;
+  uint32_t g[8];
+  column_ids<IMPLICIT>(gid, lat, e, valid, a, b, g);
+  auto gather = [&](int q, T (&v)[8]) {
+    const T* uq = u + (int64_t)q * ld;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (q < q1 && !(g[k] & kGidDirichlet)) ? uq[g[k] & kGidMask] : T(0);
+  };
+  T col[8];
+  gather(q0, col);
+  for (int q = q0; q < q1; ++q) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) su[k * P + b * R + a] = col[k];
+    T ut[8];
+    line8<T, 0>(col, ut);
+    T cn[8];
+    gather(q + 1, cn);           // next right-hand side's loads overlap this one's work
+    __syncthreads();
+    {
+      T v[8], o[8];
+      ld_row(su + b * P + a * R, v);
+      line8<T, 0>(v, o);
+      st_row(sr + b * P + a * R, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = su[b * P + j * R + a];
+      line8<T, 0>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ss[b * P + j * R + a] = o[j];
+    }
+    if (q == q0) {               // geometric factors must have landed (once per block)
+      bool ok = false;
+      for (uint32_t w = 0; w < kWaitLimit; ++w)
+        if (mbar_try_wait(&bar, 0)) {
+          ok = true;
+          break;
+        }
+      if (!__syncthreads_and(ok ? 1 : 0)) {
+        if (tid == 0) atomicExch(err, 1u);
+        for (uint32_t w = 0; w < kWaitLimit; ++w)
+          if (mbar_try_wait(&bar, 0)) break;
+        return;
+      }
+    } else {
+      __syncthreads();           // the line passes above wrote points other threads read next
+    }
+    T wt[8];
+    const T* gG = sG + le * C::GELEM;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int p = k * 64 + b * 8 + a;
+      const int qq = k * P + b * R + a;
+      const T ur = sr[qq], us = ss[qq], utk = ut[k];
+      const T g00 = gG[p], g01 = gG[512 + p], g02 = gG[1024 + p];
+      const T g11 = gG[1536 + p], g12 = gG[2048 + p], g22 = gG[2560 + p];
+      sr[qq] = g00 * ur + g01 * us + g02 * utk;
+      ss[qq] = g01 * ur + g11 * us + g12 * utk;
+      wt[k] = g02 * ur + g12 * us + g22 * utk;
+    }
+    T yt[8];
+    line8<T, 1>(wt, yt);
+    __syncthreads();
+    {
+      T v[8], o[8];
+      ld_row(sr + b * P + a * R, v);
+      line8<T, 1>(v, o);
+      st_row(su + b * P + a * R, o);
+    }
+    __syncthreads();
+    {
+      T v[8], o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = ss[b * P + j * R + a];
+      line8<T, 1>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) su[b * P + j * R + a] += o[j];
+    }
+    __syncthreads();
+    if (valid) {
+      T* yq = y + (int64_t)q * ld;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const T v = su[k * P + b * R + a] + yt[k];
+        if (!(g[k] & kGidDirichlet)) atomicAdd(&yq[g[k] & kGidMask], v);
+      }
+    }
+    __syncthreads();             // stage buffers free for the next right-hand side
+#pragma unroll
+    for (int k = 0; k < 8; ++k) col[k] = cn[k];
+  }
+}
+
 }  // namespace
 
 cudaError_t sem_ax8_set_D(const double* D) {
@@ -464,6 +597,22 @@ static void launch_ax8p(int64_t E, const uint32_t* gid, const Lattice& lat, cons
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+template <typename T, int EB, bool IM>
+static void launch_ax8b(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                        unsigned* err, int nb, int64_t ld, int rb, cudaStream_t s) {
+  using C = Ax8<T, EB>;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_sem_ax8b<T, EB, IM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)C::smem_bytes());
+    configured = true;
+  }
+  if (rb < 1) rb = 1;
+  const dim3 blocks((unsigned)((E + EB - 1) / EB), (unsigned)((nb + rb - 1) / rb));
+  k_sem_ax8b<T, EB, IM><<<blocks, 64 * EB, C::smem_bytes(), s>>>(E, gid, lat, G, u, y, err, nb, ld, rb);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 template <typename T>
 size_t sem_ax8_smem(int eb) {
   eb %= 100;
@@ -504,11 +653,32 @@ void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, con
   else dispatch_ax8<T, false>(E, gid, lat, G, u, y, err, variant, s);
 }
 
+template <typename T>
+void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                     unsigned* err, int variant, int nb, int64_t ld, cudaStream_t s) {
+  const int rb = variant / 1000;
+  const bool im = (variant % 1000) >= 100;
+  const int eb = variant % 100;
+  if (im) {
+    if (eb == 1) launch_ax8b<T, 1, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+    else if (eb == 4) launch_ax8b<T, 4, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+    else launch_ax8b<T, 2, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+  } else {
+    if (eb == 1) launch_ax8b<T, 1, false>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+    else if (eb == 4) launch_ax8b<T, 4, false>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+    else launch_ax8b<T, 2, false>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+  }
+}
+
 template bool sem_ax8_variant_fits<float>(int);
 template bool sem_ax8_variant_fits<double>(int);
 template void sem_ax8<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
                              unsigned*, int, cudaStream_t);
 template void sem_ax8<double>(int64_t, const uint32_t*, const Lattice&, const double*, const double*, double*,
                               unsigned*, int, cudaStream_t);
+template void sem_ax8_batched<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
+                                     unsigned*, int, int, int64_t, cudaStream_t);
+template void sem_ax8_batched<double>(int64_t, const uint32_t*, const Lattice&, const double*, const double*,
+                                      double*, unsigned*, int, int, int64_t, cudaStream_t);
 
 }  // namespace chebmg

@@ -58,7 +58,10 @@ __device__ __forceinline__ uint32_t lattice_id(const Lattice& L, int N, ElemCoor
 // rc += P^T rf (rc zeroed by the caller; coarse contributions summed by atomics)
 template <typename T, int QF, int QC>
 __global__ void __launch_bounds__(64 * kEB)
-k_restrict_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ rf, T* __restrict__ rc) {
+k_restrict_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ rf, T* __restrict__ rc, int64_t ldf,
+               int64_t ldc) {
+  rf += (int64_t)blockIdx.y * ldf;   // right-hand side of a batch
+  rc += (int64_t)blockIdx.y * ldc;
   constexpr int NF = QF - 1, NC = QC - 1;
   __shared__ T sA[kEB][QF * QF * QF];
   __shared__ T sB[kEB][QF * QF * QC];
@@ -129,7 +132,10 @@ k_restrict_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ rf, T* _
 // zf (+)= P zc at the owned fine copies
 template <typename T, int QF, int QC>
 __global__ void __launch_bounds__(64 * kEB)
-k_prolong_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ zc, T* __restrict__ zf, int accumulate) {
+k_prolong_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ zc, T* __restrict__ zf, int accumulate,
+              int64_t ldf, int64_t ldc) {
+  zf += (int64_t)blockIdx.y * ldf;
+  zc += (int64_t)blockIdx.y * ldc;
   constexpr int NF = QF - 1, NC = QC - 1;
   __shared__ T sA[kEB][QC * QC * QC];
   __shared__ T sB[kEB][QC * QC * QF];
@@ -220,29 +226,29 @@ bool transfer_box_supported(int Qf, int Qc) { return (Qf == 8 && Qc == 4) || (Qf
 
 template <typename T>
 void restrict_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* rf, T* rc,
-                  cudaStream_t s) {
-  const unsigned blocks = (unsigned)((E + kEB - 1) / kEB);
-  if (Qf == 8) k_restrict_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc);
-  else k_restrict_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc);
+                  cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
+  const dim3 blocks((unsigned)((E + kEB - 1) / kEB), nb);
+  if (Qf == 8) k_restrict_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
+  else k_restrict_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 template <typename T>
 void prolong_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* zc, T* zf,
-                 int accumulate, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((E + kEB - 1) / kEB);
-  if (Qf == 8) k_prolong_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate);
-  else k_prolong_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate);
+                 int accumulate, cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
+  const dim3 blocks((unsigned)((E + kEB - 1) / kEB), nb);
+  if (Qf == 8) k_prolong_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+  else k_prolong_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 template void restrict_box<float>(int, int, int64_t, const Lattice&, const Lattice&, const float*, float*,
-                                  cudaStream_t);
+                                  cudaStream_t, int, int64_t, int64_t);
 template void restrict_box<double>(int, int, int64_t, const Lattice&, const Lattice&, const double*, double*,
-                                   cudaStream_t);
+                                   cudaStream_t, int, int64_t, int64_t);
 template void prolong_box<float>(int, int, int64_t, const Lattice&, const Lattice&, const float*, float*, int,
-                                 cudaStream_t);
+                                 cudaStream_t, int, int64_t, int64_t);
 template void prolong_box<double>(int, int, int64_t, const Lattice&, const Lattice&, const double*, double*, int,
-                                  cudaStream_t);
+                                  cudaStream_t, int, int64_t, int64_t);
 
 }  // namespace chebmg
