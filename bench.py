@@ -152,6 +152,108 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+BATCH_NE, BATCH_NRHS = 8, 64
+UNEVEN = [(ne, Nn) for ne in (4, 6, 8, 12) for Nn in (5, 7, 9)]
+
+
+def bench_batched(cm, W, torch, timed, reps):
+    """64 right-hand sides on E = 8^3, N = 7 in one batched solve, and the uneven group of meshes
+    E in {4^3, 6^3, 8^3, 12^3} x N in {5, 7, 9} (one right-hand side each) in one grouped solve,
+    each against the same problems solved one after another by the single-right-hand-side
+    FP64 and mixed forms.  Times are seconds for the whole set, inputs resident in HBM."""
+    import numpy as np
+    common = dict(orders=ORDERS, kind=KIND, order=K_ORDER, sided=SIDED)
+    v = W.sem_box_vertices(BATCH_NE, BATCH_NE, BATCH_NE)
+    s32 = cm.Solver("sem", verts=v, prec="mixed", **common)
+    lmax = [s32.lambda_max(j) for j in range(len(ORDERS) - 1)]
+    s64 = cm.Solver("sem", verts=v, prec="fp64", lmax=lmax, **common)
+    n = s32.size(0)
+    B = torch.tensor(np.stack([W.sem_rhs(BATCH_NE, BATCH_NE, BATCH_NE, NORDER, seed=q)
+                               for q in range(BATCH_NRHS)]), device="cuda")
+    U = torch.zeros_like(B)
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+    def batched(s, graph):
+        code, its, rel = cm.chebmg_pcg_solve_batched(s.ctx, B, U, RTOL, 500, graph=graph)
+        assert code == cm.CHEBMG_OK and max(rel) <= RTOL, (code, max(rel))
+        return its
+
+    def sequential(s):
+        its = []
+        for q in range(BATCH_NRHS):
+            code, it, rel, _ = cm.chebmg_pcg_solve(s.ctx, B[q], u, RTOL, 500)
+            assert code == cm.CHEBMG_OK and rel <= RTOL
+            its.append(it)
+        return its
+
+    out = {"workload": f"{BATCH_NRHS} RHS (seeds 0..{BATCH_NRHS - 1}) on SEM E={BATCH_NE}^3 N={NORDER}, "
+                       f"p-MG {ORDERS}, {KIND} one-sided ({2 * K_ORDER},0), FCG to 1e-8",
+           "n_dof_per_rhs": n, "time_s": {}}
+    for name, fn in [("batched_mixed_graph", lambda: batched(s32, True)),
+                     ("batched_mixed_eager", lambda: batched(s32, False)),
+                     ("batched_fp64_graph", lambda: batched(s64, True)),
+                     ("sequential_mixed", lambda: sequential(s32)),
+                     ("sequential_fp64", lambda: sequential(s64))]:
+        fn()
+        l0 = cm.chebmg_launch_count()
+        t, its = timed(fn, reps)
+        out["time_s"][name] = t
+        if name == "batched_mixed_graph":
+            out["iterations"] = {"min": min(its), "max": max(its)}
+            out["gpu_launches"] = (cm.chebmg_launch_count() - l0) // reps
+    tb = out["time_s"]["batched_mixed_graph"]
+    out["gdofs_batched_mixed_graph"] = BATCH_NRHS * n / tb / 1e9
+    out["speedup_vs_sequential_fp64"] = out["time_s"]["sequential_fp64"] / tb
+    out["speedup_vs_sequential_mixed"] = out["time_s"]["sequential_mixed"] / tb
+    out["ax8_batched_variant"] = {"fp32": cm.chebmg_batch_info(s32.ctx, BATCH_NRHS, 0, cm.CHEBMG_F32)[0],
+                                  "fp64": cm.chebmg_batch_info(s64.ctx, BATCH_NRHS, 0, cm.CHEBMG_F64)[0]}
+    out["coarse_degree"] = cm.chebmg_batch_info(s32.ctx, BATCH_NRHS, 0, cm.CHEBMG_F32)[1]
+    s32.close()
+    s64.close()
+
+    # ---- uneven group of meshes ----
+    g32, g64, bs, us = [], [], [], []
+    for k, (ne, Nn) in enumerate(UNEVEN):
+        vv = W.sem_box_vertices(ne, ne, ne)
+        a = cm.Solver("sem", verts=vv, prec="mixed", **dict(common, orders=(Nn, 3, 1)))
+        lm = [a.lambda_max(j) for j in range(2)]
+        g32.append(a)
+        g64.append(cm.Solver("sem", verts=vv, prec="fp64", lmax=lm, **dict(common, orders=(Nn, 3, 1))))
+        bs.append(torch.tensor(W.sem_rhs(ne, ne, ne, Nn, seed=k), device="cuda"))
+        us.append(torch.zeros_like(bs[-1]))
+    ctxs = [a.ctx for a in g32]
+    grp = cm.chebmg_group_create(ctxs)
+
+    def group(graph):
+        code, its, rel = cm.chebmg_group_pcg_solve(grp, ctxs, bs, us, RTOL, 500, graph=graph)
+        assert code == cm.CHEBMG_OK and max(rel) <= RTOL
+        return its
+
+    def seq(solvers):
+        its = []
+        for a, bb, uu in zip(solvers, bs, us):
+            code, it, rel, _ = cm.chebmg_pcg_solve(a.ctx, bb, uu, RTOL, 500)
+            assert code == cm.CHEBMG_OK and rel <= RTOL
+            its.append(it)
+        return its
+
+    un = {"workload": "one RHS each on SEM E in {4,6,8,12}^3 x N in {5,7,9}, p-MG (N,3,1), "
+                      f"{KIND} one-sided ({2 * K_ORDER},0), FCG to 1e-8",
+          "n_dof_total": int(sum(bb.numel() for bb in bs)), "time_s": {}}
+    for name, fn in [("group_mixed_graph", lambda: group(True)), ("group_mixed_eager", lambda: group(False)),
+                     ("sequential_mixed", lambda: seq(g32)), ("sequential_fp64", lambda: seq(g64))]:
+        fn()
+        t, _ = timed(fn, reps)
+        un["time_s"][name] = t
+    un["speedup_vs_sequential_fp64"] = un["time_s"]["sequential_fp64"] / un["time_s"]["group_mixed_graph"]
+    un["speedup_vs_sequential_mixed"] = un["time_s"]["sequential_mixed"] / un["time_s"]["group_mixed_graph"]
+    cm.chebmg_group_destroy(grp)
+    for a in g32 + g64:
+        a.close()
+    out["uneven"] = un
+    return out
+
+
 def main():
     global NE
     ap = argparse.ArgumentParser()
@@ -160,6 +262,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched / grouped measurements")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched / grouped measurements (printed as one JSON object)")
     ap.add_argument("--ne", type=int, default=NE,
                     help="elements per direction (profiling runs only; the benchmark uses 32)")
     ap.add_argument("--profile-smoother", choices=["mixed", "fp64"], default=None,
@@ -281,6 +386,12 @@ def main():
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps), out
 
+    if args.batched_only:
+        s32.close()
+        s64.close()
+        print(json.dumps({"batched": bench_batched(cm, W, torch, timed, max(1, args.steps))}))
+        return 0
+
     for _ in range(args.warmup):
         it32 = solve(s32)
     it64 = solve(s64)
@@ -354,6 +465,10 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roofline, "roofline_fp64": fp64_alu,
             "clocks": clk}
+    if not args.no_batched:
+        s32.close()
+        s64.close()
+        line["batched"] = bench_batched(cm, W, torch, timed, max(1, min(args.steps, 3)))
     if rank == 0 and not args.no_cpu_baseline:
         r = run_oracle(1)
         t = r["times"][0]
