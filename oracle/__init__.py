@@ -22,6 +22,8 @@ chebyshev  Algorithm 1 (1st kind) and Algorithm 2 ((optimized) 4th kind), the
 multigrid  V-cycle error propagator, symmetric (k,k) and one-sided (2k,0)
            (Eqs. 2.2, 2.4-2.6).
 krylov     flexible CG, Jacobi-PCG coarse solve, Lanczos lambda_max, SplitMix64.
+sensitivity  error reduction of three V-cycles and its gradient with respect to the
+           4th-kind weights and the lambda_max scale (forward mode).
 theory     gamma^{-1}(k) (Eq. 2.14), closed forms (Eqs. 2.18-2.24), critical C
            (Eqs. 2.25-2.28), grid complexity (Eq. 3.2).
 
