@@ -226,6 +226,31 @@ int chebmg_group_pcg_solve(chebmg_group* group, const double* const* B, double* 
                            double rtol, int maxit, int flags, int* iters, double* relres);
 void chebmg_group_destroy(chebmg_group* group);
 
+/* ---- smoother weights and their gradient ----------------------------------------- */
+
+/* Error reduction of `steps` V-cycles (Sec. 3, Eq. 3.1: observed convergence) and its
+ * gradient.  With B one FP64 V-cycle (Eq. 2.2) whose Algorithm-2 smoother uses the weights
+ * betas[0..nbeta-1] (beta_i of Sec. 2.3, for every smoothing call of the cycle) and
+ * lambda_max_j = lmax_scale * (the context's lambda_max of level j), and E = I - B A:
+ *   *f = (1/nrhs) sum_q ||E^steps e0_q||^2 / ||e0_q||^2 ,
+ * and grad_betas[i] = df/dbeta_i, *grad_scale = df/dlmax_scale.  E0: FP64 device array
+ * [nrhs][n] of the finest level (Dirichlet entries ignored).  f_each: host, nrhs values or
+ * NULL.  The gradient is exact up to rounding: reverse mode through the cycle (A and S are
+ * symmetric, so the adjoint is the transposed cycle), each cycle recomputed from its input
+ * instead of being stored, all nrhs errors as one batch; the coarse solve is taken as the
+ * linear map A_c^{-1} (its tolerance, coarse_rtol, bounds the error of that reading).
+ * Needs a 4th-kind context (CHEBMG_CHEB_4TH or _4TH_OPT) with nbeta equal to the smoothing
+ * order (pre, and post if nonzero).  The context's own weights are left unchanged. */
+int chebmg_cycle_error_grad(chebmg_ctx* ctx, int nrhs, const double* E0, int steps,
+                            const double* betas, int nbeta, double lmax_scale, double* f,
+                            double* grad_betas, double* grad_scale, double* f_each);
+
+/* Replaces the Algorithm-2 weights used by every later smoothing call of order nbeta (for
+ * example weights tuned with chebmg_cycle_error_grad), and scales every level's lambda_max
+ * by lmax_scale.  nbeta = 0 restores the defaults of the context's kind (lmax_scale still
+ * applies). */
+int chebmg_set_smoother_weights(chebmg_ctx* ctx, const double* betas, int nbeta, double lmax_scale);
+
 /* ---- self-test -------------------------------------------------------------- */
 
 /* Failure-path self-test of the persistent SEM coarse solver (not part of the paper's

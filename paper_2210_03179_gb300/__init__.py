@@ -99,6 +99,10 @@ _SIGNATURES = {
                                          POINTER(c_int), POINTER(c_double)]),
     "chebmg_apply_A_batched": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "chebmg_vcycle_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "chebmg_cycle_error_grad": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_double), c_int, c_double,
+                                        POINTER(c_double), POINTER(c_double), POINTER(c_double),
+                                        POINTER(c_double)]),
+    "chebmg_set_smoother_weights": (c_int, [c_void_p, POINTER(c_double), c_int, c_double]),
     "chebmg_batch_info": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_int), POINTER(c_int)]),
     "chebmg_set_batch_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "chebmg_group_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
@@ -343,6 +347,27 @@ def chebmg_vcycle_batched(ctx, R, Z):
     nrhs = R.shape[0]
     _check(lib().chebmg_vcycle_batched(ctx, nrhs, _ptr(R, nrhs * n, CHEBMG_F64, "R"),
                                        _ptr(Z, nrhs * n, CHEBMG_F64, "Z")), "chebmg_vcycle_batched")
+
+
+def chebmg_cycle_error_grad(ctx, E0, betas, lmax_scale=1.0, steps=3):
+    """E0: contiguous FP64 CUDA tensor (nrhs, n).  Returns (f, grad_betas list, grad_scale, f_each list)."""
+    n = chebmg_level_size(ctx, 0)
+    if E0.dim() != 2 or E0.shape[1] != n:
+        raise ValueError(f"E0 must have shape (nrhs, {n})")
+    nrhs = E0.shape[0]
+    k = len(betas)
+    b = (c_double * k)(*[float(v) for v in betas])
+    f, gs = c_double(), c_double()
+    gb, fe = (c_double * k)(), (c_double * nrhs)()
+    _check(lib().chebmg_cycle_error_grad(ctx, nrhs, _ptr(E0, nrhs * n, CHEBMG_F64, "E0"), int(steps), b, k,
+                                         float(lmax_scale), byref(f), gb, byref(gs), fe), "chebmg_cycle_error_grad")
+    return f.value, list(gb), gs.value, list(fe)
+
+
+def chebmg_set_smoother_weights(ctx, betas=(), lmax_scale=1.0):
+    k = len(betas)
+    b = (c_double * max(k, 1))(*[float(v) for v in betas])
+    _check(lib().chebmg_set_smoother_weights(ctx, b, k, float(lmax_scale)), "chebmg_set_smoother_weights")
 
 
 def chebmg_batch_info(ctx, nrhs, level=0, dtype=CHEBMG_F64):

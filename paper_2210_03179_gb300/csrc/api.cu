@@ -154,6 +154,18 @@ struct chebmg_ctx {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   int gexec_nb = 0;
   int64_t glaunches[2] = {0, 0};   // kernels per replay of each graph
+  // ---- smoother parameter overrides (weight tuning) ----
+  std::vector<double> beta_ovr;  // weights of Algorithm 2 for smoothing order beta_ovr.size()
+  double lscale = 1.0;           // every level smooths with lscale * lambda_max
+  // ---- adjoint workspace ----
+  struct GradWork {
+    int nb = 0, kmax = 0, steps = 0;
+    std::vector<std::vector<double*>> lv;   // per level: the vectors of enum GW
+    std::vector<double*> D, SR;             // recorded d_i and S r_i of one smoother call
+    std::vector<double*> Et;                // e_0 .. e_steps
+    double *W = nullptr, *Z = nullptr, *EB = nullptr, *ZB = nullptr, *WB = nullptr;
+    double *part = nullptr, *acc = nullptr, *rows = nullptr, *coef = nullptr;
+  } gw;
 };
 
 namespace {
@@ -260,7 +272,7 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
   T* d = vec<T>(L, VD);
   T* y = vec<T>(L, VY);
   const T* S = invD_of<T>(L);
-  const double lmax = L.lmax;
+  const double lmax = L.lmax * c->lscale;
   zero<T>(c, y, span(c, L));
   if (!x_zero) apply_into<T>(c, j, x, y);
   if (c->o.kind == CHEBMG_CHEB_1ST) {
@@ -278,6 +290,7 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
     axpy<T>(n, 1.0, d, x, c->s, nb, ld);
   } else {
     const double* beta = (c->o.kind == CHEBMG_CHEB_4TH_OPT) ? kBeta[order - 1] : nullptr;
+    if (!c->beta_ovr.empty() && (int)c->beta_ovr.size() == order) beta = c->beta_ovr.data();
     cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), x_zero ? 1 : 0, c->s, nb, ld);
     for (int i = 1; i < order; ++i) {
       apply_into<T>(c, j, d, y);
@@ -1174,6 +1187,248 @@ int pcg_batched(chebmg_ctx* c, int nrhs, const double* B, int64_t ldb, double* U
   return bfcg_finish(c, U, ldu, iters, relres);
 }
 
+// ===========================================================================
+// Adjoint of the smoothed V-cycle (gradient of the error-reduction ratio)
+// ===========================================================================
+enum GW { GW_XB = 0, GW_BB, GW_X0B, GW_RB, GW_RHO, GW_DEL, GW_YA, GW_XM, GW_XS, GW_N };
+
+void grad_alloc(chebmg_ctx* c, int nb, int kmax, int steps) {
+  auto& g = c->gw;
+  if (g.nb >= nb && g.kmax >= kmax && g.steps >= steps) return;
+  CK(cudaStreamSynchronize(c->s));
+  auto take = [&](double*& p, int64_t count) {
+    void* v = p;
+    replace_alloc(c, v, sizeof(double) * (size_t)count);
+    p = static_cast<double*>(v);
+  };
+  nb = std::max(nb, g.nb);
+  kmax = std::max(kmax, g.kmax);
+  steps = std::max(steps, g.steps);
+  const int nl = (int)c->L.size();
+  g.lv.resize(nl);
+  for (int j = 0; j < nl; ++j) {
+    g.lv[j].resize(GW_N, nullptr);
+    for (int w = 0; w < GW_N; ++w) take(g.lv[j][w], (int64_t)nb * c->L[j].ld);
+  }
+  const int64_t v0 = (int64_t)nb * c->L[0].ld;
+  g.D.resize(kmax, nullptr);
+  g.SR.resize(kmax, nullptr);
+  for (int i = 0; i < kmax; ++i) {
+    take(g.D[i], v0);
+    take(g.SR[i], v0);
+  }
+  g.Et.resize(steps + 1, nullptr);
+  for (auto& p : g.Et) take(p, v0);
+  for (double** p : {&g.W, &g.Z, &g.EB, &g.ZB, &g.WB}) take(*p, v0);
+  take(g.part, adj_dot_scratch(c->L[0].n, nb));
+  take(g.acc, kmax + nl);
+  take(g.rows, 2 * (int64_t)nb);
+  take(g.coef, nb);
+  g.nb = nb;
+  g.kmax = kmax;
+  g.steps = steps;
+}
+
+// Forward V-cycle in FP64 (Eq. 2.2) that also keeps each level's iterate before the
+// post-smoother (the input of that smoother call, needed by its adjoint).
+int vcycle_store(chebmg_ctx* c, int j, const double* b, double* x) {
+  const int last = (int)c->L.size() - 1;
+  if (j == last) return coarse<double>(c, b, x);
+  Level& L = c->L[j];
+  Level& C = c->L[j + 1];
+  if (c->pre > 0) smooth<double>(c, j, b, x, c->pre, true);
+  else zero<double>(c, x, span(c, L));
+  double* y = vec<double>(L, VY);
+  double* r = vec<double>(L, VR);
+  zero<double>(c, y, span(c, L));
+  apply_into<double>(c, j, x, y);
+  residual<double>(L.n, b, y, r, c->s, c->nb, ldv(c, L));
+  restrict_to<double>(c, j, r, vec<double>(C, VB));
+  const int rc = vcycle_store(c, j + 1, vec<double>(C, VB), vec<double>(C, VX));
+  if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
+  prolong_to<double>(c, j, vec<double>(C, VX), x, 1);
+  if (c->post > 0) {
+    CK(cudaMemcpyAsync(c->gw.lv[j][GW_XM], x, sizeof(double) * span(c, L), cudaMemcpyDeviceToDevice, c->s));
+    smooth<double>(c, j, b, x, c->post, false);
+  }
+  check_launch();
+  return rc;
+}
+
+// Adjoint of one Algorithm-2 smoother call on level j (inputs b and x0, x0 = null for a zero
+// guess) for the output adjoint xbar: bbar += b-bar, x0bar = x0-bar (if x0), and the weight
+// and lambda adjoints accumulate into gw.acc[0 .. order-1] and gw.acc[kmax + j].
+void smooth_adj(chebmg_ctx* c, int j, const double* b, const double* x0, int order, const double* xbar,
+                double* bbar, double* x0bar) {
+  auto& g = c->gw;
+  Level& L = c->L[j];
+  const int nb = c->nb;
+  const int64_t n = L.n, ld = ldv(c, L), sp = span(c, L);
+  const double* S = static_cast<const double*>(L.invD[CHEBMG_F64]);
+  const double lam = L.lmax * c->lscale;
+  const std::vector<double>& beta = c->beta_ovr;
+  double* r = vec<double>(L, VR);
+  double* d = vec<double>(L, VD);
+  double* y = vec<double>(L, VY);
+  double* xs = g.lv[j][GW_XS];
+  // forward recomputation, recording d_i and S r_i
+  zero<double>(c, y, sp);
+  if (x0) {
+    CK(cudaMemcpyAsync(xs, x0, sizeof(double) * sp, cudaMemcpyDeviceToDevice, c->s));
+    apply_into<double>(c, j, xs, y);
+  }
+  cheb4_init<double>(n, b, xs, r, d, y, S, 4.0 / (3.0 * lam), x0 ? 0 : 1, c->s, nb, ld);
+  adj_record(n, ld, nb, d, r, S, g.D[0], g.SR[0], c->s);
+  for (int i = 1; i < order; ++i) {
+    zero<double>(c, y, sp);
+    apply_into<double>(c, j, d, y);
+    const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0);
+    const double c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lam);
+    cheb4_step<double>(n, xs, r, d, y, S, beta[i - 1], c1, c2, c->s, nb, ld);
+    adj_record(n, ld, nb, d, r, S, g.D[i], g.SR[i], c->s);
+  }
+  // backward
+  const int lslot = g.kmax + j;
+  for (int i = 1; i <= order; ++i) dot_accumulate(n, ld, nb, xbar, g.D[i - 1], 1.0, g.part, g.acc, i - 1, c->s);
+  double* rho = g.lv[j][GW_RHO];
+  double* del = g.lv[j][GW_DEL];
+  double* ya = g.lv[j][GW_YA];
+  lincomb(n, ld, nb, beta[order - 1], xbar, 0.0, nullptr, del, c->s);
+  zero<double>(c, rho, sp);
+  zero<double>(c, ya, sp);
+  for (int i = order - 1; i >= 1; --i) {
+    const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0);
+    const double c2 = (8.0 * i + 4.0) / (2.0 * i + 3.0);
+    adj_rho(n, ld, nb, c2 / lam, S, del, rho, c->s);
+    dot_accumulate(n, ld, nb, del, g.SR[i], -c2 / (lam * lam), g.part, g.acc, lslot, c->s);
+    apply_into<double>(c, j, rho, ya);
+    adj_delta(n, ld, nb, beta[i - 1], c1, xbar, del, ya, c->s);
+  }
+  adj_rho(n, ld, nb, 4.0 / (3.0 * lam), S, del, rho, c->s);
+  dot_accumulate(n, ld, nb, del, g.SR[0], -4.0 / (3.0 * lam * lam), g.part, g.acc, lslot, c->s);
+  lincomb(n, ld, nb, 1.0, bbar, 1.0, rho, bbar, c->s);
+  if (x0) {
+    zero<double>(c, ya, sp);
+    apply_into<double>(c, j, rho, ya);
+    lincomb(n, ld, nb, 1.0, xbar, -1.0, ya, x0bar, c->s);
+  }
+  check_launch();
+}
+
+// Transposed V-cycle from level j: bbar = B_j^T xbar, with the parameter adjoints accumulated.
+// Uses the forward state of the last vcycle_store (each level's right-hand side in VB, the
+// pre-post-smoother iterates in gw XM); b is level j's forward right-hand side.
+int vcycle_adj(chebmg_ctx* c, int j, const double* b, const double* xbar, double* bbar) {
+  auto& g = c->gw;
+  const int last = (int)c->L.size() - 1;
+  if (j == last) return coarse<double>(c, xbar, bbar);   // A_c^{-1} is symmetric
+  Level& L = c->L[j];
+  Level& C = c->L[j + 1];
+  const int nb = c->nb;
+  const int64_t n = L.n, ld = ldv(c, L), sp = span(c, L);
+  double* x0bar = g.lv[j][GW_X0B];
+  zero<double>(c, bbar, sp);
+  if (c->post > 0) smooth_adj(c, j, b, g.lv[j][GW_XM], c->post, xbar, bbar, x0bar);
+  else CK(cudaMemcpyAsync(x0bar, xbar, sizeof(double) * sp, cudaMemcpyDeviceToDevice, c->s));
+  // x_mid = x_pre + P x_c
+  restrict_to<double>(c, j, x0bar, g.lv[j + 1][GW_XB]);
+  const int rc = vcycle_adj(c, j + 1, vec<double>(C, VB), g.lv[j + 1][GW_XB], g.lv[j + 1][GW_BB]);
+  if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
+  // r_c = P^T (b - A x_pre)
+  double* rb = g.lv[j][GW_RB];
+  prolong_to<double>(c, j, g.lv[j + 1][GW_BB], rb, 0);
+  lincomb(n, ld, nb, 1.0, bbar, 1.0, rb, bbar, c->s);
+  double* ya = g.lv[j][GW_YA];
+  zero<double>(c, ya, sp);
+  apply_into<double>(c, j, rb, ya);
+  lincomb(n, ld, nb, 1.0, x0bar, -1.0, ya, x0bar, c->s);
+  if (c->pre > 0) smooth_adj(c, j, b, nullptr, c->pre, x0bar, bbar, nullptr);
+  check_launch();
+  return rc;
+}
+
+// f = mean_q ||(I - B A)^steps e0_q||^2 / ||e0_q||^2 and its gradient with respect to the
+// weights and the lambda_max scale, for nrhs initial errors E0 [nrhs][n] (device).
+int cycle_error_grad(chebmg_ctx* c, int nrhs, const double* E0, int steps, const double* betas, int nbeta,
+                     double scale, double* f_out, double* gbeta, double* gscale, double* f_each) {
+  if (c->o.kind == CHEBMG_CHEB_1ST) throw Error(CHEBMG_EINVAL, "the weights belong to the 4th-kind smoother");
+  if (nbeta != c->pre || (c->post != 0 && c->post != c->pre))
+    throw Error(CHEBMG_EINVAL, "one weight per smoothing step: nbeta must equal the smoothing order");
+  if (c->L.size() < 2) throw Error(CHEBMG_EINVAL, "need at least two levels");
+  reserve_batch(c, nrhs);
+  autotune_batch(c, nrhs);
+  grad_alloc(c, nrhs, nbeta, steps);
+  auto& g = c->gw;
+  struct Restore {
+    chebmg_ctx* c;
+    std::vector<double> b;
+    double s;
+    ~Restore() {
+      c->beta_ovr = b;
+      c->lscale = s;
+    }
+  } restore{c, c->beta_ovr, c->lscale};
+  c->beta_ovr.assign(betas, betas + nbeta);
+  c->lscale = scale;
+  BatchScope bs(c, nrhs);
+  Level& L = c->L[0];
+  const int64_t n = L.n, ld = ldv(c, L), sp = span(c, L);
+  const double* S = static_cast<const double*>(L.invD[CHEBMG_F64]);
+  CK(cudaMemsetAsync(c->dstat, 0, sizeof(unsigned) * 2, c->s));
+  masked_copy(n, E0, S, g.Et[0], c->s, nrhs, n, ld);
+  dot_rows(n, ld, nrhs, g.Et[0], g.Et[0], g.part, g.rows, c->s);
+  int rc = CHEBMG_OK;
+  for (int t = 0; t < steps; ++t) {
+    zero<double>(c, g.W, sp);
+    apply_into<double>(c, 0, g.Et[t], g.W);
+    rc = vcycle_store(c, 0, g.W, g.Z);
+    if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
+    lincomb(n, ld, nrhs, 1.0, g.Et[t], -1.0, g.Z, g.Et[t + 1], c->s);
+  }
+  dot_rows(n, ld, nrhs, g.Et[steps], g.Et[steps], g.part, g.rows + nrhs, c->s);
+  std::vector<double> rows(2 * (size_t)nrhs);
+  CK(cudaMemcpyAsync(rows.data(), g.rows, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  double f = 0.0;
+  std::vector<double> coef(nrhs);
+  for (int q = 0; q < nrhs; ++q) {
+    if (!(rows[q] > 0.0)) throw Error(CHEBMG_EINVAL, "an initial error is zero");
+    const double fq = rows[nrhs + q] / rows[q];
+    if (f_each) f_each[q] = fq;
+    f += fq / nrhs;
+    coef[q] = 2.0 / (nrhs * rows[q]);
+  }
+  *f_out = f;
+  CK(cudaMemcpyAsync(g.coef, coef.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->s));
+  scale_rows(n, ld, nrhs, g.coef, g.Et[steps], g.EB, c->s);
+  CK(cudaMemsetAsync(g.acc, 0, sizeof(double) * (g.kmax + c->L.size()), c->s));
+  for (int t = steps - 1; t >= 0; --t) {
+    lincomb(n, ld, nrhs, -1.0, g.EB, 0.0, nullptr, g.ZB, c->s);
+    zero<double>(c, g.W, sp);
+    apply_into<double>(c, 0, g.Et[t], g.W);
+    rc = vcycle_store(c, 0, g.W, g.Z);                  // recomputed forward state of cycle t
+    if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
+    rc = vcycle_adj(c, 0, g.W, g.ZB, g.WB);
+    if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
+    double* ya = g.lv[0][GW_YA];
+    zero<double>(c, ya, sp);
+    apply_into<double>(c, 0, g.WB, ya);
+    lincomb(n, ld, nrhs, 1.0, g.EB, 1.0, ya, g.EB, c->s);
+  }
+  std::vector<double> acc(g.kmax + c->L.size());
+  CK(cudaMemcpyAsync(acc.data(), g.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaMemcpyAsync(c->hdstat, c->dstat, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  check_launch();
+  if (c->hdstat[0]) return CHEBMG_ETIMEOUT;
+  if (c->hdstat[1] == CS_BREAKDOWN) return CHEBMG_EBREAKDOWN;
+  for (int i = 0; i < nbeta; ++i) gbeta[i] = acc[i];
+  double gs = 0.0;
+  for (size_t j = 0; j + 1 < c->L.size(); ++j) gs += acc[g.kmax + j] * c->L[j].lmax;
+  *gscale = gs;
+  return CHEBMG_OK;
+}
+
 }  // namespace
 
 // A fixed set of contexts (meshes of different sizes and orders) solved together: one
@@ -1790,6 +2045,31 @@ int chebmg_vcycle_batched(chebmg_ctx* c, int nrhs, const double* R, double* Z) {
     if (c->hdstat[0]) return CHEBMG_ETIMEOUT;
     if (c->hdstat[1] == CS_BREAKDOWN) return CHEBMG_EBREAKDOWN;
     return rc == CHEBMG_ENOTCONV ? CHEBMG_OK : rc;
+  });
+}
+
+int chebmg_cycle_error_grad(chebmg_ctx* c, int nrhs, const double* E0, int steps, const double* betas,
+                            int nbeta, double lmax_scale, double* f, double* grad_betas, double* grad_scale,
+                            double* f_each) {
+  return guard([&]() -> int {
+    enter(c);
+    if (!E0 || !betas || !f || !grad_betas || !grad_scale || nrhs < 1 || nrhs > 65535 || steps < 1 ||
+        steps > 64 || nbeta < 1 || nbeta > 64 || !(lmax_scale > 0.0))
+      throw Error(CHEBMG_EINVAL, "bad gradient arguments");
+    return cycle_error_grad(c, nrhs, E0, steps, betas, nbeta, lmax_scale, f, grad_betas, grad_scale, f_each);
+  });
+}
+
+int chebmg_set_smoother_weights(chebmg_ctx* c, const double* betas, int nbeta, double lmax_scale) {
+  return guard([&]() -> int {
+    enter(c);
+    if (nbeta < 0 || nbeta > 64 || (nbeta > 0 && !betas) || !(lmax_scale > 0.0))
+      throw Error(CHEBMG_EINVAL, "bad smoother weights");
+    if (nbeta > 0 && c->o.kind == CHEBMG_CHEB_1ST) throw Error(CHEBMG_EINVAL, "weights need the 4th kind");
+    c->beta_ovr.assign(betas, betas + nbeta);
+    c->lscale = lmax_scale;
+    drop_graphs(c);
+    return CHEBMG_OK;
   });
 }
 

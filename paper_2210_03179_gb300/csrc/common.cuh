@@ -215,6 +215,30 @@ struct CoarseBlock {
 bool coarse_block_supported(int64_t n);
 bool coarse_block_launch(const CoarseBlock& a, int nb, cudaStream_t s);
 
+// ---- adjoint V-cycle (adjoint.cu), FP64, batched at leading dimension ld ----
+// Dout = d, SRout = S r
+void adj_record(int64_t n, int64_t ld, int nb, const double* d, const double* r, const double* S, double* Dout,
+                double* SRout, cudaStream_t s);
+// rho += a S delta
+void adj_rho(int64_t n, int64_t ld, int nb, double a, const double* S, const double* delta, double* rho,
+             cudaStream_t s);
+// delta = beta xbar + c1 delta - y; y = 0
+void adj_delta(int64_t n, int64_t ld, int nb, double beta, double c1, const double* xbar, double* delta, double* y,
+               cudaStream_t s);
+// out = a x + b y (y may be null); out may alias x or y
+void lincomb(int64_t n, int64_t ld, int nb, double a, const double* x, double b, const double* y, double* out,
+             cudaStream_t s);
+// out_q = coef[q] x_q (coef on the device)
+void scale_rows(int64_t n, int64_t ld, int nb, const double* coef, const double* x, double* out, cudaStream_t s);
+// scratch doubles needed by the two dot routines below
+int adj_dot_scratch(int64_t n, int nb);
+// acc[slot] += coef * sum_q <a_q, b_q>  (deterministic order)
+void dot_accumulate(int64_t n, int64_t ld, int nb, const double* a, const double* b, double coef, double* part,
+                    double* acc, int slot, cudaStream_t s);
+// out[q] = <a_q, b_q>
+void dot_rows(int64_t n, int64_t ld, int nb, const double* a, const double* b, double* part, double* out,
+              cudaStream_t s);
+
 // ---- Lanczos helpers ----
 void splitmix_fill(int64_t n, uint64_t seed, const double* invD, double* v, cudaStream_t s);
 // t = sqrt(invD) * v
