@@ -254,6 +254,52 @@ def bench_batched(cm, W, torch, timed, reps):
     return out
 
 
+DIFF_NRHS, DIFF_ADAM_STEPS = 16, 200
+
+
+def bench_differentiation(cm, W, torch, timed, reps):
+    """Gradient of mean ||(I - B A)^3 e0||^2 / ||e0||^2 over 16 e0 with respect to the k = 4
+    weights and the lambda_max scale (symmetric (4,4) cycles, FP64 adjoint on the GPU) on
+    FD 255 x 255 and SEM E = 8^3, N = 7: time per objective, per gradient and per central-
+    difference gradient, and 200 Adam steps from the plain 4th kind beside the paper's
+    optimized weights (Table 5)."""
+    import numpy as np
+    from paper_2210_03179_gb300 import tuning
+    table4 = [1.00391310427285, 1.04035811188593, 1.14863498546254, 1.38268869241000]
+    cases = []
+    fd = cm.Solver("fd2d", m=255, kind="4th", order=4, sided="symmetric")
+    cases.append(("FD 255x255, 6 levels to 7x7", fd, torch.tensor(W.random_vectors(255 * 255, DIFF_NRHS, 0),
+                                                                    device="cuda")))
+    v = W.sem_box_vertices(BATCH_NE, BATCH_NE, BATCH_NE)
+    sem = cm.Solver("sem", verts=v, orders=ORDERS, kind="4th", order=4, sided="symmetric")
+    mask = W.sem_boundary_mask(BATCH_NE, BATCH_NE, BATCH_NE, NORDER)
+    cases.append((f"SEM E={BATCH_NE}^3 N={NORDER}, p-MG {ORDERS}", sem,
+                  torch.tensor(W.random_vectors(sem.size(0), DIFF_NRHS, 0) * ~mask[None, :], device="cuda")))
+    out = []
+    for name, s, E0 in cases:
+        ones = [1.0] * 4
+        cm.chebmg_cycle_error_grad(s.ctx, E0, ones, 1.0)
+        t_obj, _ = timed(lambda: cm.chebmg_cycle_error(s.ctx, E0, ones, 1.0), reps)
+        t_grad, _ = timed(lambda: cm.chebmg_cycle_error_grad(s.ctx, E0, ones, 1.0), reps)
+        f_plain = cm.chebmg_cycle_error(s.ctx, E0, ones, 1.0)[0]
+        f_table = cm.chebmg_cycle_error(s.ctx, E0, table4, 1.0)[0]
+        b_t, s_t, hist = tuning.tune_weights(s.ctx, E0, ones, 1.0, iters=DIFF_ADAM_STEPS, lr=0.01)
+        f_tuned = cm.chebmg_cycle_error(s.ctx, E0, b_t.tolist(), s_t)[0]
+        b_w, s_w, _ = tuning.tune_weights(s.ctx, E0, ones, 1.0, iters=DIFF_ADAM_STEPS, lr=0.01, tune_scale=False)
+        f_tuned_w = cm.chebmg_cycle_error(s.ctx, E0, b_w.tolist(), 1.0)[0]
+        out.append({"workload": name + f", symmetric (4,4), {DIFF_NRHS} e0, 3 cycles",
+                    "n_dof": s.size(0), "objective_ms": t_obj * 1e3, "gradient_ms": t_grad * 1e3,
+                    "central_difference_gradient_ms": 2 * 5 * t_obj * 1e3,
+                    "f": {"plain_4th_kind": f_plain, "paper_optimized_table5": f_table,
+                          "adam_weights_only": f_tuned_w, "adam_weights_and_scale": f_tuned},
+                    "weights": {"paper_table5": table4, "adam_weights_only": [float(x) for x in b_w],
+                                "adam_weights_and_scale": [float(x) for x in b_t], "adam_scale": s_t},
+                    "adam_steps": DIFF_ADAM_STEPS})
+    fd.close()
+    sem.close()
+    return out
+
+
 def main():
     global NE
     ap = argparse.ArgumentParser()
@@ -263,6 +309,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched / grouped measurements")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="set up the 64-RHS E=8^3 batch, warm up, run one batched solve (kernels launched "
+                         "one by one) inside the NVTX range 'bsolve' and exit")
+    ap.add_argument("--no-diff", action="store_true", help="skip the gradient / weight-tuning measurements")
+    ap.add_argument("--diff-only", action="store_true",
+                    help="only the gradient / weight-tuning measurements (printed as one JSON object)")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched / grouped measurements (printed as one JSON object)")
     ap.add_argument("--ne", type=int, default=NE,
@@ -325,6 +377,22 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    if args.profile_batched:
+        v = W.sem_box_vertices(BATCH_NE, BATCH_NE, BATCH_NE)
+        s = cm.Solver("sem", verts=v, prec="mixed", orders=ORDERS, kind=KIND, order=K_ORDER, sided=SIDED)
+        B = torch.tensor(np.stack([W.sem_rhs(BATCH_NE, BATCH_NE, BATCH_NE, NORDER, seed=q)
+                                   for q in range(BATCH_NRHS)]), device="cuda")
+        U = torch.zeros_like(B)
+        cm.chebmg_pcg_solve_batched(s.ctx, B, U, RTOL, 500, graph=False)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bsolve")
+        code, its, rel = cm.chebmg_pcg_solve_batched(s.ctx, B, U, RTOL, 500, graph=False)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_batched": BATCH_NRHS, "code": code, "iterations": max(its)}))
+        s.close()
+        return 0
+
     verts = W.sem_box_vertices(NE, NE, NE)
     b_np = W.sem_rhs(NE, NE, NE, NORDER)
     n = b_np.size
@@ -385,6 +453,12 @@ def main():
         e1.synchronize()
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps), out
+
+    if args.diff_only:
+        s32.close()
+        s64.close()
+        print(json.dumps({"differentiation": bench_differentiation(cm, W, torch, timed, max(1, args.steps))}))
+        return 0
 
     if args.batched_only:
         s32.close()
@@ -469,6 +543,10 @@ def main():
         s32.close()
         s64.close()
         line["batched"] = bench_batched(cm, W, torch, timed, max(1, min(args.steps, 3)))
+    if not args.no_diff:
+        s32.close()
+        s64.close()
+        line["differentiation"] = bench_differentiation(cm, W, torch, timed, max(1, min(args.steps, 3)))
     if rank == 0 and not args.no_cpu_baseline:
         r = run_oracle(1)
         t = r["times"][0]

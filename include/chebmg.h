@@ -240,7 +240,8 @@ void chebmg_group_destroy(chebmg_group* group);
  * instead of being stored, all nrhs errors as one batch; the coarse solve is taken as the
  * linear map A_c^{-1} (its tolerance, coarse_rtol, bounds the error of that reading).
  * Needs a 4th-kind context (CHEBMG_CHEB_4TH or _4TH_OPT) with nbeta equal to the smoothing
- * order (pre, and post if nonzero).  The context's own weights are left unchanged. */
+ * order (pre, and post if nonzero).  The context's own weights are left unchanged.
+ * grad_betas and grad_scale both NULL: the objective only (no adjoint pass). */
 int chebmg_cycle_error_grad(chebmg_ctx* ctx, int nrhs, const double* E0, int steps,
                             const double* betas, int nbeta, double lmax_scale, double* f,
                             double* grad_betas, double* grad_scale, double* f_each);

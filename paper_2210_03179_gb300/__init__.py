@@ -364,6 +364,20 @@ def chebmg_cycle_error_grad(ctx, E0, betas, lmax_scale=1.0, steps=3):
     return f.value, list(gb), gs.value, list(fe)
 
 
+def chebmg_cycle_error(ctx, E0, betas, lmax_scale=1.0, steps=3):
+    """The objective of chebmg_cycle_error_grad alone: (f, f_each list)."""
+    n = chebmg_level_size(ctx, 0)
+    if E0.dim() != 2 or E0.shape[1] != n:
+        raise ValueError(f"E0 must have shape (nrhs, {n})")
+    nrhs = E0.shape[0]
+    k = len(betas)
+    b = (c_double * k)(*[float(v) for v in betas])
+    f, fe = c_double(), (c_double * nrhs)()
+    _check(lib().chebmg_cycle_error_grad(ctx, nrhs, _ptr(E0, nrhs * n, CHEBMG_F64, "E0"), int(steps), b, k,
+                                         float(lmax_scale), byref(f), None, None, fe), "chebmg_cycle_error_grad")
+    return f.value, list(fe)
+
+
 def chebmg_set_smoother_weights(ctx, betas=(), lmax_scale=1.0):
     k = len(betas)
     b = (c_double * max(k, 1))(*[float(v) for v in betas])

@@ -1399,6 +1399,7 @@ int cycle_error_grad(chebmg_ctx* c, int nrhs, const double* E0, int steps, const
     coef[q] = 2.0 / (nrhs * rows[q]);
   }
   *f_out = f;
+  if (!gbeta) return CHEBMG_OK;   // objective only
   CK(cudaMemcpyAsync(g.coef, coef.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->s));
   scale_rows(n, ld, nrhs, g.coef, g.Et[steps], g.EB, c->s);
   CK(cudaMemsetAsync(g.acc, 0, sizeof(double) * (g.kmax + c->L.size()), c->s));
@@ -2053,7 +2054,7 @@ int chebmg_cycle_error_grad(chebmg_ctx* c, int nrhs, const double* E0, int steps
                             double* f_each) {
   return guard([&]() -> int {
     enter(c);
-    if (!E0 || !betas || !f || !grad_betas || !grad_scale || nrhs < 1 || nrhs > 65535 || steps < 1 ||
+    if (!E0 || !betas || !f || (!grad_betas) != (!grad_scale) || nrhs < 1 || nrhs > 65535 || steps < 1 ||
         steps > 64 || nbeta < 1 || nbeta > 64 || !(lmax_scale > 0.0))
       throw Error(CHEBMG_EINVAL, "bad gradient arguments");
     return cycle_error_grad(c, nrhs, E0, steps, betas, nbeta, lmax_scale, f, grad_betas, grad_scale, f_each);

@@ -48,7 +48,7 @@ def tune_weights(solver_ctx, E0, betas0, scale0=1.0, steps=3, iters=200, lr=0.01
         f = error_ratio(solver_ctx, E0, betas, scale, steps)
         f.backward()
         opt.step()
-        hist.append(float(f))
+        hist.append(float(f.detach()))
         with torch.no_grad():
             scale.clamp_(min=0.05)
     return betas.detach().clone(), float(scale.detach()), hist
