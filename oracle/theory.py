@@ -119,3 +119,70 @@ def critical_C_opt4th(k):                  # Eq. 2.26
 def grid_complexity(nnz_per_level):        # Eq. 3.2
     nnz = np.asarray(nnz_per_level, dtype=np.float64)
     return float(nnz.sum() / nnz[0])
+
+
+def _fourth_kind_directions(k: int, lam):
+    """d_0 .. d_{k-1} of Algorithm 2 on the scalar problem (A = lambda, S = 1, lambda_max = 1,
+    b = 1, x0 = 0), as columns: x_k = sum_i beta_i d_{i-1}, so p(lambda) = 1 - lambda x_k is
+    affine in the weights."""
+    r = np.ones_like(lam)
+    d = (4.0 / 3.0) * r
+    cols = [d.copy()]
+    for i in range(1, k):
+        r = r - lam * d
+        d = (2.0 * i - 1.0) / (2.0 * i + 3.0) * d + (8.0 * i + 4.0) / (2.0 * i + 3.0) * r
+        cols.append(d.copy())
+    return np.stack(cols, axis=1)
+
+
+def optimal_betas(k: int, npts: int = 8000, rounds: int = 2):
+    """Weights beta_1..beta_k of Algorithm 2 that maximise gamma^{-1} (Eq. 2.14), the
+    criterion of the optimized 4th kind (Sec. 2.3, Table 5).
+
+    lambda p^2 / (1 - p^2) <= t is |p(lambda)| <= c_t = sqrt(t / (lambda + t)); as p is affine in
+    the weights, for a fixed t the feasible weights on a set of lambda points form a polyhedron.
+    Bisection on t with a linear-programming feasibility test (maximal common slack) gives the
+    smallest feasible t, i.e. the largest gamma^{-1}.  The points are Chebyshev-spaced on (0, 1],
+    then the local maxima of lambda p^2 / (1 - p^2) for the computed weights are added and the
+    bisection is repeated.  Returns (betas, gamma^{-1})."""
+    from scipy.optimize import linprog
+
+    theta = np.linspace(0.0, np.pi, npts + 1)[1:]
+    lam = 0.5 * (1.0 - np.cos(theta))
+
+    def slack(G, lm, t):
+        c = np.sqrt(t / (lm + t))
+        lo, hi = 1.0 / ((lm + t) * (1.0 + c)), (1.0 + c) / lm   # (1 - c) / lambda without cancellation
+        w = 0.5 * (hi - lo)
+        A = np.vstack([np.hstack([-G, w[:, None]]), np.hstack([G, w[:, None]])])
+        rhs = np.concatenate([-lo, hi])
+        cost = np.zeros(k + 1)
+        cost[-1] = -1.0
+        res = linprog(cost, A_ub=A, b_ub=rhs, bounds=[(None, None)] * k + [(None, 1.0)], method="highs")
+        return res.x[-1], res.x[:k]
+
+    def solve(lm):
+        G = _fourth_kind_directions(k, lm)
+        g_est = 4.0 / np.pi ** 2 * (2 * k + 1) ** 2 - 2.0 / 3.0
+        lo_t, hi_t = 0.25 / g_est, 4.0 / g_est
+        for _ in range(80):
+            mid = np.sqrt(lo_t * hi_t)
+            if slack(G, lm, mid)[0] >= 0.0:
+                hi_t = mid
+            else:
+                lo_t = mid
+            if hi_t / lo_t - 1.0 < 1e-13:
+                break
+        return slack(G, lm, hi_t)[1]
+
+    betas = solve(lam)
+    for _ in range(rounds):
+        fine = 0.5 * (1.0 - np.cos(np.linspace(0.0, np.pi, 40 * npts + 1)[1:]))
+        x = _fourth_kind_directions(k, fine) @ betas
+        p = 1.0 - fine * x
+        f = p * p / (x * (1.0 + p))          # lambda p^2 / (1 - p^2) with 1 - p = lambda x
+        peaks = np.where((f[1:-1] >= f[:-2]) & (f[1:-1] >= f[2:]))[0] + 1
+        lam = np.unique(np.concatenate([lam, fine[peaks], fine[np.clip(peaks - 1, 0, None)],
+                                        fine[np.clip(peaks + 1, None, len(fine) - 1)]]))
+        betas = solve(lam)
+    return betas, gamma_inv("opt4th", k, betas=betas)

@@ -129,3 +129,30 @@ def test_smoother_on_vectors_matches_scalar_polynomial():
             x = chebyshev_4th(lambda v: Adiag * v, S, b, k, 3.0, betas=bt)
         p = T.smoothing_polynomial(kind, k, lam)
         np.testing.assert_allclose(e0 - x, p * e0, atol=1e-13)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_gamma_maximising_weights_reproduce_table5(k):
+    # the optimizer behind the weights of orders beyond Table 5 recovers the table's rows
+    b, gi = T.optimal_betas(k, npts=4000, rounds=1)
+    assert np.abs(b - np.array(BETA_TABLE[k])).max() < 2e-6
+    assert gi == pytest.approx(T.gamma_inv("opt4th", k), rel=2e-6)
+
+
+def test_stored_weights_beyond_table5_are_optimal():
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "optimal_betas.json")))
+    for key, rec in gold["orders"].items():
+        k = int(key)
+        b = np.array(rec["betas"])
+        assert len(b) == k
+        g0 = T.gamma_inv("opt4th", k, betas=b)
+        assert g0 == pytest.approx(rec["gamma_inv"], rel=1e-9)
+        assert abs(g0 / T.gamma_inv_opt4th(k) - 1) < 0.01             # Eq. 2.20
+        assert g0 > 1.2 * T.gamma_inv("4th", k)                        # above the 4th kind (ratio -> 12/pi^2)
+        for i in (0, k // 2, k - 1):                                   # locally optimal
+            for s in (-1, 1):
+                bp = b.copy()
+                bp[i] *= 1 + s * 3e-3
+                assert T.gamma_inv("opt4th", k, betas=bp) <= g0 * (1 + 1e-7)
