@@ -161,6 +161,16 @@ int chebmg_vcycle(chebmg_ctx* ctx, const double* r, double* z);
 int chebmg_pcg_solve(chebmg_ctx* ctx, const double* b, double* u, double rtol, int maxit,
                      int* iters, double* relres, double* history);
 
+/* Restarted flexible GMRES(restart) (x0 = 0), right preconditioned by one V-cycle per
+ * iteration, classical Gram-Schmidt: the outer solver of the paper's experiments (Sec. 6.1) and
+ * of its FD study (Table 1, Sec. 3).  Stops when the true relative residual ||b - A u|| / ||b||
+ * <= rtol at the end of a restart cycle (a cycle ends early when the least-squares residual
+ * estimate reaches rtol).  iters = Arnoldi steps = preconditioner applications.  history: host,
+ * maxit+1 doubles of residual estimates, or NULL.  1 <= restart <= 64.  Returns ENOTCONV
+ * (u and relres valid) after maxit steps. */
+int chebmg_gmres_solve(chebmg_ctx* ctx, const double* b, double* u, double rtol, int restart,
+                       int maxit, int* iters, double* relres, double* history);
+
 /* Same as chebmg_pcg_solve with HOST b and u: copies b in and u out on the
  * context stream (end-to-end entry point). */
 int chebmg_pcg_solve_host(chebmg_ctx* ctx, const double* b_host, double* u_host, double rtol,

@@ -91,6 +91,8 @@ _SIGNATURES = {
     "chebmg_vcycle": (c_int, [c_void_p, c_void_p, c_void_p]),
     "chebmg_pcg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int),
                                  POINTER(c_double), POINTER(c_double)]),
+    "chebmg_gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, POINTER(c_int),
+                                   POINTER(c_double), POINTER(c_double)]),
     "chebmg_pcg_solve_host": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_double, c_int,
                                       POINTER(c_int), POINTER(c_double)]),
     "chebmg_fd_smooth_noalloc": (c_int, [c_int, c_double, c_double, c_int, c_int, c_double, c_double, c_void_p,
@@ -293,6 +295,18 @@ def chebmg_pcg_solve(ctx, b, u, rtol=1e-8, maxit=500, history=False):
     code = _check(lib().chebmg_pcg_solve(ctx, _ptr(b, n, CHEBMG_F64, "b"), _ptr(u, n, CHEBMG_F64, "u"),
                                          float(rtol), int(maxit), byref(it), byref(rel), hist),
                   "chebmg_pcg_solve", allow=(CHEBMG_ENOTCONV,))
+    h = list(hist)[: it.value + 1] if history else None
+    return code, it.value, rel.value, h
+
+
+def chebmg_gmres_solve(ctx, b, u, rtol=1e-6, restart=20, maxit=500, history=False):
+    """Returns (status, iterations, relres, history-or-None); raises on errors other than ENOTCONV."""
+    n = chebmg_level_size(ctx, 0)
+    it, rel = c_int(), c_double()
+    hist = (c_double * (maxit + 1))() if history else None
+    code = _check(lib().chebmg_gmres_solve(ctx, _ptr(b, n, CHEBMG_F64, "b"), _ptr(u, n, CHEBMG_F64, "u"),
+                                           float(rtol), int(restart), int(maxit), byref(it), byref(rel), hist),
+                  "chebmg_gmres_solve", allow=(CHEBMG_ENOTCONV,))
     h = list(hist)[: it.value + 1] if history else None
     return code, it.value, rel.value, h
 

@@ -166,6 +166,12 @@ struct chebmg_ctx {
     double *W = nullptr, *Z = nullptr, *EB = nullptr, *ZB = nullptr, *WB = nullptr;
     double *part = nullptr, *acc = nullptr, *rows = nullptr, *coef = nullptr;
   } gw;
+  // ---- GMRES workspace ----
+  struct GmresWork {
+    int m = 0;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *bm = nullptr, *part = nullptr, *h = nullptr;
+    double* hh = nullptr;   // pinned host copy of a Hessenberg column
+  } gm;
 };
 
 namespace {
@@ -813,6 +819,7 @@ void destroy_ctx(chebmg_ctx* c) {
   for (auto& g : c->gexec)
     if (g) cudaGraphExecDestroy(g);
   if (c->gs) cudaStreamDestroy(c->gs);
+  if (c->gm.hh) cudaFreeHost(c->gm.hh);
   delete c;
 }
 
@@ -1428,6 +1435,128 @@ int cycle_error_grad(chebmg_ctx* c, int nrhs, const double* E0, int steps, const
   for (size_t j = 0; j + 1 < c->L.size(); ++j) gs += acc[g.kmax + j] * c->L[j].lmax;
   *gscale = gs;
   return CHEBMG_OK;
+}
+
+// ===========================================================================
+// Restarted flexible GMRES(m) preconditioned by one V-cycle (Sec. 6.1; Table 1 of Sec. 3)
+// ===========================================================================
+int gmres_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int m, int maxit, int* iters,
+                double* relres, double* history) {
+  Level& L = c->L[0];
+  const int64_t n = L.n, ld = L.ld;
+  auto& g = c->gm;
+  if (g.m < m) {
+    CK(cudaStreamSynchronize(c->s));
+    replace_vec(c, g.V, (int64_t)(m + 1) * ld);
+    replace_vec(c, g.Z, (int64_t)m * ld);
+    replace_vec(c, g.w, ld);
+    replace_vec(c, g.bm, ld);
+    replace_vec(c, g.part, gmres_part_size(n));
+    replace_vec(c, g.h, m + 2);
+    if (g.hh) cudaFreeHost(g.hh);
+    g.hh = nullptr;
+    void* hp = nullptr;
+    CK(cudaMallocHost(&hp, sizeof(double) * (m + 2)));
+    g.hh = static_cast<double*>(hp);
+    g.m = m;
+  }
+  const double* S = static_cast<const double*>(L.invD[CHEBMG_F64]);
+  reset_coarse_sticky(c);
+  CK(cudaMemsetAsync(c->dstat, 0, sizeof(unsigned), c->s));
+  masked_copy(n, b, S, g.bm, c->s);
+  zero<double>(c, u, n);
+  double* r = g.w;
+  CK(cudaMemcpyAsync(r, g.bm, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
+  auto read_norm = [&]() {
+    CK(cudaMemcpyAsync(g.hh, g.h, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return g.hh[0];
+  };
+  gmres_norm_scale(n, r, g.part, g.h, nullptr, c->s);
+  const double bnorm = read_norm();
+  if (iters) *iters = 0;
+  if (history) history[0] = 1.0;
+  if (!std::isfinite(bnorm)) return CHEBMG_EBREAKDOWN;
+  if (bnorm == 0.0) {
+    if (relres) *relres = 0.0;
+    return CHEBMG_OK;
+  }
+  double beta = bnorm;
+  int its = 0;
+  std::vector<double> R((size_t)m * (m + 1)), cs(m), sn(m), gv(m + 1), y(m);
+  while (its < maxit) {
+    // v_0 = r / beta
+    gmres_norm_scale(n, r, g.part, g.h, g.V, c->s);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jd = 0;
+    double est = 1.0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = g.V + (int64_t)j * ld;
+      double* zj = g.Z + (int64_t)j * ld;
+      const int rc = vcycle_top(c, vj, zj);
+      if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
+      zero<double>(c, g.w, n);
+      apply_into<double>(c, 0, zj, g.w);
+      gmres_mdot(n, ld, j + 1, g.V, g.w, g.part, g.h, c->s);
+      gmres_maxpy_norm(n, ld, j + 1, g.V, g.h, -1.0, g.w, g.part, g.h + j + 1, g.V + (int64_t)(j + 1) * ld, c->s);
+      check_launch();
+      CK(cudaMemcpyAsync(g.hh, g.h, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->s));
+      CK(cudaMemcpyAsync(c->hdstat, c->dstat, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, c->s));
+      if (c->cctl) CK(cudaMemcpyAsync(c->hcctl, c->cctl, sizeof(unsigned) * 5, cudaMemcpyDeviceToHost, c->s));
+      CK(cudaStreamSynchronize(c->s));
+      ++its;
+      const int crc = coarse_sticky_error(c);
+      if (crc != CHEBMG_OK) {
+        if (iters) *iters = its;
+        return crc;
+      }
+      double* col = R.data() + (size_t)j * (m + 1);
+      for (int i = 0; i <= j + 1; ++i) col[i] = g.hh[i];
+      if (!std::isfinite(col[j + 1])) {
+        if (iters) *iters = its;
+        return CHEBMG_EBREAKDOWN;
+      }
+      const double hlast = col[j + 1];
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      cs[j] = den > 0.0 ? col[j] / den : 1.0;
+      sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      est = std::fabs(gv[j + 1]) / bnorm;
+      if (history) history[its] = est;
+      jd = j + 1;
+      if (est <= rtol || hlast == 0.0 || its >= maxit) break;
+    }
+    // y = R^{-1} g, u += Z y
+    for (int i = jd - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int k = i + 1; k < jd; ++k) t -= R[(size_t)k * (m + 1) + i] * y[k];
+      const double d = R[(size_t)i * (m + 1) + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+    CK(cudaMemcpyAsync(g.h, y.data(), sizeof(double) * jd, cudaMemcpyHostToDevice, c->s));
+    gmres_maxpy_norm(n, ld, jd, g.Z, g.h, 1.0, u, nullptr, nullptr, nullptr, c->s);
+    // true residual r = b - A u
+    zero<double>(c, g.w, n);
+    apply_into<double>(c, 0, u, g.w);
+    lincomb(n, n, 1, 1.0, g.bm, -1.0, g.w, g.w, c->s);   // w = b - A u
+    gmres_norm_scale(n, r, g.part, g.h, nullptr, c->s);
+    beta = read_norm();
+    const double rel = beta / bnorm;
+    if (iters) *iters = its;
+    if (relres) *relres = rel;
+    if (!std::isfinite(rel)) return CHEBMG_EBREAKDOWN;
+    if (rel <= rtol) return CHEBMG_OK;
+  }
+  return CHEBMG_ENOTCONV;
 }
 
 }  // namespace
@@ -2157,6 +2286,16 @@ void chebmg_group_destroy(chebmg_group* g) {
   if (g->fork) cudaEventDestroy(g->fork);
   if (g->s) cudaStreamDestroy(g->s);
   delete g;
+}
+
+int chebmg_gmres_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int restart, int maxit, int* iters,
+                       double* relres, double* history) {
+  return guard([&]() -> int {
+    enter(c);
+    if (!b || !u || maxit < 0 || !(rtol > 0.0) || restart < 1 || restart + 1 > gmres_max_basis())
+      throw Error(CHEBMG_EINVAL, "bad GMRES arguments");
+    return gmres_solve(c, b, u, rtol, restart, maxit, iters, relres, history);
+  });
 }
 
 int chebmg_selftest_coarse_timeout(chebmg_ctx* c, int* status) {

@@ -239,6 +239,18 @@ void dot_accumulate(int64_t n, int64_t ld, int nb, const double* a, const double
 void dot_rows(int64_t n, int64_t ld, int nb, const double* a, const double* b, double* part, double* out,
               cudaStream_t s);
 
+// ---- restarted flexible GMRES (gmres.cu), FP64; V, Z: [nv][ld] ----
+int gmres_max_basis();                 // restart + 1 at most
+int gmres_part_size(int64_t n);        // doubles of scratch for the routines below
+// h[i] = <V_i, w>, i < nv (device h)
+void gmres_mdot(int64_t n, int64_t ld, int nv, const double* V, const double* w, double* part, double* h,
+                cudaStream_t s);
+// w += sign * sum_i h[i] V_i; if hn: *hn = ||w|| (device), and if wn: wn = w / ||w||
+void gmres_maxpy_norm(int64_t n, int64_t ld, int nv, const double* V, const double* h, double sign, double* w,
+                      double* part, double* hn, double* wn, cudaStream_t s);
+// *hn = ||w|| and (if wn) wn = w / ||w||
+void gmres_norm_scale(int64_t n, const double* w, double* part, double* hn, double* wn, cudaStream_t s);
+
 // ---- Lanczos helpers ----
 void splitmix_fill(int64_t n, uint64_t seed, const double* invD, double* v, cudaStream_t s);
 // t = sqrt(invD) * v
