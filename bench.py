@@ -254,6 +254,55 @@ def bench_batched(cm, W, torch, timed, reps):
     return out
 
 
+# Table 1 (Sec. 3): configuration with the fewest fine mat-vecs per row, GMRES(20) to 1e-6, n = 128
+TABLE1 = [  # Lx, coarsening, complexity, kind, m, n, matvecs, iterations (printed)
+    (1, 2, 1.568, "4th", 2, 2, 20, 4), (8, 2, 1.568, "4th", 14, 0, 75, 5),
+    (64, 2, 1.568, "opt4th", 20, 0, 252, 12), (128, 2, 1.568, "opt4th", 20, 0, 252, 12),
+    (1, 8, 1.023, "4th", 7, 7, 60, 4), (8, 8, 1.023, "opt4th", 14, 0, 195, 13),
+    (64, 8, 1.023, "opt4th", 18, 0, 323, 17), (128, 8, 1.023, "opt4th", 20, 0, 294, 14)]
+
+
+def bench_fd_table1(cm, torch, timed, reps):
+    """The paper's FD study on the GPU: each Table 1 row whose smoothing order has tabulated
+    weights (order <= 16; Table 5 stops there), with the GPU's own Lanczos lambda_max,
+    u = sin(3 pi x / Lx) sin(4 pi y) + g (g uniform[-1,1], seed 0), b = A u."""
+    import numpy as np
+    out = []
+    for Lx, c, cx, kind, m, nn, mv, its in TABLE1:
+        row = {"Lx": Lx, "coarsening": c, "kind": kind, "m": m, "n": nn,
+               "paper": {"iterations": its, "matvecs": mv, "grid_complexity": cx}}
+        if m + nn > 16:
+            row["skipped"] = "smoothing order above 16: Table 5 lists no weights (the library takes them " \
+                             "through chebmg_set_smoother_weights; the GPU tests run this row)"
+            out.append(row)
+            continue
+        k, sided = (m // 2, "one-sided") if nn == 0 else (m, "symmetric")
+        s = cm.Solver("fd2d", m=127, Lx=float(Lx), Ly=1.0, coarsening=c, coarsest=1, kind=kind, order=k,
+                      sided=sided)
+        sizes = [int(round(s.size(j) ** 0.5)) for j in range(s.num_levels)]
+        nnz = [5 * sizes[0] ** 2 - 4 * sizes[0]] + [(3 * q - 2) ** 2 for q in sizes[1:]]
+        x = np.arange(1, 128) * (Lx / 128.0)
+        y = np.arange(1, 128) / 128.0
+        X, Y = np.meshgrid(x, y)
+        ue = (np.sin(3 * np.pi * X / Lx) * np.sin(4 * np.pi * Y)).ravel() + \
+            np.random.default_rng(0).uniform(-1, 1, 127 * 127)
+        b = torch.zeros(127 * 127, dtype=torch.float64, device="cuda")
+        cm.chebmg_apply_A(s.ctx, 0, cm.CHEBMG_F64, torch.tensor(ue, device="cuda"), b)
+        u = torch.zeros_like(b)
+
+        def solve():
+            code, it, rel, _ = cm.chebmg_gmres_solve(s.ctx, b, u, 1e-6, 20, 500)
+            assert code == cm.CHEBMG_OK
+            return it
+        solve()
+        t, it = timed(solve, reps)
+        row.update({"levels": sizes, "grid_complexity": sum(nnz) / nnz[0], "iterations": it,
+                    "matvecs": it * (m + nn + 1), "time_to_1e6_ms": t * 1e3})
+        s.close()
+        out.append(row)
+    return out
+
+
 DIFF_NRHS, DIFF_ADAM_STEPS = 16, 200
 
 
@@ -313,6 +362,8 @@ def main():
                     help="set up the 64-RHS E=8^3 batch, warm up, run one batched solve (kernels launched "
                          "one by one) inside the NVTX range 'bsolve' and exit")
     ap.add_argument("--no-diff", action="store_true", help="skip the gradient / weight-tuning measurements")
+    ap.add_argument("--no-table1", action="store_true", help="skip the FD study of Table 1")
+    ap.add_argument("--table1-only", action="store_true", help="only the FD study of Table 1")
     ap.add_argument("--diff-only", action="store_true",
                     help="only the gradient / weight-tuning measurements (printed as one JSON object)")
     ap.add_argument("--batched-only", action="store_true",
@@ -454,6 +505,12 @@ def main():
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps), out
 
+    if args.table1_only:
+        s32.close()
+        s64.close()
+        print(json.dumps({"fd_table1": bench_fd_table1(cm, torch, timed, max(1, args.steps))}))
+        return 0
+
     if args.diff_only:
         s32.close()
         s64.close()
@@ -543,6 +600,10 @@ def main():
         s32.close()
         s64.close()
         line["batched"] = bench_batched(cm, W, torch, timed, max(1, min(args.steps, 3)))
+    if not args.no_table1:
+        s32.close()
+        s64.close()
+        line["fd_table1"] = bench_fd_table1(cm, torch, timed, max(1, min(args.steps, 3)))
     if not args.no_diff:
         s32.close()
         s64.close()
