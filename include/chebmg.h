@@ -66,7 +66,8 @@ typedef struct {
   int order;             /* k >= 1: (k,k) symmetric or (2k,0) one-sided */
   int sided;             /* CHEBMG_SYMMETRIC | CHEBMG_ONE_SIDED */
   int prec;              /* CHEBMG_FP64 | CHEBMG_FP32_SMOOTHER */
-  double lmin_ratio;     /* 1st kind: lambda_min / lambda_max (0.1) */
+  double lmin_ratio;     /* 1st kind: lambda_min / lambda_max (0.1); <= 0: for each smoothing
+                            order the ratio that maximises gamma^{-1} (Eq. 2.14; Eq. 2.24 fits it) */
   double lmax_scale;     /* multiplies the Lanczos estimate (1.0) */
   int lanczos_steps;     /* Lanczos steps per level (30) */
   const double* lmax_override; /* host, one per smoothed level, or NULL */
@@ -235,6 +236,11 @@ int chebmg_group_create(chebmg_ctx* const* ctxs, int nctx, chebmg_group** group)
 int chebmg_group_pcg_solve(chebmg_group* group, const double* const* B, double* const* U,
                            double rtol, int maxit, int flags, int* iters, double* relres);
 void chebmg_group_destroy(chebmg_group* group);
+
+/* lambda_min / lambda_max that the 1st-kind smoother (Algorithm 1) of the given order uses in
+ * this context: the fixed lmin_ratio, or the gamma^{-1}-optimal ratio (Sec. 2.4, Eq. 2.24)
+ * when lmin_ratio <= 0 (computed on the host on first use, then cached). */
+int chebmg_lambda_min_ratio(chebmg_ctx* ctx, int order, double* ratio);
 
 /* ---- smoother weights and their gradient ----------------------------------------- */
 

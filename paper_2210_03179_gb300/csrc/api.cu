@@ -155,6 +155,7 @@ struct chebmg_ctx {
   int gexec_nb = 0;
   int64_t glaunches[2] = {0, 0};   // kernels per replay of each graph
   // ---- smoother parameter overrides (weight tuning) ----
+  std::vector<double> lmin_opt;  // optimal lambda_min / lambda_max per smoothing order (1st kind)
   std::vector<double> beta_ovr;  // weights of Algorithm 2 for smoothing order beta_ovr.size()
   double lscale = 1.0;           // every level smooths with lscale * lambda_max
   // ---- adjoint workspace ----
@@ -267,6 +268,15 @@ void zero(chebmg_ctx* c, T* p, int64_t n) {
   CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, c->s));
 }
 
+// lambda_min / lambda_max of the 1st-kind smoother of the given order: the option's fixed ratio,
+// or (option <= 0) the ratio that maximises gamma^{-1} for that order (computed once).
+double lmin_ratio_for(chebmg_ctx* c, int order) {
+  if (c->o.lmin_ratio > 0.0) return c->o.lmin_ratio;
+  if ((int)c->lmin_opt.size() <= order) c->lmin_opt.resize(order + 1, 0.0);
+  if (c->lmin_opt[order] == 0.0) c->lmin_opt[order] = cheb1_optimal_lmin_ratio(order);
+  return c->lmin_opt[order];
+}
+
 // One smoother application (Algorithm 1 or 2) of the given order on level j.
 template <typename T>
 void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
@@ -282,7 +292,7 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
   zero<T>(c, y, span(c, L));
   if (!x_zero) apply_into<T>(c, j, x, y);
   if (c->o.kind == CHEBMG_CHEB_1ST) {
-    const double lmin = c->o.lmin_ratio * lmax;
+    const double lmin = lmin_ratio_for(c, order) * lmax;
     const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
     const double sigma = theta / delta;
     double rho = 1.0 / sigma;
@@ -754,6 +764,10 @@ void finish_setup(chebmg_ctx* c) {
   }
   c->pre = c->o.sided == CHEBMG_ONE_SIDED ? 2 * c->o.order : c->o.order;
   c->post = c->o.sided == CHEBMG_ONE_SIDED ? 0 : c->o.order;
+  if (c->o.kind == CHEBMG_CHEB_1ST) {
+    lmin_ratio_for(c, c->pre);
+    if (c->post > 0) lmin_ratio_for(c, c->post);
+  }
   for (int j = 0; j + 1 < nl; ++j) {
     double lm;
     if (c->o.lmax_override) lm = c->o.lmax_override[j];
@@ -779,8 +793,8 @@ void validate_opts(const chebmg_opts* o) {
     throw Error(CHEBMG_EINVAL, "optimized 4th-kind coefficients are tabulated up to order 16");
   if (o->sided != CHEBMG_SYMMETRIC && o->sided != CHEBMG_ONE_SIDED) throw Error(CHEBMG_EINVAL, "bad sided");
   if (o->prec != CHEBMG_FP64 && o->prec != CHEBMG_FP32_SMOOTHER) throw Error(CHEBMG_EINVAL, "bad prec");
-  if (o->kind == CHEBMG_CHEB_1ST && !(o->lmin_ratio > 0.0 && o->lmin_ratio < 1.0))
-    throw Error(CHEBMG_EINVAL, "lmin_ratio must be in (0, 1)");
+  if (o->kind == CHEBMG_CHEB_1ST && !(o->lmin_ratio < 1.0) )
+    throw Error(CHEBMG_EINVAL, "lmin_ratio must be below 1 (<= 0: optimal per order)");
   if (!(o->lmax_scale > 0.0)) throw Error(CHEBMG_EINVAL, "lmax_scale must be > 0");
   if (o->lanczos_steps < 1 && !o->lmax_override) throw Error(CHEBMG_EINVAL, "lanczos_steps must be >= 1");
   if (!(o->coarse_rtol > 0.0) || o->coarse_maxit < 1) throw Error(CHEBMG_EINVAL, "bad coarse tolerance");
@@ -1905,6 +1919,14 @@ int chebmg_coarse_info(const chebmg_ctx* c, int* degree, double* lmax) {
   *degree = (c->coop_ok && c->L.back().type == TYPE_SEM) ? c->coarse_degree : 1;
   *lmax = c->coarse_lmax;
   return CHEBMG_OK;
+}
+
+int chebmg_lambda_min_ratio(chebmg_ctx* c, int order, double* ratio) {
+  return guard([&]() -> int {
+    if (!c || !ratio || order < 1 || order > 256) throw Error(CHEBMG_EINVAL, "bad arguments");
+    *ratio = lmin_ratio_for(c, order);
+    return CHEBMG_OK;
+  });
 }
 
 int chebmg_set_coarse_degree(chebmg_ctx* c, int degree) {

@@ -369,3 +369,91 @@ bool fd_dense_inverse(const double st[9], int mx, int my, std::vector<double>& i
 }
 
 }  // namespace chebmg
+
+namespace chebmg {
+
+// gamma(lambda_min) = sup_{0 < lambda <= 1} lambda p^2 / (1 - p^2) (Eq. 2.14) of the 1st-kind
+// polynomial p(lambda) = T_k((theta - lambda) / delta) / T_k(theta / delta), theta = (1 + lmin) / 2,
+// delta = (1 - lmin) / 2 (lambda_max = 1): dense Chebyshev-spaced sampling, then a golden-section
+// refinement around the largest sample.
+static double cheb1_gamma(int k, double lmin) {
+  const double theta = 0.5 * (1.0 + lmin), delta = 0.5 * (1.0 - lmin);
+  auto Tk = [k](double x) {
+    if (std::fabs(x) <= 1.0) return std::cos(k * std::acos(x));
+    const double s = x > 0 ? 1.0 : ((k & 1) ? -1.0 : 1.0);
+    return s * std::cosh(k * std::acosh(std::fabs(x)));
+  };
+  const double den = Tk(theta / delta);
+  auto f = [&](double lam) {
+    const double p = Tk((theta - lam) / delta) / den;
+    const double q = 1.0 - p * p;
+    return q > 0.0 ? lam * p * p / q : 1e300;
+  };
+  const int npts = 20000;
+  double best = -1.0, bl = 0.0;
+  for (int i = 1; i <= npts; ++i) {
+    const double lam = 0.5 * (1.0 - std::cos(M_PI * i / npts));
+    const double v = f(lam);
+    if (v > best) {
+      best = v;
+      bl = lam;
+    }
+  }
+  double a = std::max(1e-12, bl - 4e-4), b = std::min(1.0, bl + 4e-4);
+  const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+  double x1 = b - gr * (b - a), x2 = a + gr * (b - a), f1 = f(x1), f2 = f(x2);
+  for (int it = 0; it < 100; ++it) {
+    if (f1 > f2) {
+      b = x2;
+      x2 = x1;
+      f2 = f1;
+      x1 = b - gr * (b - a);
+      f1 = f(x1);
+    } else {
+      a = x1;
+      x1 = x2;
+      f1 = f2;
+      x2 = a + gr * (b - a);
+      f2 = f(x2);
+    }
+  }
+  return std::max(best, std::max(f1, f2));
+}
+
+double cheb1_optimal_lmin_ratio(int k) {
+  // maximise gamma^{-1} over lambda_min / lambda_max: log-spaced scan, then golden section
+  double bestl = 0.1, bestg = 1e300;
+  const int nscan = 240;
+  const double lo = 1e-4, hi = 0.9;
+  for (int i = 0; i <= nscan; ++i) {
+    const double l = lo * std::pow(hi / lo, (double)i / nscan);
+    const double g = cheb1_gamma(k, l);
+    if (g < bestg) {
+      bestg = g;
+      bestl = l;
+    }
+  }
+  const double step = std::pow(hi / lo, 1.0 / nscan);
+  double a = std::log(bestl / step), b = std::log(bestl * step);
+  const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+  double x1 = b - gr * (b - a), x2 = a + gr * (b - a);
+  double g1 = cheb1_gamma(k, std::exp(x1)), g2 = cheb1_gamma(k, std::exp(x2));
+  for (int it = 0; it < 60; ++it) {
+    if (g1 < g2) {
+      b = x2;
+      x2 = x1;
+      g2 = g1;
+      x1 = b - gr * (b - a);
+      g1 = cheb1_gamma(k, std::exp(x1));
+    } else {
+      a = x1;
+      x1 = x2;
+      g1 = g2;
+      x2 = a + gr * (b - a);
+      g2 = cheb1_gamma(k, std::exp(x2));
+    }
+  }
+  return std::exp(0.5 * (a + b));
+}
+
+}  // namespace chebmg

@@ -51,4 +51,8 @@ void fd_galerkin_stencil(const double fine[9], int c, double coarse[9]);
 // Dense inverse of the stencil operator on an m x m grid via Cholesky (host).
 bool fd_dense_inverse(const double st[9], int mx, int my, std::vector<double>& inv);
 
+// lambda_min / lambda_max that maximises gamma^{-1} (Eq. 2.14) of the order-k 1st-kind
+// smoother (Algorithm 1): the "optimal lambda_min" of Sec. 2.4 (Eq. 2.24 fits it).
+double cheb1_optimal_lmin_ratio(int k);
+
 }  // namespace chebmg
