@@ -303,6 +303,32 @@ def bench_fd_table1(cm, torch, timed, reps):
     return out
 
 
+def bench_schedules(cm, W, torch, timed, reps, verts, b):
+    """Solves at the benchmark size (E = 32^3, N = 7, mixed form, FCG to 1e-8) with the p-MG
+    schedule 7 -> 5 -> 3 -> 1 beside 7 -> 3 -> 1, and with the 1st-kind smoother at
+    lambda_min = 0.1 lambda_max beside the gamma^{-1}-optimal lambda_min (one-sided (4,0))."""
+    u = torch.zeros_like(b)
+    out = {}
+    for name, kw in [("opt4th (7,3,1)", dict(orders=(7, 3, 1), kind="opt4th")),
+                     ("opt4th (7,5,3,1)", dict(orders=(7, 5, 3, 1), kind="opt4th")),
+                     ("1st kind lmin=0.1 (7,3,1)", dict(orders=(7, 3, 1), kind="1st", lmin_ratio=0.1)),
+                     ("1st kind lmin optimal (7,3,1)", dict(orders=(7, 3, 1), kind="1st", lmin_ratio=0.0))]:
+        s = cm.Solver("sem", verts=verts, order=K_ORDER, sided=SIDED, prec="mixed", **kw)
+
+        def solve():
+            code, it, rel, _ = cm.chebmg_pcg_solve(s.ctx, b, u, RTOL, 500)
+            assert code == cm.CHEBMG_OK and rel <= RTOL
+            return it
+        solve()
+        t, it = timed(solve, reps)
+        rec = {"time_to_1e8_s": t, "iterations": it}
+        if kw["kind"] == "1st":
+            rec["lmin_ratio"] = cm.chebmg_lambda_min_ratio(s.ctx, 2 * K_ORDER)
+        out[name] = rec
+        s.close()
+    return out
+
+
 DIFF_NRHS, DIFF_ADAM_STEPS = 16, 200
 
 
@@ -363,6 +389,10 @@ def main():
                          "one by one) inside the NVTX range 'bsolve' and exit")
     ap.add_argument("--no-diff", action="store_true", help="skip the gradient / weight-tuning measurements")
     ap.add_argument("--no-table1", action="store_true", help="skip the FD study of Table 1")
+    ap.add_argument("--no-schedules", action="store_true",
+                    help="skip the 7-5-3-1 schedule and optimal-lambda_min solves at E=32^3")
+    ap.add_argument("--schedules-only", action="store_true",
+                    help="only the 7-5-3-1 schedule and optimal-lambda_min solves at E=32^3")
     ap.add_argument("--table1-only", action="store_true", help="only the FD study of Table 1")
     ap.add_argument("--diff-only", action="store_true",
                     help="only the gradient / weight-tuning measurements (printed as one JSON object)")
@@ -505,6 +535,12 @@ def main():
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps), out
 
+    if args.schedules_only:
+        s32.close()
+        s64.close()
+        print(json.dumps({"schedules": bench_schedules(cm, W, torch, timed, max(1, args.steps), verts, b)}))
+        return 0
+
     if args.table1_only:
         s32.close()
         s64.close()
@@ -600,6 +636,10 @@ def main():
         s32.close()
         s64.close()
         line["batched"] = bench_batched(cm, W, torch, timed, max(1, min(args.steps, 3)))
+    if not args.no_schedules:
+        s32.close()
+        s64.close()
+        line["schedules"] = bench_schedules(cm, W, torch, timed, max(1, min(args.steps, 3)), verts, b)
     if not args.no_table1:
         s32.close()
         s64.close()
