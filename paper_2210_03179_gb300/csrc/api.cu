@@ -127,7 +127,7 @@ struct chebmg_ctx {
   bool coop_ok = false;
   unsigned* cctl = nullptr;     // [5] control words of the persistent kernel
   unsigned* hcctl = nullptr;    // pinned host copy
-  double* cpart = nullptr;      // [3 * coarse_grid + 3]
+  double* cpart = nullptr;      // [2][3 * coarse_grid] block partials, by generation parity
   double* cxbuf[2] = {nullptr, nullptr};   // exchange buffers of the persistent coarse CG
   unsigned* cflag = nullptr;    // [coarse_grid] exchange flags
   int coarse_rows_per_block = 0;
@@ -375,7 +375,6 @@ CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
   a.rows_per_block = c->coarse_rows_per_block;
   a.halo = c->coarse_halo;
   a.part = c->cpart;
-  a.tot = c->cpart + 3 * std::max(1, c->coarse_grid);
   a.ctl = c->cctl;
   a.rtol = c->o.coarse_rtol;
   a.maxit = c->o.coarse_maxit;
@@ -662,7 +661,7 @@ void common_alloc(chebmg_ctx* c) {
     CK(cudaMallocHost(&h, sizeof(unsigned) * 5));
     c->hcctl = static_cast<unsigned*>(h);
     std::memset(c->hcctl, 0, sizeof(unsigned) * 5);
-    c->cpart = dalloc<double>(c, 3 * std::max(1, grid) + 3);
+    c->cpart = dalloc<double>(c, 6 * std::max(1, grid));   // two generations of 3 partials per block
     c->cxbuf[0] = dalloc<double>(c, nc);
     c->cxbuf[1] = dalloc<double>(c, nc);
     c->cflag = dalloc<unsigned>(c, std::max(1, grid));

@@ -141,8 +141,9 @@ void cg_update(int64_t n, double* x, double* r, double* z, const double* p, cons
                const double* invD, double* partial, double* scal, cudaStream_t s);
 
 // ---- persistent coarse solve (one cooperative launch per solve) ----
-// Control words: ctl[0] barrier arrivals, ctl[1] barrier generation, ctl[2] status of the
-// last solve, ctl[3] its iterations, ctl[4] sticky worst error since the caller reset it.
+// Control words: ctl[0] reduction arrivals (monotonic within a launch), ctl[1] unused, ctl[2]
+// status of the last solve, ctl[3] its iterations, ctl[4] sticky worst error since the caller
+// reset it.
 enum CoarseStatus { CS_NONE = 0, CS_OK = 1, CS_NOTCONV = 2, CS_BREAKDOWN = 3, CS_TIMEOUT = 4 };
 struct CoarseCG {
   int64_t n;
@@ -156,9 +157,8 @@ struct CoarseCG {
   unsigned* flag;        // [gridDim] last generation each block has published
   int rows_per_block;    // block q owns rows [q * rows_per_block, (q + 1) * rows_per_block)
   int halo;              // block q reads rows owned by blocks q - halo .. q + halo (symmetric)
-  double* part;          // [3 * gridDim] block partials
-  double* tot;           // [3] their totals, published by the last block to reach the barrier
-  unsigned* ctl;         // [5], ctl[0..1] zero at launch
+  double* part;          // [2][3 * gridDim] block partials, double-buffered by reduction parity
+  unsigned* ctl;         // [5], ctl[0] (monotonic arrival counter) zero at launch
   double rtol;
   int maxit;
   int degree;            // degree of the 4th-kind Chebyshev preconditioner (1 = Jacobi)

@@ -727,7 +727,6 @@ void cg_update(int64_t n, double* x, double* r, double* z, const double* p, cons
 // (bounded) wait, so the kernel always finishes.
 // ===========================================================================
 constexpr int kCoarseThreads = 256;
-constexpr unsigned kSpinLimit = 1u << 24;   // x ~64 ns sleep: about a second
 
 __device__ __forceinline__ void block_allsum2(double& a, double& b) {
   __shared__ double sa[kCoarseThreads / 32], sb[kCoarseThreads / 32];
@@ -748,37 +747,6 @@ __device__ __forceinline__ void block_allsum2(double& a, double& b) {
   }
   a = ta;
   b = tb;
-}
-
-__device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned& gen, unsigned expected) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned target = gen + 1;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&ctl[0], 1u);
-    if (arrived == expected - 1) {
-      atomicExch(&ctl[0], 0u);
-      __threadfence();
-      atomicExch(&ctl[1], target);
-    } else {
-      unsigned spins = 0;
-      while (*(volatile unsigned*)&ctl[1] != target) {
-        if (++spins > kSpinLimit) {
-          atomicMax((int*)&ctl[4], (int)CS_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  gen += 1;
-  return s_ok != 0;
 }
 
 // Block sum of three values: one warp adds the per-thread values through shared memory
@@ -815,63 +783,70 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
   c = res[2];
 }
 
-// Grid barrier that also reduces: the last block to arrive sums the 3 * gridDim partials in a
-// fixed order, publishes the totals and releases the others, who then read three numbers.
-// Waits are bounded as in grid_barrier.
-__device__ __forceinline__ bool barrier_reduce3(unsigned* ctl, unsigned& gen, unsigned expected,
-                                                const double* part, double* tot, double& A, double& B,
-                                                double& C) {
-  __shared__ int s_last, s_ok;
-  __syncthreads();
-  const unsigned target = gen + 1;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(&ctl[0], 1u) == expected - 1;
-    s_ok = 1;
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t kWaitNs = 1000000000ull;   // every wait gives up after about a second
+
+// Spins until *p >= target (acquire); false after kWaitNs, with the timeout recorded.
+__device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target, unsigned* ctl) {
+  if (ld_acquire(p) >= target) return true;
+  const uint64_t t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    __nanosleep(20);                     // back off: polling competes with the producers' stores
+    if (ld_acquire(p) >= target) return true;
+    if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) {
+      atomicMax((int*)&ctl[4], (int)CS_TIMEOUT);
+      return false;
+    }
   }
-  __syncthreads();
-  if (s_last) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
-      a += ((volatile const double*)part)[3 * q];
-      b += ((volatile const double*)part)[3 * q + 1];
-      c += ((volatile const double*)part)[3 * q + 2];
-    }
-    block_sum3(a, b, c);
-    if (threadIdx.x == 0) {
-      tot[0] = a;
-      tot[1] = b;
-      tot[2] = c;
-      __threadfence();
-      atomicExch(&ctl[0], 0u);
-      __threadfence();
-      atomicExch(&ctl[1], target);
-    }
-  } else if (threadIdx.x == 0) {
-    unsigned spins = 0;
-    while (*(volatile unsigned*)&ctl[1] != target) {
-      if (++spins > kSpinLimit) {
-        atomicMax((int*)&ctl[4], (int)CS_TIMEOUT);
-        s_ok = 0;
-        break;
-      }
-      __nanosleep(32);
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  gen += 1;
-  A = ((volatile const double*)tot)[0];
-  B = ((volatile const double*)tot)[1];
-  C = ((volatile const double*)tot)[2];
-  return s_ok != 0;
 }
 
-// Exchange of one vector with the neighbouring blocks (the rows a product reads): each block
-// writes its rows into the buffer of the new generation's parity, fences, raises its flag,
-// and waits -- bounded -- until every block within `halo` has raised the same generation.
-// Because the neighbourhood is symmetric, a block can only reuse a buffer parity after all
-// its readers have published the next generation, i.e. finished reading the old one.
+// Grid-wide sum of three values (a, b, c: this block's totals, the same in every thread),
+// replaced by the grid totals.  Each block posts its partials into the buffer of this
+// generation's parity and arrives at a monotonic counter (release); once all `expected`
+// blocks have arrived (acquire), every block sums all partials in the same fixed order, so
+// the totals are bitwise identical everywhere.  Two buffers suffice: a block can only write a
+// buffer again two reductions later, after every block has passed the reduction in between,
+// i.e. after every block has finished reading it.
+__device__ __forceinline__ bool allreduce3(unsigned* ctl, unsigned& gen, unsigned expected, double* part,
+                                           double& a, double& b, double& c) {
+  __shared__ int s_ok;
+  const unsigned g1 = gen + 1;
+  double* p = part + (size_t)(g1 & 1u) * 3 * gridDim.x;
+  if (threadIdx.x == 0) {
+    p[3 * blockIdx.x] = a;
+    p[3 * blockIdx.x + 1] = b;
+    p[3 * blockIdx.x + 2] = c;
+    red_release_add(&ctl[0], 1u);
+    s_ok = wait_at_least(&ctl[0], g1 * expected, ctl) ? 1 : 0;
+  }
+  __syncthreads();
+  double A = 0.0, B = 0.0, C = 0.0;
+  if (s_ok)
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+      A += __ldcg(&p[3 * q]);
+      B += __ldcg(&p[3 * q + 1]);
+      C += __ldcg(&p[3 * q + 2]);
+    }
+  const bool ok = s_ok != 0;
+  block_sum3(A, B, C);
+  gen = g1;
+  a = A;
+  b = B;
+  c = C;
+  return ok;
+}
 __device__ __forceinline__ void publish_rows(const CoarseCG& a, unsigned gen, const double* v, int rpt,
                                              int64_t base) {
   double* buf = a.xbuf[gen & 1u];
@@ -885,28 +860,27 @@ __device__ __forceinline__ void publish_rows(const CoarseCG& a, unsigned gen, co
     atomicExch(&a.flag[blockIdx.x], gen);
   }
 }
-
 __device__ __forceinline__ bool wait_neighbours(const CoarseCG& a, unsigned gen) {
   const int lo = max(0, (int)blockIdx.x - a.halo);
   const int hi = min((int)gridDim.x - 1, (int)blockIdx.x + a.halo);
   int ok = 1;
   if ((int)threadIdx.x <= hi - lo) {
     const unsigned* f = &a.flag[lo + threadIdx.x];
-    unsigned spins = 0;
-    while (*(volatile const unsigned*)f < gen) {
-      if (++spins > kSpinLimit) {
-        atomicMax((int*)&a.ctl[4], (int)CS_TIMEOUT);
-        ok = 0;
-        break;
+    if (*(volatile const unsigned*)f < gen) {
+      const uint64_t t0 = global_ns();
+      for (unsigned it = 1; *(volatile const unsigned*)f < gen; ++it) {
+        __nanosleep(20);
+        if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) {
+          atomicMax((int*)&a.ctl[4], (int)CS_TIMEOUT);
+          ok = 0;
+          break;
+        }
       }
-      __nanosleep(20);
     }
     __threadfence();
   }
   return __syncthreads_and(ok) != 0;
 }
-
-// y = A v for the owned rows, v read from the exchange buffer of generation gen.
 template <int NS, int RPT>
 __device__ __forceinline__ void coarse_spmv(const CoarseCG& a, unsigned gen, int64_t base, double (&y)[RPT]) {
   const double* v = a.xbuf[gen & 1u];
@@ -998,13 +972,8 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     rr += r[q] * r[q];
   }
   block_sum3(rz, rr, zero);
-  if (threadIdx.x == 0) {
-    a.part[3 * blockIdx.x] = rz;
-    a.part[3 * blockIdx.x + 1] = rr;
-    a.part[3 * blockIdx.x + 2] = 0.0;
-  }
-  double gam, bb, unused;
-  if (!barrier_reduce3(a.ctl, gb, expected, a.part, a.tot, gam, bb, unused)) return;
+  if (!allreduce3(a.ctl, gb, expected, a.part, rz, rr, zero)) return;
+  double gam = rz, bb = rr;
   if (!(bb > 0.0) || !(gam >= 0.0)) {
     finish(bb == 0.0 ? CS_OK : CS_BREAKDOWN, 0);
     return;
@@ -1018,13 +987,8 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
 #pragma unroll
     for (int q = 0; q < RPT; ++q) pq += p[q] * y[q];
     block_sum3(pq, z1, z2);
-    if (threadIdx.x == 0) {
-      a.part[3 * blockIdx.x] = pq;
-      a.part[3 * blockIdx.x + 1] = 0.0;
-      a.part[3 * blockIdx.x + 2] = 0.0;
-    }
-    double pq_tot;
-    if (!barrier_reduce3(a.ctl, gb, expected, a.part, a.tot, pq_tot, z1, z2)) return;
+    if (!allreduce3(a.ctl, gb, expected, a.part, pq, z1, z2)) return;
+    const double pq_tot = pq;
     if (!(pq_tot > 0.0)) {
       finish(CS_BREAKDOWN, it);
       return;
@@ -1044,13 +1008,8 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
       rr2 += r[q] * r[q];
     }
     block_sum3(rz2, rr2, z1);
-    if (threadIdx.x == 0) {
-      a.part[3 * blockIdx.x] = rz2;
-      a.part[3 * blockIdx.x + 1] = rr2;
-      a.part[3 * blockIdx.x + 2] = 0.0;
-    }
-    double gam_new, rr_tot;
-    if (!barrier_reduce3(a.ctl, gb, expected, a.part, a.tot, gam_new, rr_tot, z1)) return;
+    if (!allreduce3(a.ctl, gb, expected, a.part, rz2, rr2, z1)) return;
+    const double gam_new = rz2, rr_tot = rr2;
     if (!(rr_tot == rr_tot)) {
       finish(CS_BREAKDOWN, it);
       return;
