@@ -6,7 +6,7 @@
 // (Sec. 4.1) apply J x J x J per element.  FD (Sec. 3): a constant 3x3
 // stencil per level (five-point on the finest, Galerkin nine-point below).
 // Chebyshev recurrences: Algorithms 1 and 2 split into an operator pass and
-// an elementwise pass.
+// an elementwise pass (the elementwise kernels are in chebyshev.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +28,8 @@ inline unsigned grid_for(int64_t n, int bs) {
 }
 
 inline void count() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+constexpr int kVecThreads = 256;
 
 }  // namespace
 
@@ -362,206 +364,6 @@ __global__ void k_dense_matvec(int n, const double* __restrict__ M, const double
 
 void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s, int nb, int64_t ld) {
   k_dense_matvec<<<dim3((n + 127) / 128, nb), 128, 0, s>>>(n, M, x, y, ld);
-  count();
-}
-
-// ===========================================================================
-// Chebyshev recurrences and vector updates
-// ===========================================================================
-template <typename T>
-__global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                             T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD, T c0,
-                             int x_is_zero, int64_t ld) {
-  { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    T rv;
-    if (x_is_zero) {
-      rv = b[g];
-      x[g] = T(0);
-    } else {
-      rv = b[g] - y[g];
-      y[g] = T(0);
-    }
-    r[g] = rv;
-    d[g] = c0 * invD[g] * rv;
-  }
-}
-
-// Vector type of 16 bytes for T (float4 / double2) and its lane count.
-template <typename T>
-struct V16;
-template <>
-struct V16<float> {
-  using type = float4;
-  static constexpr int L = 4;
-};
-template <>
-struct V16<double> {
-  using type = double2;
-  static constexpr int L = 2;
-};
-
-template <typename T>
-__device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T c1, T c2) {
-  const T dv = d;
-  const T rv = r - y;
-  x += beta * dv;
-  r = rv;
-  d = c1 * dv + c2 * s * rv;
-  y = T(0);
-}
-
-// x += beta d; r -= y; d = c1 d + c2 S r; y = 0 -- 16-byte vector accesses over the aligned
-// body (every pointer comes from a 256-byte aligned allocation), scalar tail.
-template <typename T, bool VEC>
-__global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
-                             T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, int64_t ld) {
-  { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
-  using VT = typename V16<T>::type;
-  constexpr int L = V16<T>::L;
-  const int64_t nv = VEC ? n / L : 0;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = tid; q < nv; q += stride) {
-    VT xv = reinterpret_cast<VT*>(x)[q], rv = reinterpret_cast<VT*>(r)[q], dv = reinterpret_cast<VT*>(d)[q];
-    VT yv = reinterpret_cast<VT*>(y)[q];
-    const VT sv = reinterpret_cast<const VT*>(invD)[q];
-    T* xs = reinterpret_cast<T*>(&xv);
-    T* rs = reinterpret_cast<T*>(&rv);
-    T* ds = reinterpret_cast<T*>(&dv);
-    T* ys = reinterpret_cast<T*>(&yv);
-    const T* ss = reinterpret_cast<const T*>(&sv);
-#pragma unroll
-    for (int l = 0; l < L; ++l) cheb4_one(xs[l], rs[l], ds[l], ys[l], ss[l], beta, c1, c2);
-    reinterpret_cast<VT*>(x)[q] = xv;
-    reinterpret_cast<VT*>(r)[q] = rv;
-    reinterpret_cast<VT*>(d)[q] = dv;
-    reinterpret_cast<VT*>(y)[q] = yv;
-  }
-  for (int64_t g = nv * L + tid; g < n; g += stride) cheb4_one(x[g], r[g], d[g], y[g], invD[g], beta, c1, c2);
-}
-
-template <typename T>
-__global__ void k_cheb1_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                             T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD,
-                             T inv_theta, int x_is_zero, int64_t ld) {
-  { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    T rv;
-    if (x_is_zero) {
-      rv = invD[g] * b[g];
-      x[g] = T(0);
-    } else {
-      rv = invD[g] * (b[g] - y[g]);
-      y[g] = T(0);
-    }
-    r[g] = rv;
-    d[g] = rv * inv_theta;
-  }
-}
-
-template <typename T>
-__global__ void k_cheb1_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
-                             T* __restrict__ y, const T* __restrict__ invD, T c1, T c2, int64_t ld) {
-  { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const T dv = d[g];
-    const T rv = r[g] - invD[g] * y[g];
-    x[g] += dv;
-    r[g] = rv;
-    d[g] = c1 * dv + c2 * rv;
-    y[g] = T(0);
-  }
-}
-
-template <typename T>
-__global__ void k_axpy(int64_t n, T a, const T* __restrict__ d, T* __restrict__ x, int64_t ld) {
-  { const int64_t off_ = (int64_t)blockIdx.y * ld; d += off_; x += off_; }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    x[g] += a * d[g];
-}
-
-template <typename T>
-__global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y, T* __restrict__ r, int64_t ld) {
-  { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; y += off_; r += off_; }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    r[g] = b[g] - y[g];
-    y[g] = T(0);
-  }
-}
-
-template <typename Tin, typename Tout>
-__global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out, int64_t ldi, int64_t ldo) {
-  in += (int64_t)blockIdx.y * ldi;
-  out += (int64_t)blockIdx.y * ldo;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    out[g] = (Tout)in[g];
-}
-
-__global__ void k_masked_copy(int64_t n, const double* __restrict__ in, const double* __restrict__ invD,
-                              double* __restrict__ out, int64_t ldi, int64_t ldo) {
-  in += (int64_t)blockIdx.y * ldi;
-  out += (int64_t)blockIdx.y * ldo;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    out[g] = invD[g] != 0.0 ? in[g] : 0.0;
-}
-
-constexpr int kVecThreads = 256;
-
-template <typename T>
-void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0, int x_is_zero,
-                cudaStream_t s, int nb, int64_t ld) {
-  k_cheb4_init<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)c0,
-                                                                             x_is_zero, ld ? ld : n);
-  count();
-}
-template <typename T>
-void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
-                cudaStream_t s, int nb, int64_t ld) {
-  if (!ld) ld = n;
-  const uintptr_t align = (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
-  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
-    k_cheb4_step<T, true><<<dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), kVecThreads, 0, s>>>(
-        n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, ld);
-  else
-    k_cheb4_step<T, false><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)beta,
-                                                                                     (T)c1, (T)c2, ld);
-  count();
-}
-template <typename T>
-void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
-                int x_is_zero, cudaStream_t s, int nb, int64_t ld) {
-  k_cheb1_init<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)inv_theta,
-                                                                             x_is_zero, ld ? ld : n);
-  count();
-}
-template <typename T>
-void cheb1_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double c1, double c2, cudaStream_t s, int nb,
-                int64_t ld) {
-  k_cheb1_step<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)c1, (T)c2,
-                                                                             ld ? ld : n);
-  count();
-}
-template <typename T>
-void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s, int nb, int64_t ld) {
-  k_axpy<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, (T)a, d, x, ld ? ld : n);
-  count();
-}
-template <typename T>
-void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s, int nb, int64_t ld) {
-  k_residual<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, y, r, ld ? ld : n);
-  count();
-}
-template <typename Tin, typename Tout>
-void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s, int nb, int64_t ldi, int64_t ldo) {
-  k_cast<Tin, Tout><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, in, out, ldi ? ldi : n,
-                                                                               ldo ? ldo : n);
-  count();
-}
-void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s, int nb, int64_t ldi,
-                 int64_t ldo) {
-  k_masked_copy<<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, in, invD, out, ldi ? ldi : n,
-                                                                           ldo ? ldo : n);
   count();
 }
 
@@ -1140,21 +942,9 @@ void scale(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
   template void fd_apply<T>(int, int, const Stencil9<T>&, const T*, T*, cudaStream_t, int, int64_t);    \
   template void fd_restrict<T>(int, int, int, int, int, const T*, T*, cudaStream_t, int, int64_t, int64_t); \
   template void fd_prolong<T>(int, int, int, int, int, const T*, T*, int, cudaStream_t, int, int64_t,     \
-                              int64_t);                                                               \
-  template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
-                              int64_t);                                                                 \
-  template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t, int,   \
-                              int64_t);                                                                 \
-  template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
-                              int64_t);                                                                 \
-  template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t, int, int64_t); \
-  template void axpy<T>(int64_t, double, const T*, T*, cudaStream_t, int, int64_t);                     \
-  template void residual<T>(int64_t, const T*, T*, T*, cudaStream_t, int, int64_t);
+                              int64_t);
 
 CHEBMG_INST(float)
 CHEBMG_INST(double)
-template void cast<double, float>(int64_t, const double*, float*, cudaStream_t, int, int64_t, int64_t);
-template void cast<float, double>(int64_t, const float*, double*, cudaStream_t, int, int64_t, int64_t);
-template void cast<double, double>(int64_t, const double*, double*, cudaStream_t, int, int64_t, int64_t);
 
 }  // namespace chebmg
