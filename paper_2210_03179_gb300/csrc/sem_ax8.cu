@@ -108,6 +108,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 constexpr uint32_t kWaitLimit = 1u << 22;
 
+// L2 policy for the geometric factors: each byte is read once per operator application, so the
+// copies are marked evict-first and leave the L2 to the vectors that the update kernel reads
+// next (the gathered d and the accumulated y).
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// One bulk copy global -> shared, completion counted on `bar`, with the evict-first L2 hint.
+__device__ __forceinline__ void bulk_copy_g(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(evict_first_policy())
+      : "memory");
+}
+
 // Global ids (with the Dirichlet flag) of the column (i = a, j = b, k = 0..7) of element e:
 // read from the element-to-global map, or (IMPLICIT) computed from the box lattice, which the
 // library's meshes always have -- connectivity of a box, arbitrary vertex positions.  32-bit
@@ -172,11 +190,7 @@ k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __r
     const uint32_t bytes = (uint32_t)(nvalid * C::GELEM * sizeof(T));
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)), "r"(bytes)
                  : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(sG)),
-        "l"(G + e0 * C::GELEM), "r"(bytes), "r"(smem_addr(&bar))
-        : "memory");
+    bulk_copy_g(sG, G + e0 * C::GELEM, bytes, &bar);
   }
 
   T* su = sU + le * C::STAGE;
@@ -298,11 +312,7 @@ k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
     const uint32_t bytes = (uint32_t)(nv * C::GELEM * sizeof(T));
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[buf])), "r"(bytes)
                  : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(sG + buf * EB * C::GELEM)),
-        "l"(G + e0 * C::GELEM), "r"(bytes), "r"(smem_addr(&bar[buf]))
-        : "memory");
+    bulk_copy_g(sG + buf * EB * C::GELEM, G + e0 * C::GELEM, bytes, &bar[buf]);
   };
   auto gather = [&](int64_t bt, uint32_t (&g)[8], T (&v)[8]) {
     const int64_t e = bt * EB + le;
@@ -440,11 +450,7 @@ k_sem_ax8b(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
     const uint32_t bytes = (uint32_t)(nvalid * C::GELEM * sizeof(T));
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)), "r"(bytes)
                  : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(sG)),
-        "l"(G + e0 * C::GELEM), "r"(bytes), "r"(smem_addr(&bar))
-        : "memory");
+    bulk_copy_g(sG, G + e0 * C::GELEM, bytes, &bar);
   }
   T* su = sU + le * C::STAGE;
   T* sr = sR + le * C::STAGE;
