@@ -73,7 +73,8 @@ void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T
 template <typename T>
 bool sem_ax8_variant_fits(int eb);
 
-// p-multigrid transfers on the box lattice for the order pairs (7,3) and (3,1) (Q 8->4, 4->2).
+// p-multigrid transfers on the box lattice for the order pairs (7,3), (3,1), (7,5), (5,3)
+// (Q 8->4, 4->2, 8->6, 6->4).
 cudaError_t transfer_box_set_J(int Qf, int Qc, const double* J);
 bool transfer_box_supported(int Qf, int Qc);
 template <typename T>

@@ -1,5 +1,5 @@
-// p-multigrid interpolation and restriction (Sec. 4.1) for fixed order pairs, on the box
-// lattice of the library's meshes.
+// p-multigrid interpolation and restriction (Sec. 4.1) for fixed order pairs (7->3, 3->1 and
+// the 7->5->3 steps of the 7-5-3-1 schedule), on the box lattice of the library's meshes.
 //
 // P z_c = W Q_f^T (J x J x J) Q_c z_c and P^T r_f = Q_c^T (J^T x J^T x J^T) O^T r_f, where
 // O^T keeps each fine node only in its owner element (equal to Q_f W on the continuous range
@@ -19,6 +19,10 @@ __constant__ double c_J84_d[8 * 4];
 __constant__ float c_J84_f[8 * 4];
 __constant__ double c_J42_d[4 * 2];
 __constant__ float c_J42_f[4 * 2];
+__constant__ double c_J86_d[8 * 6];
+__constant__ float c_J86_f[8 * 6];
+__constant__ double c_J64_d[6 * 4];
+__constant__ float c_J64_f[6 * 4];
 
 template <typename T, int QF, int QC>
 __device__ __forceinline__ T Jv(int f, int c);
@@ -30,6 +34,14 @@ template <>
 __device__ __forceinline__ double Jv<double, 4, 2>(int f, int c) { return c_J42_d[f * 2 + c]; }
 template <>
 __device__ __forceinline__ float Jv<float, 4, 2>(int f, int c) { return c_J42_f[f * 2 + c]; }
+template <>
+__device__ __forceinline__ double Jv<double, 8, 6>(int f, int c) { return c_J86_d[f * 6 + c]; }
+template <>
+__device__ __forceinline__ float Jv<float, 8, 6>(int f, int c) { return c_J86_f[f * 6 + c]; }
+template <>
+__device__ __forceinline__ double Jv<double, 6, 4>(int f, int c) { return c_J64_d[f * 4 + c]; }
+template <>
+__device__ __forceinline__ float Jv<float, 6, 4>(int f, int c) { return c_J64_f[f * 4 + c]; }
 
 constexpr int kEB = 4;   // elements per block
 
@@ -206,29 +218,33 @@ k_prolong_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ zc, T* __
 
 }  // namespace
 
+template <int QF, int QC>
+static cudaError_t set_J(const double* J, const void* sym_d, const void* sym_f) {
+  float f[QF * QC];
+  for (int q = 0; q < QF * QC; ++q) f[q] = (float)J[q];
+  cudaError_t e = cudaMemcpyToSymbol(sym_d, J, sizeof(double) * QF * QC);
+  return e != cudaSuccess ? e : cudaMemcpyToSymbol(sym_f, f, sizeof(f));
+}
+
 cudaError_t transfer_box_set_J(int Qf, int Qc, const double* J) {
-  if (Qf == 8 && Qc == 4) {
-    float f[32];
-    for (int q = 0; q < 32; ++q) f[q] = (float)J[q];
-    cudaError_t e = cudaMemcpyToSymbol(c_J84_d, J, sizeof(double) * 32);
-    return e != cudaSuccess ? e : cudaMemcpyToSymbol(c_J84_f, f, sizeof(f));
-  }
-  if (Qf == 4 && Qc == 2) {
-    float f[8];
-    for (int q = 0; q < 8; ++q) f[q] = (float)J[q];
-    cudaError_t e = cudaMemcpyToSymbol(c_J42_d, J, sizeof(double) * 8);
-    return e != cudaSuccess ? e : cudaMemcpyToSymbol(c_J42_f, f, sizeof(f));
-  }
+  if (Qf == 8 && Qc == 4) return set_J<8, 4>(J, c_J84_d, c_J84_f);
+  if (Qf == 4 && Qc == 2) return set_J<4, 2>(J, c_J42_d, c_J42_f);
+  if (Qf == 8 && Qc == 6) return set_J<8, 6>(J, c_J86_d, c_J86_f);
+  if (Qf == 6 && Qc == 4) return set_J<6, 4>(J, c_J64_d, c_J64_f);
   return cudaErrorInvalidValue;
 }
 
-bool transfer_box_supported(int Qf, int Qc) { return (Qf == 8 && Qc == 4) || (Qf == 4 && Qc == 2); }
+bool transfer_box_supported(int Qf, int Qc) {
+  return (Qf == 8 && Qc == 4) || (Qf == 4 && Qc == 2) || (Qf == 8 && Qc == 6) || (Qf == 6 && Qc == 4);
+}
 
 template <typename T>
 void restrict_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* rf, T* rc,
                   cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
   const dim3 blocks((unsigned)((E + kEB - 1) / kEB), nb);
-  if (Qf == 8) k_restrict_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
+  if (Qf == 8 && Qc == 4) k_restrict_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
+  else if (Qf == 8 && Qc == 6) k_restrict_box<T, 8, 6><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
+  else if (Qf == 6 && Qc == 4) k_restrict_box<T, 6, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
   else k_restrict_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
@@ -237,8 +253,14 @@ template <typename T>
 void prolong_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* zc, T* zf,
                  int accumulate, cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
   const dim3 blocks((unsigned)((E + kEB - 1) / kEB), nb);
-  if (Qf == 8) k_prolong_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
-  else k_prolong_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+  if (Qf == 8 && Qc == 4)
+    k_prolong_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+  else if (Qf == 8 && Qc == 6)
+    k_prolong_box<T, 8, 6><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+  else if (Qf == 6 && Qc == 4)
+    k_prolong_box<T, 6, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+  else
+    k_prolong_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 

@@ -35,7 +35,7 @@ def solver(v, orders, kind="opt4th", k=2, sided="one-sided", prec="fp64", lmax=N
     return cm.Solver("sem", verts=v, orders=orders, kind=kind, order=k, sided=sided, prec=prec, lmax=lmax, **kw)
 
 
-@pytest.mark.parametrize("orders", [(7, 3, 1), (9, 5, 2), (8, 4), (6, 1), (2, 1), (4, 3, 2, 1)])
+@pytest.mark.parametrize("orders", [(7, 3, 1), (7, 5, 3, 1), (9, 5, 2), (8, 4), (6, 1), (2, 1), (4, 3, 2, 1)])
 def test_operator_diagonal_and_transfers(verts, orders):
     levels = [SemLevel(verts, Nn) for Nn in orders]
     s = solver(verts, orders, lmax=[1.0] * (len(orders) - 1))
