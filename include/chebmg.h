@@ -242,6 +242,14 @@ void chebmg_group_destroy(chebmg_group* group);
  * when lmin_ratio <= 0 (computed on the host on first use, then cached). */
 int chebmg_lambda_min_ratio(chebmg_ctx* ctx, int order, double* ratio);
 
+/* Precision of the SEM coarse CG's polynomial preconditioner: CHEBMG_F64 (the default of an
+ * FP64 context) or CHEBMG_F32 (the default of a CHEBMG_FP32_SMOOTHER context).  The CG itself -- iterate, residual, the products A p, the dot products and the
+ * 1e-10 stopping test -- stays FP64 either way; with FP32 the preconditioner's products,
+ * recurrence and neighbour exchanges use FP32 copies and the CG takes the flexible
+ * (Polak-Ribiere) beta.  retune != 0 re-times the preconditioner degree for the new
+ * precision.  EINVAL for contexts without an SEM coarse CG. */
+int chebmg_set_coarse_precond_dtype(chebmg_ctx* ctx, int dtype, int retune);
+
 /* ---- smoother weights and their gradient ----------------------------------------- */
 
 /* Error reduction of `steps` V-cycles (Sec. 3, Eq. 3.1: observed convergence) and its

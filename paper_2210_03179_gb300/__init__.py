@@ -80,6 +80,7 @@ _SIGNATURES = {
     "chebmg_launch_count": (c_int, [c_void_p, POINTER(c_int64)]),
     "chebmg_tile_choice": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
     "chebmg_set_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "chebmg_set_coarse_precond_dtype": (c_int, [c_void_p, c_int, c_int]),
     "chebmg_lambda_min_ratio": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "chebmg_coarse_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
     "chebmg_set_coarse_degree": (c_int, [c_void_p, c_int]),
@@ -229,6 +230,11 @@ def chebmg_tile_choice(ctx, level, dtype) -> int:
     v = c_int()
     _check(lib().chebmg_tile_choice(ctx, int(level), int(dtype), byref(v)), "chebmg_tile_choice")
     return v.value
+
+
+def chebmg_set_coarse_precond_dtype(ctx, dtype, retune=True):
+    _check(lib().chebmg_set_coarse_precond_dtype(ctx, int(dtype), 1 if retune else 0),
+           "chebmg_set_coarse_precond_dtype")
 
 
 def chebmg_lambda_min_ratio(ctx, order) -> float:

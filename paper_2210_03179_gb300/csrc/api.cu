@@ -129,6 +129,10 @@ struct chebmg_ctx {
   unsigned* hcctl = nullptr;    // pinned host copy
   double* cpart = nullptr;      // [2][3 * coarse_grid] block partials, by generation parity
   double* cxbuf[2] = {nullptr, nullptr};   // exchange buffers of the persistent coarse CG
+  float* cxbufF[2] = {nullptr, nullptr};   // FP32 exchange buffers (FP32 preconditioner)
+  float* ell_valf = nullptr;    // FP32 copies for the FP32 preconditioner
+  float* coarse_invDf = nullptr;
+  bool coarse_pf32 = false;     // coarse CG preconditioner in FP32
   unsigned* cflag = nullptr;    // [coarse_grid] exchange flags
   int coarse_rows_per_block = 0;
   int coarse_halo = 0;
@@ -381,6 +385,11 @@ CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
   a.degree = c->coarse_degree;
   a.lmax = c->coarse_lmax > 0.0 ? c->coarse_lmax : 1.0;
   a.phantom_blocks = 0;
+  a.pf32 = c->coarse_pf32 ? 1 : 0;
+  a.valf = c->ell_valf;
+  a.invDf = c->coarse_invDf;
+  a.xbufF[0] = c->cxbufF[0];
+  a.xbufF[1] = c->cxbufF[1];
   return a;
 }
 
@@ -664,6 +673,8 @@ void common_alloc(chebmg_ctx* c) {
     c->cpart = dalloc<double>(c, 6 * std::max(1, grid));   // two generations of 3 partials per block
     c->cxbuf[0] = dalloc<double>(c, nc);
     c->cxbuf[1] = dalloc<double>(c, nc);
+    c->cxbufF[0] = dalloc<float>(c, nc);
+    c->cxbufF[1] = dalloc<float>(c, nc);
     c->cflag = dalloc<unsigned>(c, std::max(1, grid));
   }
 }
@@ -775,8 +786,11 @@ void finish_setup(chebmg_ctx* c) {
     c->L[j].lmax = lm;
   }
   if (c->ell_col) {
-    // lambda_max of S A on the coarse level (same Lanczos), then the preconditioner degree
+    // lambda_max of S A on the coarse level (same Lanczos), then the preconditioner degree.
+    // The mixed form evaluates the coarse CG's preconditioner in FP32 as well (the CG stays
+    // FP64); the FP64 form keeps it in FP64.
     c->coarse_lmax = lanczos(c, nl - 1, c->o.lanczos_steps >= 1 ? c->o.lanczos_steps : 30);
+    c->coarse_pf32 = c->fp32;
     if (c->coop_ok) autotune_coarse_degree(c);
   }
   CK(cudaStreamSynchronize(c->s));
@@ -1869,6 +1883,8 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
           c->ell_col = dalloc<int>(c, (int64_t)col.size());
           CK(cudaMemcpy(c->ell_col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
           c->ell_val = upload<double>(c, val);
+          c->ell_valf = upload<float>(c, val);
+          c->coarse_invDf = upload<float>(c, invd);
         }
         c->L.push_back(L);
         alloc_vectors(c, c->L.back(), c->fp32);
@@ -1924,6 +1940,19 @@ int chebmg_lambda_min_ratio(chebmg_ctx* c, int order, double* ratio) {
   return guard([&]() -> int {
     if (!c || !ratio || order < 1 || order > 256) throw Error(CHEBMG_EINVAL, "bad arguments");
     *ratio = lmin_ratio_for(c, order);
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_set_coarse_precond_dtype(chebmg_ctx* c, int dtype, int retune) {
+  return guard([&]() -> int {
+    enter(c);
+    if (dtype != CHEBMG_F64 && dtype != CHEBMG_F32) throw Error(CHEBMG_EINVAL, "bad dtype");
+    if (!c->ell_col) throw Error(CHEBMG_EINVAL, "no SEM coarse CG in this context");
+    c->coarse_pf32 = dtype == CHEBMG_F32;
+    if (retune && c->coop_ok) autotune_coarse_degree(c);
+    drop_graphs(c);
+    CK(cudaStreamSynchronize(c->s));
     return CHEBMG_OK;
   });
 }

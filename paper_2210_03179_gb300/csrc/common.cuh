@@ -165,6 +165,14 @@ struct CoarseCG {
   int degree;            // degree of the 4th-kind Chebyshev preconditioner (1 = Jacobi)
   double lmax;           // lambda_max of S A on the coarse level
   unsigned phantom_blocks;   // self-test only: barrier also waits for this many blocks that never come
+  // preconditioner in FP32 (pf32 != 0): the polynomial's products, recurrence and exchanges
+  // run on FP32 copies; the CG itself (iterate, residual, products A p, dots) stays FP64 and
+  // takes the flexible (Polak-Ribiere) beta, since rounded FP32 arithmetic makes the
+  // preconditioner slightly non-symmetric.
+  int pf32;
+  const float* valf;     // ELL values, FP32
+  const float* invDf;    // Jacobi diagonal, FP32
+  float* xbufF[2];       // FP32 exchange buffers
 };
 // Rows per thread the persistent coarse kernel can keep in registers.
 constexpr int kCoarseMaxRowsPerThread = 8;

@@ -662,6 +662,19 @@ __device__ __forceinline__ void publish_rows(const CoarseCG& a, unsigned gen, co
     atomicExch(&a.flag[blockIdx.x], gen);
   }
 }
+__device__ __forceinline__ void publish_rows_f(const CoarseCG& a, unsigned gen, const float* v, int rpt,
+                                               int64_t base) {
+  float* buf = a.xbufF[gen & 1u];
+  for (int q = 0; q < rpt; ++q) {
+    const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
+    if (g < a.n && g < base + a.rows_per_block) buf[g] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(&a.flag[blockIdx.x], gen);
+  }
+}
 __device__ __forceinline__ bool wait_neighbours(const CoarseCG& a, unsigned gen) {
   const int lo = max(0, (int)blockIdx.x - a.halo);
   const int hi = min((int)gridDim.x - 1, (int)blockIdx.x + a.halo);
@@ -705,19 +718,41 @@ __device__ __forceinline__ void coarse_spmv(const CoarseCG& a, unsigned gen, int
   }
 }
 
+template <int NS, int RPT>
+__device__ __forceinline__ void coarse_spmv_f(const CoarseCG& a, unsigned gen, int64_t base, float (&y)[RPT]) {
+  const float* v = a.xbufF[gen & 1u];
+  const int64_t n = a.n;
+  const int ns = NS > 0 ? NS : a.nslot;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
+    float acc = 0.f;
+    if (g < n && g < base + a.rows_per_block) {
+      if (NS > 0) {
+#pragma unroll
+        for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
+          acc = fmaf(__ldg(&a.valf[k * n + g]), __ldcg(&v[__ldg(&a.col[k * n + g])]), acc);
+      } else {
+        for (int k = 0; k < ns; ++k) acc = fmaf(__ldg(&a.valf[k * n + g]), __ldcg(&v[__ldg(&a.col[k * n + g])]), acc);
+      }
+    }
+    y[q] = acc;
+  }
+}
+
 // Persistent preconditioned CG on the assembled coarse operator.  The preconditioner is one
 // application of Algorithm 2 (4th kind, beta = 1) of degree m from a zero guess, Jacobi-
 // scaled -- SPD for every m, and for m = 1 simply Jacobi.  Per CG iteration: m products,
 // each needing only the neighbouring blocks' rows (flag exchange), and two grid-wide
 // reductions (reduce-then-release barrier).  Owned rows live in registers.
-template <int NS, int RPT>
+template <int NS, int RPT, bool PF32>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
   const int64_t n = a.n;
   const int64_t base = (int64_t)blockIdx.x * a.rows_per_block;
   const unsigned expected = gridDim.x + a.phantom_blocks;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   unsigned gb = 0, gx = 0;   // generations: grid barrier, neighbour exchange
-  double x[RPT], r[RPT], p[RPT], z[RPT], S[RPT], d[RPT], rp[RPT], y[RPT];
+  double x[RPT], r[RPT], p[RPT], z[RPT], S[RPT], d[RPT], rp[RPT], y[RPT], ro[RPT];
   bool live[RPT];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
@@ -728,8 +763,39 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     x[q] = p[q] = 0.0;
   }
   const double c0 = 4.0 / (3.0 * a.lmax);
+  // z = M r in FP32 (same recurrence on FP32 copies)
+  auto precond_f = [&]() -> bool {
+    float df[RPT], rf[RPT], zf[RPT], yf[RPT], sf[RPT];
+    const float c0f = (float)c0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
+      sf[q] = live[q] ? __ldg(&a.invDf[g]) : 0.f;
+      rf[q] = (float)r[q];
+      df[q] = c0f * sf[q] * rf[q];
+      zf[q] = 0.f;
+    }
+    for (int i = 1; i < a.degree; ++i) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) zf[q] += df[q];
+      publish_rows_f(a, ++gx, df, RPT, base);
+      if (!wait_neighbours(a, gx)) return false;
+      coarse_spmv_f<NS, RPT>(a, gx, base, yf);
+      const float c1 = (float)((2.0 * i - 1.0) / (2.0 * i + 3.0));
+      const float c2 = (float)((8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax));
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        rf[q] -= yf[q];
+        df[q] = c1 * df[q] + c2 * sf[q] * rf[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) z[q] = (double)(zf[q] + df[q]);
+    return true;
+  };
   // z = M r: Algorithm 2 from a zero guess; returns false on a failed exchange
   auto precond = [&]() -> bool {
+    if (PF32) return precond_f();
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       rp[q] = r[q];
@@ -798,6 +864,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     const double alpha = gam / pq_tot;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
+      ro[q] = r[q];
       x[q] = fma(alpha, p[q], x[q]);
       r[q] = fma(-alpha, y[q], r[q]);
     }
@@ -808,6 +875,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     for (int q = 0; q < RPT; ++q) {
       rz2 += r[q] * z[q];
       rr2 += r[q] * r[q];
+      if (PF32) z1 += ro[q] * z[q];
     }
     block_sum3(rz2, rr2, z1);
     if (!allreduce3(a.ctl, gb, expected, a.part, rz2, rr2, z1)) return;
@@ -820,7 +888,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
       finish(CS_OK, it);
       return;
     }
-    const double beta = gam_new / gam;
+    // Fletcher-Reeves for the exact (symmetric) FP64 preconditioner; Polak-Ribiere
+    // (z_new, r_new - r_old) / (z_old, r_old) for the FP32 one
+    const double beta = PF32 ? (gam_new - z1) / gam : gam_new / gam;
     gam = gam_new;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) p[q] = fma(beta, p[q], z[q]);
@@ -829,13 +899,13 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
   finish(CS_NOTCONV, a.maxit);
 }
 
-template <int NS>
+template <int NS, bool PF32>
 static const void* coarse_kernel(int rpt) {
   switch (rpt) {
-    case 1: return (const void*)k_coarse_pcg<NS, 1>;
-    case 2: return (const void*)k_coarse_pcg<NS, 2>;
-    case 4: return (const void*)k_coarse_pcg<NS, 4>;
-    default: return (const void*)k_coarse_pcg<NS, 8>;
+    case 1: return (const void*)k_coarse_pcg<NS, 1, PF32>;
+    case 2: return (const void*)k_coarse_pcg<NS, 2, PF32>;
+    case 4: return (const void*)k_coarse_pcg<NS, 4, PF32>;
+    default: return (const void*)k_coarse_pcg<NS, 8, PF32>;
   }
 }
 
@@ -868,7 +938,8 @@ bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t*
     if (err) *err = cudaErrorInvalidConfiguration;
     return false;
   }
-  const void* fn = a.nslot == 27 ? coarse_kernel<27>(rpt) : coarse_kernel<0>(rpt);
+  const void* fn = a.pf32 ? (a.nslot == 27 ? coarse_kernel<27, true>(rpt) : coarse_kernel<0, true>(rpt))
+                         : (a.nslot == 27 ? coarse_kernel<27, false>(rpt) : coarse_kernel<0, false>(rpt));
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoarseThreads), params, 0, s);
   count();
   if (err) *err = e;

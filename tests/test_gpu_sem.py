@@ -127,6 +127,18 @@ def test_coarse_cg_and_lanczos(verts):
         assert relerr(zz, x_ref) < 1e-8
         if deg == 1:
             assert abs(iters - K.pcg_jacobi(Lc.apply_A, Lc.invD, r, 1e-10)[1]) <= 1
+    # FP32 preconditioner (the mixed form's default): the FP64 CG still reaches 1e-10 and takes
+    # the FP64 preconditioner's iteration count within one
+    cm.chebmg_set_coarse_precond_dtype(s.ctx, F32, retune=False)
+    for deg in (1, 8):
+        cm.chebmg_set_coarse_degree(s.ctx, deg)
+        z = empty(Lc.n)
+        iters = cm.chebmg_coarse_solve(s.ctx, T(r), z)
+        zz = N(z)
+        assert np.linalg.norm(r - Lc.apply_A(zz)) <= 1.01e-10 * np.linalg.norm(r)
+        x_ref, it_ref = K.pcg_cheb4(Lc.apply_A, Lc.invD, r, lc, deg, 1e-10)
+        assert abs(iters - it_ref) <= 1, (deg, iters, it_ref)
+        assert relerr(zz, x_ref) < 1e-8
     s.close()
 
 
