@@ -483,6 +483,9 @@ int coarse_solve64_batched(chebmg_ctx* c, const double* b, double* x) {
     a.lmax = c->coarse_lmax > 0.0 ? c->coarse_lmax : 1.0;
     a.stat = c->bcstat;
     a.sticky = c->dstat + 1;
+    a.pf32 = c->coarse_pf32 ? 1 : 0;
+    a.valf = c->ell_valf;
+    a.invDf = c->coarse_invDf;
     if (!coarse_block_launch(a, c->nb, c->s)) throw Error(CHEBMG_ECUDA, "batched coarse launch failed");
     check_launch();
     return CHEBMG_OK;
@@ -1021,7 +1024,7 @@ void autotune_batch(chebmg_ctx* c, int nrhs) {
     std::vector<unsigned> st(2 * (size_t)nrhs);
     float best = 1e30f;
     int best_m = 1;
-    for (int m : {1, 2, 4, 8, 12, 16}) {
+    for (int m : {1, 2, 4, 8, 12, 16, 24}) {
       c->bcoarse_degree = m;
       const float t = time_it([&]() { coarse_solve64_batched(c, c->cb, c->cx); }, 2);
       CK(cudaMemcpy(st.data(), c->bcstat, sizeof(unsigned) * st.size(), cudaMemcpyDeviceToHost));

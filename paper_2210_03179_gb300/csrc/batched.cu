@@ -240,13 +240,33 @@ __device__ __forceinline__ void cb_spmv(const CoarseBlock& a, const double* sv, 
 }
 
 template <int NS, int RPT>
+__device__ __forceinline__ void cb_spmv_f(const CoarseBlock& a, const float* sv, float (&y)[RPT]) {
+  const int64_t n = a.n;
+  const int ns = NS > 0 ? NS : a.nslot;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t g = threadIdx.x + (int64_t)q * kCBThreads;
+    float acc = 0.f;
+    if (g < n) {
+      if (NS > 0) {
+#pragma unroll
+        for (int k = 0; k < (NS > 0 ? NS : 1); ++k) acc = fmaf(__ldg(&a.valf[k * n + g]), sv[__ldg(&a.col[k * n + g])], acc);
+      } else {
+        for (int k = 0; k < ns; ++k) acc = fmaf(__ldg(&a.valf[k * n + g]), sv[__ldg(&a.col[k * n + g])], acc);
+      }
+    }
+    y[q] = acc;
+  }
+}
+
+template <int NS, int RPT, bool PF32>
 __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
   extern __shared__ double sv[];   // [n]: the vector of the current product
   const int64_t n = a.n;
   const int64_t off = (int64_t)blockIdx.x * a.ld;
   const double* b = a.b + off;
   double* xo = a.x + off;
-  double x[RPT], r[RPT], p[RPT], z[RPT], d[RPT], rp[RPT], y[RPT];
+  double x[RPT], r[RPT], p[RPT], z[RPT], d[RPT], rp[RPT], y[RPT], ro[RPT];
   bool live[RPT];
   // S = invD is re-read (L1) where needed instead of taking RPT more registers
   auto Sv = [&](int q) { return live[q] ? __ldg(&a.invD[threadIdx.x + q * kCBThreads]) : 0.0; };
@@ -266,7 +286,43 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
     cb_spmv<NS, RPT>(a, sv, y);
   };
   const double c0 = 4.0 / (3.0 * a.lmax);
+  // the same polynomial on FP32 copies (the vector of each product in the same shared memory)
+  auto precond_f = [&]() {
+    float* svf = reinterpret_cast<float*>(sv);
+    float df[RPT], rf[RPT], zf[RPT], yf[RPT];
+    auto Sf = [&](int q) { return live[q] ? __ldg(&a.invDf[threadIdx.x + q * kCBThreads]) : 0.f; };
+    const float c0f = (float)c0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      rf[q] = (float)r[q];
+      df[q] = c0f * Sf(q) * rf[q];
+      zf[q] = 0.f;
+    }
+    for (int i = 1; i < a.degree; ++i) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) zf[q] += df[q];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+        if (live[q]) svf[threadIdx.x + q * kCBThreads] = df[q];
+      __syncthreads();
+      cb_spmv_f<NS, RPT>(a, svf, yf);
+      const float c1 = (float)((2.0 * i - 1.0) / (2.0 * i + 3.0));
+      const float c2 = (float)((8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax));
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        rf[q] -= yf[q];
+        df[q] = c1 * df[q] + c2 * Sf(q) * rf[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) z[q] = (double)(zf[q] + df[q]);
+  };
   auto precond = [&]() {
+    if (PF32) {
+      precond_f();
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       rp[q] = r[q];
@@ -324,6 +380,7 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
     const double alpha = gam / pq;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
+      ro[q] = r[q];
       x[q] = fma(alpha, p[q], x[q]);
       r[q] = fma(-alpha, y[q], r[q]);
     }
@@ -334,6 +391,7 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
     for (int q = 0; q < RPT; ++q) {
       gnew += r[q] * z[q];
       rr += r[q] * r[q];
+      if (PF32) u1 += ro[q] * z[q];
     }
     cb_sum3(gnew, rr, u1);
     if (!(rr == rr)) {
@@ -344,7 +402,7 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
       finish(CS_OK, it);
       return;
     }
-    const double beta = gnew / gam;
+    const double beta = PF32 ? (gnew - u1) / gam : gnew / gam;   // flexible beta for FP32
     gam = gnew;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) p[q] = fma(beta, p[q], z[q]);
@@ -352,14 +410,14 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
   finish(CS_NOTCONV, a.maxit);
 }
 
-template <int NS>
+template <int NS, bool PF32>
 const void* cb_kernel(int rpt) {
   switch (rpt) {
-    case 1: return (const void*)k_coarse_block<NS, 1>;
-    case 2: return (const void*)k_coarse_block<NS, 2>;
-    case 3: return (const void*)k_coarse_block<NS, 3>;
-    case 4: return (const void*)k_coarse_block<NS, 4>;
-    default: return (const void*)k_coarse_block<NS, 6>;
+    case 1: return (const void*)k_coarse_block<NS, 1, PF32>;
+    case 2: return (const void*)k_coarse_block<NS, 2, PF32>;
+    case 3: return (const void*)k_coarse_block<NS, 3, PF32>;
+    case 4: return (const void*)k_coarse_block<NS, 4, PF32>;
+    default: return (const void*)k_coarse_block<NS, 6, PF32>;
   }
 }
 
@@ -401,7 +459,8 @@ bool coarse_block_launch(const CoarseBlock& a, int nb, cudaStream_t s) {
   if (!coarse_block_supported(a.n) || nb < 1) return false;
   int rpt = (int)((a.n + kCBThreads - 1) / kCBThreads);
   if (rpt > 4) rpt = 6;
-  const void* fn = a.nslot == 27 ? cb_kernel<27>(rpt) : cb_kernel<0>(rpt);
+  const void* fn = a.pf32 ? (a.nslot == 27 ? cb_kernel<27, true>(rpt) : cb_kernel<0, true>(rpt))
+                         : (a.nslot == 27 ? cb_kernel<27, false>(rpt) : cb_kernel<0, false>(rpt));
   const size_t smem = sizeof(double) * (size_t)a.n;
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -220,6 +220,9 @@ struct CoarseBlock {
   double lmax;
   unsigned* stat;        // [nb][2]: status (CoarseStatus), iterations
   unsigned* sticky;      // worst error (atomicMax), reset by the caller
+  int pf32;              // preconditioner in FP32 (as CoarseCG::pf32)
+  const float* valf;
+  const float* invDf;
 };
 bool coarse_block_supported(int64_t n);
 bool coarse_block_launch(const CoarseBlock& a, int nb, cudaStream_t s);
