@@ -152,6 +152,24 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# Replicas (N > 1): every rank solves its own copy; the slowest rank sets the job time
+# ---------------------------------------------------------------------------
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of the ranks' values of x (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, dofs_per_rank, seconds):
+    """Whole-job GDOF/s: every rank solved dofs_per_rank unknowns; seconds is the max over ranks."""
+    return world * dofs_per_rank / seconds / 1e9
+
+
 BATCH_NE, BATCH_NRHS = 8, 64
 UNEVEN = [(ne, Nn) for ne in (4, 6, 8, 12) for Nn in (5, 7, 9)]
 
@@ -451,12 +469,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x):
+        return max_over_ranks(x, dist, "cuda")
 
     if args.profile_batched:
         v = W.sem_box_vertices(BATCH_NE, BATCH_NE, BATCH_NE)
@@ -533,7 +547,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps), out
+        return slowest(e0.elapsed_time(e1) / 1e3 / reps), out
 
     if args.schedules_only:
         s32.close()
@@ -616,7 +630,7 @@ def main():
                 "peak_source": "nominal FP64 rate of GB300", "step_us": step64 * 1e6}
 
     world_n = world
-    value = world_n * n / t32 / 1e9
+    value = job_throughput(world_n, n, t32)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t32 * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -627,7 +641,7 @@ def main():
             "iterations": {"mixed": it32, "fp64": it64},
             "speedup_mixed_vs_fp64": t64 / t32,
             "smoother_gdofs": {"fp32": n / step32 / 1e9, "fp64": n / step64 / 1e9},
-            "e2e": {"value": world_n * n / te2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+            "e2e": {"value": job_throughput(world_n, n, te2e), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "gpu_launches": int(launches),
             "roofline": roofline, "roofline_fp64": fp64_alu,
