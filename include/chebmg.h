@@ -99,6 +99,25 @@ int chebmg_setup_fd2d(int m, double Lx, double Ly, int coarsening, int coarsest,
 int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* orders,
                      int nlevels, const chebmg_opts* opts, chebmg_ctx** ctx);
 
+/* SEM on a general conforming hexahedral mesh (the problem statement's A u = b on any mesh,
+ * Sec. 1; the operator of Eq. 1.3 with isoparametric geometry).  Host arrays, copied:
+ *   coords:    E * (N+1)^3 * 3 doubles, the GLL point coordinates of each element at order N,
+ *              point (i, j, k) at index ((k (N+1) + j) (N+1) + i) * 3 (x, y, z); points shared
+ *              by several elements must have the same coordinates in each;
+ *   gid:       E * (N+1)^3 global ids in [0, n), every id used;
+ *   dirichlet: n bytes, nonzero = Dirichlet node (removed from the system);
+ *   orders:    decreasing, orders[0] = N (e.g. {7, 3, 1}).
+ * Each element must be positively oriented (its GLL Jacobian determinant > 0 everywhere; EMESH
+ * otherwise).  Coarser orders use the Lagrange interpolation of the coordinates and a numbering
+ * derived from the mesh topology (shared vertices, edges and faces found through the ids of
+ * their corner nodes); a coarse node is a Dirichlet node when every order-N node of its element
+ * vertex, edge or face is one.  Vectors of level j are in that level's numbering (level 0:
+ * the caller's gid).  Kernels that index through the box lattice are not used for such
+ * contexts. */
+int chebmg_setup_sem_mesh(int64_t E, int N, const double* coords, const int64_t* gid, int64_t n,
+                          const uint8_t* dirichlet, const int* orders, int nlevels,
+                          const chebmg_opts* opts, chebmg_ctx** ctx);
+
 void chebmg_destroy(chebmg_ctx* ctx);
 
 /* ---- queries ---------------------------------------------------------------- */

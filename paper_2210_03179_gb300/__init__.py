@@ -73,6 +73,9 @@ _SIGNATURES = {
                                   POINTER(c_void_p)]),
     "chebmg_setup_sem": (c_int, [c_int, c_int, c_int, POINTER(c_double), POINTER(c_int), c_int,
                                  POINTER(chebmg_opts), POINTER(c_void_p)]),
+    "chebmg_setup_sem_mesh": (c_int, [c_int64, c_int, POINTER(c_double), POINTER(c_int64), c_int64,
+                                      POINTER(ctypes.c_uint8), POINTER(c_int), c_int, POINTER(chebmg_opts),
+                                      POINTER(c_void_p)]),
     "chebmg_destroy": (None, [c_void_p]),
     "chebmg_num_levels": (c_int, [c_void_p, POINTER(c_int)]),
     "chebmg_level_size": (c_int, [c_void_p, c_int, POINTER(c_int64)]),
@@ -195,6 +198,24 @@ def chebmg_setup_sem(nex, ney, nez, verts, orders, opts) -> c_void_p:
     ctx = c_void_p()
     _check(lib().chebmg_setup_sem(int(nex), int(ney), int(nez), verts.ctypes.data_as(POINTER(c_double)), ords,
                                   len(orders), byref(opts), byref(ctx)), "chebmg_setup_sem")
+    return ctx
+
+
+def chebmg_setup_sem_mesh(coords, gid, n, dirichlet, orders, opts) -> c_void_p:
+    """coords: (E, (N+1)^3, 3) float64; gid: (E, (N+1)^3) int64 in [0, n); dirichlet: (n,) bool/uint8."""
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    gid = np.ascontiguousarray(gid, dtype=np.int64)
+    dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    E, NP = gid.shape
+    N = int(round(NP ** (1.0 / 3.0))) - 1
+    if (N + 1) ** 3 != NP or coords.shape != (E, NP, 3) or dirichlet.shape != (int(n),):
+        raise ValueError("coords (E, (N+1)^3, 3), gid (E, (N+1)^3), dirichlet (n,)")
+    ords = (c_int * len(orders))(*[int(o) for o in orders])
+    ctx = c_void_p()
+    _check(lib().chebmg_setup_sem_mesh(E, N, coords.ctypes.data_as(POINTER(c_double)),
+                                       gid.ctypes.data_as(POINTER(c_int64)), int(n),
+                                       dirichlet.ctypes.data_as(POINTER(ctypes.c_uint8)), ords, len(orders),
+                                       byref(opts), byref(ctx)), "chebmg_setup_sem_mesh")
     return ctx
 
 
@@ -471,7 +492,8 @@ class Solver:
 
     def __init__(self, problem: str, *, lmax=None, **kw):
         setup = {k: kw.pop(k) for k in list(kw) if k in ("m", "Lx", "Ly", "coarsening", "coarsest",
-                                                           "nex", "ney", "nez", "verts", "orders")}
+                                                           "nex", "ney", "nez", "verts", "orders",
+                                                           "coords", "gid", "n", "dirichlet")}
         self._lmax = None
         self.opts = chebmg_default_opts(**kw)
         if lmax is not None:
@@ -485,6 +507,9 @@ class Solver:
             v = setup["verts"]
             self.ctx = chebmg_setup_sem(v.shape[2] - 1, v.shape[1] - 1, v.shape[0] - 1, v,
                                         setup.get("orders", (7, 3, 1)), self.opts)
+        elif problem == "sem_mesh":
+            self.ctx = chebmg_setup_sem_mesh(setup["coords"], setup["gid"], setup["n"], setup["dirichlet"],
+                                             setup.get("orders", (7, 3, 1)), self.opts)
         else:
             raise ValueError(problem)
         self.mixed = self.opts.prec == CHEBMG_FP32_SMOOTHER

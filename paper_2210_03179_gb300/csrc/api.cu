@@ -94,6 +94,7 @@ struct Level {
   int eb[2] = {2, 2};   // variant of the order-7 operator, per dtype (autotuned)
   int beb[2] = {2002, 2002};   // variant of the batched order-7 operator (autotuned per batch size)
   Lattice lat = {0, 0, 0, 0, 0, 0};
+  bool boxed = true;    // SEM: the level carries the box lattice (lattice-indexed kernels usable)
   int64_t ld = 0;       // leading dimension of batched vectors: n rounded up to 64
 };
 
@@ -333,7 +334,7 @@ void restrict_to(chebmg_ctx* c, int j, const T* rf, T* rc) {
   const int64_t ldf = ldv(c, F), ldc = ldv(c, C);
   if (F.type == TYPE_SEM) {
     zero<T>(c, rc, span(c, C));
-    if (transfer_box_supported(F.Q, C.Q))
+    if (F.boxed && transfer_box_supported(F.Q, C.Q))
       restrict_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, rf, rc, c->s, nb, ldf, ldc);
     else
       sem_restrict<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), rf, rc, c->s, nb, ldf, ldc);
@@ -352,7 +353,7 @@ void prolong_to(chebmg_ctx* c, int j, const T* zc, T* zf, int accumulate) {
   const int nb = c->nb;
   const int64_t ldf = ldv(c, F), ldc = ldv(c, C);
   if (F.type == TYPE_SEM) {
-    if (transfer_box_supported(F.Q, C.Q))
+    if (F.boxed && transfer_box_supported(F.Q, C.Q))
       prolong_box<T>(F.Q, C.Q, F.E, F.lat, C.lat, zc, zf, accumulate, c->s, nb, ldf, ldc);
     else
       sem_prolong<T>(F.Q, C.Q, F.E, F.gid, C.gid, static_cast<const T*>(F.Jn[dt]), zc, zf, accumulate, c->s, nb,
@@ -707,6 +708,7 @@ void autotune_ax8(chebmg_ctx* c, int j) {
   int best_eb = 2;
   for (int eb : {1, 2, 4, 12, 14, 101, 102, 104, 112, 114}) {
     if (!sem_ax8_variant_fits<T>(eb)) continue;
+    if (eb >= 100 && !L.boxed) continue;   // lattice ids need the box lattice
     L.eb[dt] = eb;
     apply_into<T>(c, j, x, y);   // warm-up / first-launch configuration
     float t_min = 1e30f;
@@ -994,6 +996,7 @@ void autotune_batch(chebmg_ctx* c, int nrhs) {
         for (int rb : {1, 2, 4, 8, 16}) {
           if (rb > nrhs) break;
           for (int eb : {1, 2, 4, 101, 102, 104}) {
+            if (eb >= 100 && !L.boxed) continue;
             const int v = 1000 * rb + eb;
             if (dt == CHEBMG_F64 ? !sem_ax8_variant_fits<double>(eb % 100) : !sem_ax8_variant_fits<float>(eb % 100))
               continue;
@@ -1740,6 +1743,72 @@ int group_solve(chebmg_group* g, const double* const* B, double* const* U, doubl
   return finish();
 }
 
+// Uploads the host-built SEM levels (finest first) and assembles the coarsest level's ELL
+// form; boxed = the levels carry the box lattice (lattice kernels usable).
+void upload_sem_levels(chebmg_ctx* c, std::vector<SemHostLevel>& H, bool boxed) {
+  const int nlevels = (int)H.size();
+  for (int j = 0; j < nlevels; ++j) {
+    SemHostLevel& h = H[j];
+    Level L;
+    L.type = TYPE_SEM;
+    L.N = h.N;
+    L.Q = h.NQ;
+    L.boxed = boxed;
+    if (boxed)
+      L.lat = {h.nex, h.ney, h.nez, (int)(h.nex * h.N + 1), (int)(h.ney * h.N + 1), (int)(h.nez * h.N + 1)};
+    L.NP = h.NP;
+    L.E = h.E;
+    L.n = h.n;
+    L.ld = (L.n + 63) / 64 * 64;
+    L.gid = dalloc<uint32_t>(c, (int64_t)h.gid.size());
+    CK(cudaMemcpy(L.gid, h.gid.data(), sizeof(uint32_t) * h.gid.size(), cudaMemcpyHostToDevice));
+    std::vector<double> invd((size_t)h.n, 0.0);
+    for (int64_t g = 0; g < h.n; ++g)
+      if (!h.dirichlet[g]) invd[g] = 1.0 / h.diag[g];
+    const bool smoothed32 = c->fp32 && j + 1 < nlevels;
+    L.G[CHEBMG_F64] = upload<double>(c, h.G);
+    L.invD[CHEBMG_F64] = upload<double>(c, invd);
+    L.D[CHEBMG_F64] = upload<double>(c, h.Dm);
+    if (h.N == 7) CK(sem_ax8_set_D(h.Dm.data()));
+    if (smoothed32) {
+      L.G[CHEBMG_F32] = upload<float>(c, h.G);
+      L.invD[CHEBMG_F32] = upload<float>(c, invd);
+      L.D[CHEBMG_F32] = upload<float>(c, h.Dm);
+    }
+    if (j + 1 < nlevels) {
+      std::vector<double> J;
+      lagrange_interp(H[j + 1].x, h.x, J);
+      if (boxed && transfer_box_supported(h.NQ, H[j + 1].NQ))
+        CK(transfer_box_set_J(h.NQ, H[j + 1].NQ, J.data()));
+      L.Jn[CHEBMG_F64] = upload<double>(c, J);
+      if (c->fp32) L.Jn[CHEBMG_F32] = upload<float>(c, J);
+    }
+    if (j + 1 == nlevels) {
+      std::vector<int> col;
+      std::vector<double> val;
+      assemble_ell(h, c->nslot, col, val);
+      int grid = 0, rb = 0;
+      coarse_pcg_shape(h.n, &grid, &rb);
+      int halo = 0;
+      if (rb > 0)
+        for (int64_t g = 0; g < h.n; ++g)
+          for (int k = 0; k < c->nslot; ++k) {
+            const int64_t cc = col[(size_t)k * h.n + g];
+            halo = std::max<int>(halo, (int)std::llabs(cc / rb - g / rb));
+          }
+      c->coarse_halo = halo;
+      c->ell_col = dalloc<int>(c, (int64_t)col.size());
+      CK(cudaMemcpy(c->ell_col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
+      c->ell_val = upload<double>(c, val);
+      c->ell_valf = upload<float>(c, val);
+      c->coarse_invDf = upload<float>(c, invd);
+    }
+    c->L.push_back(L);
+    alloc_vectors(c, c->L.back(), c->fp32);
+    std::vector<double>().swap(h.G);
+  }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1836,63 +1905,52 @@ int chebmg_setup_sem(int nex, int ney, int nez, const double* verts, const int* 
         if (!build_sem_level(nex, ney, nez, verts, orders[j], H[j]))
           throw Error(CHEBMG_EMESH, "mesh has a non-positive Jacobian");
       }
+      upload_sem_levels(c, H, true);
+      common_alloc(c);
+      finish_setup(c);
+    } catch (...) {
+      destroy_ctx(c);
+      throw;
+    }
+    *out = c;
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_setup_sem_mesh(int64_t E, int N, const double* coords, const int64_t* gid, int64_t n,
+                          const uint8_t* dirichlet, const int* orders, int nlevels, const chebmg_opts* opts,
+                          chebmg_ctx** out) {
+  return guard([&]() -> int {
+    if (!out) throw Error(CHEBMG_EINVAL, "ctx output is NULL");
+    *out = nullptr;
+    if (E < 1 || N < 1 || N > 9 || !coords || !gid || n < 1 || !dirichlet || !orders || nlevels < 1)
+      throw Error(CHEBMG_EINVAL, "bad SEM mesh arguments");
+    if (orders[0] != N) throw Error(CHEBMG_EINVAL, "orders[0] must be the mesh order N");
+    for (int j = 0; j < nlevels; ++j) {
+      if (orders[j] < 1 || orders[j] > 9) throw Error(CHEBMG_EINVAL, "orders must be in 1..9");
+      if (j > 0 && orders[j] >= orders[j - 1]) throw Error(CHEBMG_EINVAL, "orders must decrease");
+    }
+    if (n >= (int64_t)kGidMask) throw Error(CHEBMG_EINVAL, "mesh too large for 30-bit global ids");
+    const int64_t NP = (int64_t)(N + 1) * (N + 1) * (N + 1);
+    for (int64_t q = 0; q < E * NP; ++q)
+      if (gid[q] < 0 || gid[q] >= n) throw Error(CHEBMG_EINVAL, "global id out of range");
+    SemMeshInput in;
+    in.E = E;
+    in.N = N;
+    in.coords = coords;
+    in.gid = gid;
+    in.n = n;
+    in.dirichlet = dirichlet;
+    chebmg_ctx* c = new_ctx(opts);
+    try {
+      c->type = TYPE_SEM;
+      std::vector<SemHostLevel> H(nlevels);
       for (int j = 0; j < nlevels; ++j) {
-        SemHostLevel& h = H[j];
-        Level L;
-        L.type = TYPE_SEM;
-        L.N = h.N;
-        L.Q = h.NQ;
-        L.lat = {nex, ney, nez, (int)(nex * h.N + 1), (int)(ney * h.N + 1), (int)(nez * h.N + 1)};
-        L.NP = h.NP;
-        L.E = h.E;
-        L.n = h.n;
-        L.ld = (L.n + 63) / 64 * 64;
-        L.gid = dalloc<uint32_t>(c, (int64_t)h.gid.size());
-        CK(cudaMemcpy(L.gid, h.gid.data(), sizeof(uint32_t) * h.gid.size(), cudaMemcpyHostToDevice));
-        std::vector<double> invd((size_t)h.n, 0.0);
-        for (int64_t g = 0; g < h.n; ++g)
-          if (!h.dirichlet[g]) invd[g] = 1.0 / h.diag[g];
-        const bool smoothed32 = c->fp32 && j + 1 < nlevels;
-        L.G[CHEBMG_F64] = upload<double>(c, h.G);
-        L.invD[CHEBMG_F64] = upload<double>(c, invd);
-        L.D[CHEBMG_F64] = upload<double>(c, h.Dm);
-        if (h.N == 7) CK(sem_ax8_set_D(h.Dm.data()));
-        if (smoothed32) {
-          L.G[CHEBMG_F32] = upload<float>(c, h.G);
-          L.invD[CHEBMG_F32] = upload<float>(c, invd);
-          L.D[CHEBMG_F32] = upload<float>(c, h.Dm);
-        }
-        if (j + 1 < nlevels) {
-          std::vector<double> J;
-          lagrange_interp(H[j + 1].x, h.x, J);
-          if (transfer_box_supported(h.NQ, H[j + 1].NQ)) CK(transfer_box_set_J(h.NQ, H[j + 1].NQ, J.data()));
-          L.Jn[CHEBMG_F64] = upload<double>(c, J);
-          if (c->fp32) L.Jn[CHEBMG_F32] = upload<float>(c, J);
-        }
-        if (j + 1 == nlevels) {
-          std::vector<int> col;
-          std::vector<double> val;
-          assemble_ell(h, c->nslot, col, val);
-          int grid = 0, rb = 0;
-          coarse_pcg_shape(h.n, &grid, &rb);
-          int halo = 0;
-          if (rb > 0)
-            for (int64_t g = 0; g < h.n; ++g)
-              for (int k = 0; k < c->nslot; ++k) {
-                const int64_t cc = col[(size_t)k * h.n + g];
-                halo = std::max<int>(halo, (int)std::llabs(cc / rb - g / rb));
-              }
-          c->coarse_halo = halo;
-          c->ell_col = dalloc<int>(c, (int64_t)col.size());
-          CK(cudaMemcpy(c->ell_col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
-          c->ell_val = upload<double>(c, val);
-          c->ell_valf = upload<float>(c, val);
-          c->coarse_invDf = upload<float>(c, invd);
-        }
-        c->L.push_back(L);
-        alloc_vectors(c, c->L.back(), c->fp32);
-        std::vector<double>().swap(h.G);
+        std::string err;
+        if (!build_sem_level_mesh(in, orders[j], H[j], err))
+          throw Error(err.find("Jacobian") != std::string::npos ? CHEBMG_EMESH : CHEBMG_EINVAL, err);
       }
+      upload_sem_levels(c, H, false);
       common_alloc(c);
       finish_setup(c);
     } catch (...) {
@@ -1977,7 +2035,7 @@ int chebmg_set_tile_choice(chebmg_ctx* c, int level, int dtype, int variant) {
       (base != 1 && base != 2 && base != 4 && base != 12 && base != 14))
     return CHEBMG_EINVAL;
   const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(variant) : sem_ax8_variant_fits<float>(variant);
-  if (!fits) return CHEBMG_EINVAL;
+  if (!fits || (variant >= 100 && !L.boxed)) return CHEBMG_EINVAL;
   L.eb[dtype] = variant;
   drop_graphs(c);
   return CHEBMG_OK;
@@ -2280,7 +2338,8 @@ int chebmg_set_batch_tile_choice(chebmg_ctx* c, int nrhs, int level, int dtype, 
     if (rb < 1 || rb > 64 || (rest != eb && rest != eb + 100) || (eb != 1 && eb != 2 && eb != 4))
       throw Error(CHEBMG_EINVAL, "bad batched variant");
     const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(eb) : sem_ax8_variant_fits<float>(eb);
-    if (!fits || (dtype == CHEBMG_F32 && !L.G[CHEBMG_F32])) throw Error(CHEBMG_EINVAL, "variant not available");
+    if (!fits || (dtype == CHEBMG_F32 && !L.G[CHEBMG_F32]) || (rest >= 100 && !L.boxed))
+      throw Error(CHEBMG_EINVAL, "variant not available");
     reserve_batch(c, nrhs);
     autotune_batch(c, nrhs);
     L.beb[dtype] = variant;

@@ -679,8 +679,8 @@ __device__ __forceinline__ bool wait_neighbours(const CoarseCG& a, unsigned gen)
   const int lo = max(0, (int)blockIdx.x - a.halo);
   const int hi = min((int)gridDim.x - 1, (int)blockIdx.x + a.halo);
   int ok = 1;
-  if ((int)threadIdx.x <= hi - lo) {
-    const unsigned* f = &a.flag[lo + threadIdx.x];
+  for (int t = threadIdx.x; t <= hi - lo && ok; t += blockDim.x) {   // halos wider than a block too
+    const unsigned* f = &a.flag[lo + t];
     if (*(volatile const unsigned*)f < gen) {
       const uint64_t t0 = global_ns();
       for (unsigned it = 1; *(volatile const unsigned*)f < gen; ++it) {
@@ -692,8 +692,8 @@ __device__ __forceinline__ bool wait_neighbours(const CoarseCG& a, unsigned gen)
         }
       }
     }
-    __threadfence();
   }
+  if ((int)threadIdx.x <= hi - lo) __threadfence();
   return __syncthreads_and(ok) != 0;
 }
 template <int NS, int RPT>

@@ -457,3 +457,276 @@ double cheb1_optimal_lmin_ratio(int k) {
 }
 
 }  // namespace chebmg
+
+// ---------------------------------------------------------------------------
+// General hexahedral meshes
+// ---------------------------------------------------------------------------
+#include <array>
+#include <unordered_map>
+
+namespace chebmg {
+
+namespace {
+
+// G (six entries) and det at one point from the Jacobian Jm[l][m] = d x_l / d r_m and the
+// quadrature weight w3 = w_i w_j w_k: G_mn = w3 / det (adj adj^T)_mn, adj = det J^{-1}.
+double point_factors(const double Jm[3][3], double w3, double* G, int64_t stride) {
+  double adj[3][3];
+  adj[0][0] = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+  adj[0][1] = Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2];
+  adj[0][2] = Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1];
+  adj[1][0] = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+  adj[1][1] = Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0];
+  adj[1][2] = Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2];
+  adj[2][0] = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+  adj[2][1] = Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1];
+  adj[2][2] = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+  const double det = Jm[0][0] * adj[0][0] + Jm[0][1] * adj[1][0] + Jm[0][2] * adj[2][0];
+  const double scale = w3 / det;
+  const int mm[6] = {0, 0, 0, 1, 1, 2}, nn[6] = {0, 1, 2, 1, 2, 2};
+  for (int q = 0; q < 6; ++q) {
+    double acc = 0.0;
+    for (int l = 0; l < 3; ++l) acc += adj[mm[q]][l] * adj[nn[q]][l];
+    G[q * stride] = scale * acc;
+  }
+  return det;
+}
+
+using Key = std::array<int64_t, 7>;
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+    for (int64_t v : k) {
+      uint64_t z = (uint64_t)v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      h ^= z ^ (z >> 31);
+    }
+    return (size_t)h;
+  }
+};
+
+}  // namespace
+
+bool build_sem_level_mesh(const SemMeshInput& in, int Nt, SemHostLevel& L, std::string& err) {
+  const int Nf = in.N, Qf = Nf + 1, NPf = Qf * Qf * Qf;
+  L.N = Nt;
+  L.NQ = Nt + 1;
+  L.NP = L.NQ * L.NQ * L.NQ;
+  L.nex = L.ney = L.nez = 0;
+  L.E = in.E;
+  const int Q = L.NQ, NP = L.NP;
+  gll_rule(Nt, L.x, L.w);
+  gll_derivative(Nt, L.x, L.Dm);
+  std::vector<double> xf, wf;
+  gll_rule(Nf, xf, wf);
+  // coordinates at this order: the caller's, or their Lagrange interpolation (isoparametric)
+  std::vector<double> X((size_t)in.E * NP * 3);
+  if (Nt == Nf) {
+    std::copy(in.coords, in.coords + X.size(), X.begin());
+  } else {
+    std::vector<double> J;
+    lagrange_interp(xf, L.x, J);   // J[a * Qf + b] = l^f_b(x^t_a)
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < in.E; ++e) {
+      const double* Xf = in.coords + (size_t)e * NPf * 3;
+      std::vector<double> t1((size_t)Qf * Qf * Q * 3), t2((size_t)Qf * Q * Q * 3);
+      for (int k = 0; k < Qf; ++k)
+        for (int j = 0; j < Qf; ++j)
+          for (int i = 0; i < Q; ++i)
+            for (int l = 0; l < 3; ++l) {
+              double acc = 0.0;
+              for (int b = 0; b < Qf; ++b) acc += J[i * Qf + b] * Xf[((k * Qf + j) * Qf + b) * 3 + l];
+              t1[((k * Qf + j) * Q + i) * 3 + l] = acc;
+            }
+      for (int k = 0; k < Qf; ++k)
+        for (int j = 0; j < Q; ++j)
+          for (int i = 0; i < Q; ++i)
+            for (int l = 0; l < 3; ++l) {
+              double acc = 0.0;
+              for (int b = 0; b < Qf; ++b) acc += J[j * Qf + b] * t1[((k * Qf + b) * Q + i) * 3 + l];
+              t2[((k * Q + j) * Q + i) * 3 + l] = acc;
+            }
+      double* Xt = &X[(size_t)e * NP * 3];
+      for (int k = 0; k < Q; ++k)
+        for (int j = 0; j < Q; ++j)
+          for (int i = 0; i < Q; ++i)
+            for (int l = 0; l < 3; ++l) {
+              double acc = 0.0;
+              for (int b = 0; b < Qf; ++b) acc += J[k * Qf + b] * t2[((b * Q + j) * Q + i) * 3 + l];
+              Xt[((k * Q + j) * Q + i) * 3 + l] = acc;
+            }
+    }
+  }
+  // numbering and Dirichlet flags
+  std::vector<int64_t> ids((size_t)in.E * NP);
+  std::vector<uint8_t> dir;
+  if (Nt == Nf) {
+    std::copy(in.gid, in.gid + ids.size(), ids.begin());
+    L.n = in.n;
+    dir.assign(in.dirichlet, in.dirichlet + in.n);
+  } else {
+    // a coarse node lies on a vertex, an edge, a face or the interior of its element; shared
+    // entities are identified by the fine global ids of their corners, and the node's place on
+    // an edge or face is expressed in a frame fixed by those ids, so every element that shares
+    // the entity computes the same key
+    std::unordered_map<Key, int64_t, KeyHash> map;
+    map.reserve((size_t)in.E * NP);
+    dir.clear();
+    auto fine = [&](int64_t e, int a, int b, int c) { return in.gid[(size_t)e * NPf + (c * Qf + b) * Qf + a]; };
+    auto fend = [&](int t) { return t == 0 ? 0 : Nf; };
+    for (int64_t e = 0; e < in.E; ++e)
+      for (int k = 0; k < Q; ++k)
+        for (int j = 0; j < Q; ++j)
+          for (int i = 0; i < Q; ++i) {
+            const int idx[3] = {i, j, k};
+            const bool end[3] = {i == 0 || i == Nt, j == 0 || j == Nt, k == 0 || k == Nt};
+            const int nend = end[0] + end[1] + end[2];
+            Key key{};
+            bool is_dir = false;
+            if (nend == 3) {
+              const int64_t g = fine(e, fend(i), fend(j), fend(k));
+              key = {0, g, 0, 0, 0, 0, 0};
+              is_dir = in.dirichlet[g] != 0;
+            } else if (nend == 2) {
+              const int d = !end[0] ? 0 : (!end[1] ? 1 : 2);
+              int c0[3] = {fend(i), fend(j), fend(k)}, c1[3] = {fend(i), fend(j), fend(k)};
+              c0[d] = 0;
+              c1[d] = Nf;
+              const int64_t g0 = fine(e, c0[0], c0[1], c0[2]), g1 = fine(e, c1[0], c1[1], c1[2]);
+              const int pos = g0 < g1 ? idx[d] : Nt - idx[d];
+              key = {1, std::min(g0, g1), std::max(g0, g1), pos, 0, 0, 0};
+              is_dir = true;
+              for (int q = 0; q < Qf && is_dir; ++q) {
+                int c[3] = {c0[0], c0[1], c0[2]};
+                c[d] = q;
+                is_dir = in.dirichlet[fine(e, c[0], c[1], c[2])] != 0;
+              }
+            } else if (nend == 1) {
+              const int f = end[0] ? 0 : (end[1] ? 1 : 2);
+              const int d1 = f == 0 ? 1 : 0, d2 = f == 2 ? 1 : 2;
+              int64_t C[2][2];
+              for (int u = 0; u < 2; ++u)
+                for (int v = 0; v < 2; ++v) {
+                  int c[3];
+                  c[f] = fend(idx[f]);
+                  c[d1] = u ? Nf : 0;
+                  c[d2] = v ? Nf : 0;
+                  C[u][v] = fine(e, c[0], c[1], c[2]);
+                }
+              int u0 = 0, v0 = 0;
+              for (int u = 0; u < 2; ++u)
+                for (int v = 0; v < 2; ++v)
+                  if (C[u][v] < C[u0][v0]) {
+                    u0 = u;
+                    v0 = v;
+                  }
+              const int a1 = u0 == 0 ? idx[d1] : Nt - idx[d1];
+              const int a2 = v0 == 0 ? idx[d2] : Nt - idx[d2];
+              const bool first = C[1 - u0][v0] < C[u0][1 - v0];
+              std::array<int64_t, 4> s = {C[0][0], C[0][1], C[1][0], C[1][1]};
+              std::sort(s.begin(), s.end());
+              key = {2, s[0], s[1], s[2], s[3], first ? a1 : a2, first ? a2 : a1};
+              is_dir = true;
+              for (int q1 = 0; q1 < Qf && is_dir; ++q1)
+                for (int q2 = 0; q2 < Qf && is_dir; ++q2) {
+                  int c[3];
+                  c[f] = fend(idx[f]);
+                  c[d1] = q1;
+                  c[d2] = q2;
+                  is_dir = in.dirichlet[fine(e, c[0], c[1], c[2])] != 0;
+                }
+            } else {
+              key = {3, e, i, j, k, 0, 0};
+            }
+            auto it = map.find(key);
+            int64_t g;
+            if (it == map.end()) {
+              g = (int64_t)map.size();
+              map.emplace(key, g);
+              dir.push_back(is_dir ? 1 : 0);
+            } else {
+              g = it->second;
+              if (is_dir) dir[g] = 1;
+            }
+            ids[(size_t)e * NP + (k * Q + j) * Q + i] = g;
+          }
+    L.n = (int64_t)map.size();
+  }
+  if (L.n >= (int64_t)kGidMask) {
+    err = "mesh too large for 30-bit global ids";
+    return false;
+  }
+  L.dirichlet = dir;
+  L.gid.assign((size_t)in.E * NP, 0u);
+  {
+    std::vector<uint8_t> seen((size_t)L.n, 0);
+    for (size_t q = 0; q < ids.size(); ++q) {
+      const int64_t g = ids[q];
+      uint32_t id = (uint32_t)g;
+      if (dir[g]) id |= kGidDirichlet;
+      if (!seen[g]) {
+        seen[g] = 1;
+        id |= kGidOwner;
+      }
+      L.gid[q] = id;
+    }
+    for (int64_t g = 0; g < L.n; ++g)
+      if (!seen[g]) {
+        err = "a global id is used by no element";
+        return false;
+      }
+  }
+  // geometric factors from the coordinates (derivatives by the GLL differentiation matrix) and
+  // the element diagonals
+  L.G.assign((size_t)in.E * 6 * NP, 0.0);
+  L.diag.assign((size_t)L.n, 0.0);
+  std::vector<double> diag_local((size_t)in.E * NP, 0.0);
+  double minJ = 1e300;
+  const double* D = L.Dm.data();
+#pragma omp parallel for schedule(static) reduction(min : minJ)
+  for (int64_t e = 0; e < in.E; ++e) {
+    const double* Xe = &X[(size_t)e * NP * 3];
+    double* G = &L.G[(size_t)e * 6 * NP];
+    for (int k = 0; k < Q; ++k)
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          const int p = (k * Q + j) * Q + i;
+          double Jm[3][3] = {{0}};
+          for (int q = 0; q < Q; ++q)
+            for (int l = 0; l < 3; ++l) {
+              Jm[l][0] += D[i * Q + q] * Xe[((k * Q + j) * Q + q) * 3 + l];
+              Jm[l][1] += D[j * Q + q] * Xe[((k * Q + q) * Q + i) * 3 + l];
+              Jm[l][2] += D[k * Q + q] * Xe[((q * Q + j) * Q + i) * 3 + l];
+            }
+          const double det = point_factors(Jm, L.w[i] * L.w[j] * L.w[k], G + p, NP);
+          minJ = std::min(minJ, det);
+        }
+    for (int k = 0; k < Q; ++k)
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          const int p = (k * Q + j) * Q + i;
+          double acc = 0.0;
+          for (int l = 0; l < Q; ++l) {
+            acc += G[0 * NP + (k * Q + j) * Q + l] * D[l * Q + i] * D[l * Q + i];
+            acc += G[3 * NP + (k * Q + l) * Q + i] * D[l * Q + j] * D[l * Q + j];
+            acc += G[5 * NP + (l * Q + j) * Q + i] * D[l * Q + k] * D[l * Q + k];
+          }
+          const double di = D[i * Q + i], dj = D[j * Q + j], dk = D[k * Q + k];
+          acc += 2.0 * (G[1 * NP + p] * di * dj + G[2 * NP + p] * di * dk + G[4 * NP + p] * dj * dk);
+          diag_local[(size_t)e * NP + p] = acc;
+        }
+  }
+  L.min_jacobian = minJ;
+  if (!(minJ > 0.0)) {
+    err = "mesh has a non-positive Jacobian";
+    return false;
+  }
+  for (size_t q = 0; q < diag_local.size(); ++q) {
+    const uint32_t id = L.gid[q];
+    if (!(id & kGidDirichlet)) L.diag[id & kGidMask] += diag_local[q];
+  }
+  return true;
+}
+
+}  // namespace chebmg

@@ -3,6 +3,7 @@
 // results are uploaded; the hot path never touches these routines.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <vector>
 
 namespace chebmg {
@@ -50,6 +51,26 @@ void fd_fine_stencil(double hx, double hy, double st[9]);
 void fd_galerkin_stencil(const double fine[9], int c, double coarse[9]);
 // Dense inverse of the stencil operator on an m x m grid via Cholesky (host).
 bool fd_dense_inverse(const double st[9], int mx, int my, std::vector<double>& inv);
+
+// A general conforming hexahedral mesh given at order N: per element the GLL point coordinates
+// coords[e][(k (N+1) + j) (N+1) + i][3], the global ids gid[e][...] in [0, n) and a Dirichlet
+// flag per global id.
+struct SemMeshInput {
+  int64_t E = 0;
+  int N = 0;
+  const double* coords = nullptr;
+  const int64_t* gid = nullptr;
+  int64_t n = 0;
+  const uint8_t* dirichlet = nullptr;
+};
+
+// Builds the order-Nt level of a general mesh: at Nt = N the caller's numbering; at a lower
+// order the coordinates are the Lagrange interpolation of the given ones (isoparametric) and
+// the nodes are numbered from the mesh topology (shared vertices, edges and faces are found
+// through the fine ids of their corners; a coarse node is a Dirichlet node when every fine node
+// of its element entity is one).  Geometric factors use derivatives by the GLL differentiation
+// matrix.  false, with a message, on an invalid mesh.
+bool build_sem_level_mesh(const SemMeshInput& in, int Nt, SemHostLevel& out, std::string& err);
 
 // lambda_min / lambda_max that maximises gamma^{-1} (Eq. 2.14) of the order-k 1st-kind
 // smoother (Algorithm 1): the "optimal lambda_min" of Sec. 2.4 (Eq. 2.24 fits it).
