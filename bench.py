@@ -104,6 +104,23 @@ def run_oracle(reps: int):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def run_oracle_all_cores():
+    """One oracle solve per host core, all at once (independent processes, one thread each):
+    the host's whole-machine oracle throughput.  Returns (total DOFs, wall seconds, cores)."""
+    cores = len(os.sched_getaffinity(0))
+    code = ORACLE_SNIPPET % dict(root=ROOT, ne=SAMPLE_NE, orders=ORDERS, kind=KIND, k=K_ORDER, sided=SIDED,
+                                 N=NORDER, rtol=RTOL, reps=1)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.DEVNULL, text=True) for _ in range(cores)]
+    outs = [p.communicate()[0] for p in procs]
+    wall = time.perf_counter() - t0
+    n = sum(json.loads(o.strip().splitlines()[-1])["n"] for o in outs)
+    return n, wall, cores
+
+
 def sample_desc(r):
     return (f"FP64 numpy oracle, one thread, full FCG solve of the same recipe at E={SAMPLE_NE}^3 "
             f"(n={r['n']}, {r['iters']} iterations), setup excluded")
@@ -226,6 +243,27 @@ def bench_batched(cm, W, torch, timed, reps):
     out["ax8_batched_variant"] = {"fp32": cm.chebmg_batch_info(s32.ctx, BATCH_NRHS, 0, cm.CHEBMG_F32)[0],
                                   "fp64": cm.chebmg_batch_info(s64.ctx, BATCH_NRHS, 0, cm.CHEBMG_F64)[0]}
     out["coarse_degree"] = cm.chebmg_batch_info(s32.ctx, BATCH_NRHS, 0, cm.CHEBMG_F32)[1]
+    # batched FP32 order-7 operator: G read once for all right-hand sides
+    X32 = torch.rand((BATCH_NRHS, n), dtype=torch.float32, device="cuda")
+    Y32 = torch.zeros_like(X32)
+    cm.chebmg_apply_A_batched(s32.ctx, 0, cm.CHEBMG_F32, X32, Y32)
+    t_ax, _ = timed(lambda: cm.chebmg_apply_A_batched(s32.ctx, 0, cm.CHEBMG_F32, X32, Y32), 10)
+    Lb = BATCH_NE ** 3 * (NORDER + 1) ** 3
+    alg = 4 * (6 * Lb + 2 * BATCH_NRHS * n)
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    # FP32 pipe: 152 SMs x 128 FMA/clock x 2 flops x max SM clock
+    fp32_peak = 152 * 128 * 2 * (peaks().get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    flops = 111 * Lb * BATCH_NRHS
+    out["roofline_batched_operator"] = {
+        "bound": "hbm", "kernel": "k_sem_ax8b<float> (64 RHS, geometric factors staged once per block) with the "
+                                  "output zeroing", "alg_bytes": alg, "time_us": t_ax * 1e6,
+        "achieved": alg / t_ax / 1e9, "peak": hbm, "unit": "GB/s", "frac": alg / t_ax / 1e9 / hbm,
+        "peak_source": "of measured" if peaks().get("hbm_gbs") else "of fallback",
+        "alu": {"achieved_tflops": flops / t_ax / 1e12, "peak_tflops": fp32_peak,
+                "frac": flops / t_ax / 1e12 / fp32_peak,
+                "peak_source": "FP32 pipe from unit counts and the maximum SM clock (152 x 128 FMA x 2)",
+                "flops": flops}}
+    del X32, Y32
     s32.close()
     s64.close()
 
@@ -401,6 +439,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle throughput")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched / grouped measurements")
     ap.add_argument("--profile-batched", action="store_true",
                     help="set up the 64-RHS E=8^3 batch, warm up, run one batched solve (kernels launched "
@@ -625,9 +664,17 @@ def main():
                 "alg_bytes_per_step": alg_bytes32, "step_us": step32 * 1e6,
                 "elements_per_block_variant": cm.chebmg_tile_choice(s32.ctx, 0, 1)}
     flops64 = 111 * L + 8 * n
+    # FP64 denominator measured like the bf16 one: a cuBLAS DGEMM, 4096^3, best of 5
+    A64 = torch.rand(4096, 4096, dtype=torch.float64, device="cuda")
+    B64 = torch.rand_like(A64)
+    torch.matmul(A64, B64)
+    t_mm, _ = timed(lambda: torch.matmul(A64, B64), 5)
+    peak64 = 2 * 4096 ** 3 / t_mm / 1e12
+    del A64, B64
     fp64_alu = {"bound": "alu", "kernel": "fine FP64 Chebyshev step", "achieved": flops64 / step64 / 1e12,
-                "peak": 1.25, "unit": "TFLOP/s", "frac": flops64 / step64 / 1e12 / 1.25,
-                "peak_source": "nominal FP64 rate of GB300", "step_us": step64 * 1e6}
+                "peak": peak64, "unit": "TFLOP/s", "frac": flops64 / step64 / 1e12 / peak64,
+                "peak_source": "of measured cuBLAS DGEMM rate (4096^3) in this run; nominal GB300 FP64 1.25",
+                "step_us": step64 * 1e6}
 
     world_n = world
     value = job_throughput(world_n, n, t32)
@@ -662,6 +709,13 @@ def main():
         s32.close()
         s64.close()
         line["differentiation"] = bench_differentiation(cm, W, torch, timed, max(1, min(args.steps, 3)))
+    if rank == 0 and not args.no_cpu_baseline and not args.no_all_cores:
+        nall, wall, cores = run_oracle_all_cores()
+        line["cpu_baseline_all_cores"] = {"value": nall / wall / 1e9, "unit": UNIT, "cores": cores,
+                                          "kind": "oracle",
+                                          "sample": f"{cores} concurrent one-thread FP64 oracle solves of the "
+                                                    f"E={SAMPLE_NE}^3 recipe (one per core), setup included in "
+                                                    f"each process, wall time {wall:.1f} s"}
     if rank == 0 and not args.no_cpu_baseline:
         r = run_oracle(1)
         t = r["times"][0]
