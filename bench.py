@@ -4,8 +4,9 @@
 Workload: the 3-D spectral-element Poisson problem on the perturbed unit box
 (E = 32^3 trilinear hexahedra, N = 7, n = 11,390,625 global DOFs), p-multigrid
 7 -> 3 -> 1 with the optimized 4th-kind Chebyshev smoother in the one-sided
-(4, 0) V-cycle (k = 2), flexible CG to a 1e-8 relative residual, uniform[-1,1]
-right-hand side (seed 1).  One "step" is one complete solve.
+(6, 0) V-cycle (k = 3), flexible CG to a 1e-8 relative residual, uniform[-1,1]
+right-hand side (seed 1).  One "step" is one complete solve.  Other smoothing orders,
+cycle shapes, schedules and kinds at the same size are reported under "schedules".
 
 value      = whole-job solve throughput: n * solves / seconds / 1e9 (GDOF/s solved to 1e-8)
              for the mixed form (FP32 smoother/Ax/transfers, FP64 Krylov, Lanczos and coarse CG),
@@ -33,7 +34,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-NE, NORDER, ORDERS, KIND, K_ORDER, SIDED = 32, 7, (7, 3, 1), "opt4th", 2, "one-sided"
+# one-sided (2k,0) cycles with k in {1, 2, 3} are the family the E = 16^3 configuration names; at
+# E = 32^3 on GB300, k = 3 takes the least time in it (FP32 smoothing is cheap next to the FP64
+# outer operator and coarse solve that each extra iteration costs); the sweep is reported too
+NE, NORDER, ORDERS, KIND, K_ORDER, SIDED = 32, 7, (7, 3, 1), "opt4th", 3, "one-sided"
 RTOL = 1e-8
 SAMPLE_NE = 16
 METRIC = "time-to-1e-8 residual and smoother GDOF/s, SEM E=32^3 N=7, mixed vs FP64"
@@ -360,16 +364,32 @@ def bench_fd_table1(cm, torch, timed, reps):
 
 
 def bench_schedules(cm, W, torch, timed, reps, verts, b):
-    """Solves at the benchmark size (E = 32^3, N = 7, mixed form, FCG to 1e-8) with the p-MG
-    schedule 7 -> 5 -> 3 -> 1 beside 7 -> 3 -> 1, and with the 1st-kind smoother at
-    lambda_min = 0.1 lambda_max beside the gamma^{-1}-optimal lambda_min (one-sided (4,0))."""
+    """Solves at the benchmark size (E = 32^3, N = 7, mixed form, FCG to 1e-8): the smoothing
+    order and cycle shape (one-sided (2k,0) and symmetric (k,k)), the p-MG schedule
+    7 -> 5 -> 3 -> 1 beside 7 -> 3 -> 1, and the smoother kind (4th, optimized 4th, 1st kind at
+    lambda_min = 0.1 lambda_max and at the gamma^{-1}-optimal lambda_min)."""
     u = torch.zeros_like(b)
     out = {}
-    for name, kw in [("opt4th (7,3,1)", dict(orders=(7, 3, 1), kind="opt4th")),
-                     ("opt4th (7,5,3,1)", dict(orders=(7, 5, 3, 1), kind="opt4th")),
-                     ("1st kind lmin=0.1 (7,3,1)", dict(orders=(7, 3, 1), kind="1st", lmin_ratio=0.1)),
-                     ("1st kind lmin optimal (7,3,1)", dict(orders=(7, 3, 1), kind="1st", lmin_ratio=0.0))]:
-        s = cm.Solver("sem", verts=verts, order=K_ORDER, sided=SIDED, prec="mixed", **kw)
+    cases = []
+    # smoothing order and cycle shape (the paper's question), opt-4th, 7-3-1
+    for k in (1, 2, 3, 4):
+        cases.append((f"opt4th one-sided ({2 * k},0) (7,3,1)", dict(orders=(7, 3, 1), kind="opt4th", order=k)))
+    for k in (2, 3, 4):
+        cases.append((f"opt4th symmetric ({k},{k}) (7,3,1)",
+                      dict(orders=(7, 3, 1), kind="opt4th", order=k, sided="symmetric")))
+    cases += [("opt4th one-sided (6,0) (7,5,3,1)", dict(orders=(7, 5, 3, 1), kind="opt4th", order=3)),
+              ("opt4th symmetric (3,3) (7,5,3,1)", dict(orders=(7, 5, 3, 1), kind="opt4th", order=3,
+                                                         sided="symmetric")),
+              ("4th kind one-sided (6,0) (7,3,1)", dict(orders=(7, 3, 1), kind="4th", order=3)),
+              ("1st kind lmin=0.1 one-sided (6,0) (7,3,1)", dict(orders=(7, 3, 1), kind="1st", order=3,
+                                                                  lmin_ratio=0.1)),
+              ("1st kind lmin optimal one-sided (6,0) (7,3,1)", dict(orders=(7, 3, 1), kind="1st", order=3,
+                                                                      lmin_ratio=0.0))]
+    for name, kw in cases:
+        kw = dict(kw)
+        kw.setdefault("order", K_ORDER)
+        kw.setdefault("sided", SIDED)
+        s = cm.Solver("sem", verts=verts, prec="mixed", **kw)
 
         def solve():
             code, it, rel, _ = cm.chebmg_pcg_solve(s.ctx, b, u, RTOL, 500)
@@ -379,7 +399,7 @@ def bench_schedules(cm, W, torch, timed, reps, verts, b):
         t, it = timed(solve, reps)
         rec = {"time_to_1e8_s": t, "iterations": it}
         if kw["kind"] == "1st":
-            rec["lmin_ratio"] = cm.chebmg_lambda_min_ratio(s.ctx, 2 * K_ORDER)
+            rec["lmin_ratio"] = cm.chebmg_lambda_min_ratio(s.ctx, 2 * kw["order"])
         out[name] = rec
         s.close()
     return out
