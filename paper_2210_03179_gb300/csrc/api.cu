@@ -596,6 +596,7 @@ double lanczos(chebmg_ctx* c, int j, int steps) {
   splitmix_fill(n, 42ull, S, v, c->s);
   dot2(n, v, v, nullptr, nullptr, S_T0, -1, POST_NONE, c->partial, c->scal, c->s);
   read_scal(c);
+  if (!(c->hscal[S_T0] > 0.0)) return 1.0;   // no free node on this level: nothing to smooth or solve
   scale(n, 1.0 / std::sqrt(c->hscal[S_T0]), v, v, c->s);
   zero<double>(c, vp, n);
   std::vector<double> al, be;
