@@ -70,6 +70,35 @@ __device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T
 
 // x += beta d; r -= y; d = c1 d + c2 S r; y = 0 -- 16-byte vector accesses over the aligned
 // body (every pointer comes from a 256-byte aligned allocation), scalar tail.
+// 16-byte global accesses with an L2 eviction hint.  The update streams x, r and S (evict
+// first) and keeps d and y in L2 (evict last): the next operator application gathers d and
+// accumulates into y, so they should still be there when it runs.
+__device__ __forceinline__ uint64_t l2_policy_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+template <typename VT>
+__device__ __forceinline__ VT ld16(const VT* p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return *reinterpret_cast<VT*>(&v);
+}
+template <typename VT>
+__device__ __forceinline__ void st16(VT* p, const VT& val, uint64_t pol) {
+  const uint4 v = *reinterpret_cast<const uint4*>(&val);
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w), "l"(pol)
+               : "memory");
+}
+
 template <typename T, bool VEC>
 __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
                              T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, int64_t ld) {
@@ -79,10 +108,11 @@ __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
   const int64_t nv = VEC ? n / L : 0;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint64_t first = l2_policy_first(), last = l2_policy_last();
   for (int64_t q = tid; q < nv; q += stride) {
-    VT xv = reinterpret_cast<VT*>(x)[q], rv = reinterpret_cast<VT*>(r)[q], dv = reinterpret_cast<VT*>(d)[q];
-    VT yv = reinterpret_cast<VT*>(y)[q];
-    const VT sv = reinterpret_cast<const VT*>(invD)[q];
+    VT xv = ld16(reinterpret_cast<VT*>(x) + q, first), rv = ld16(reinterpret_cast<VT*>(r) + q, first);
+    VT dv = ld16(reinterpret_cast<VT*>(d) + q, last), yv = ld16(reinterpret_cast<VT*>(y) + q, last);
+    const VT sv = ld16(reinterpret_cast<const VT*>(invD) + q, first);
     T* xs = reinterpret_cast<T*>(&xv);
     T* rs = reinterpret_cast<T*>(&rv);
     T* ds = reinterpret_cast<T*>(&dv);
@@ -90,10 +120,10 @@ __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
     const T* ss = reinterpret_cast<const T*>(&sv);
 #pragma unroll
     for (int l = 0; l < L; ++l) cheb4_one(xs[l], rs[l], ds[l], ys[l], ss[l], beta, c1, c2);
-    reinterpret_cast<VT*>(x)[q] = xv;
-    reinterpret_cast<VT*>(r)[q] = rv;
-    reinterpret_cast<VT*>(d)[q] = dv;
-    reinterpret_cast<VT*>(y)[q] = yv;
+    st16(reinterpret_cast<VT*>(x) + q, xv, first);
+    st16(reinterpret_cast<VT*>(r) + q, rv, first);
+    st16(reinterpret_cast<VT*>(d) + q, dv, last);
+    st16(reinterpret_cast<VT*>(y) + q, yv, last);
   }
   for (int64_t g = nv * L + tid; g < n; g += stride) cheb4_one(x[g], r[g], d[g], y[g], invD[g], beta, c1, c2);
 }
