@@ -696,6 +696,21 @@ def main():
                 "peak_source": "of measured cuBLAS DGEMM rate (4096^3) in this run; nominal GB300 FP64 1.25",
                 "step_us": step64 * 1e6}
 
+    # ---- coarse solve (N = 1, FP64 CG to the coarse tolerance) on its own ----
+    def coarse_time(s):
+        nc = s.size(len(ORDERS) - 1)
+        rc = torch.empty(nc, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+        zc = torch.zeros_like(rc)
+        its = cm.chebmg_coarse_solve(s.ctx, rc, zc)
+        t_c, _ = timed(lambda: cm.chebmg_coarse_solve(s.ctx, rc, zc), 20)
+        deg, _ = cm.chebmg_coarse_info(s.ctx)
+        kern, blocks, rows = cm.chebmg_coarse_shape(s.ctx)
+        return {"ms": t_c * 1e3, "iterations": its, "degree": deg,
+                "kernel": {cm.CHEBMG_COARSE_GRID: "grid", cm.CHEBMG_COARSE_CLUSTER: "cluster"}.get(kern, "host"),
+                "blocks": blocks, "rows_per_block": rows, "n": nc}
+
+    coarse = {"mixed": coarse_time(s32), "fp64": coarse_time(s64)}
+
     world_n = world
     value = job_throughput(world_n, n, t32)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_n, "steps": args.steps,
@@ -712,6 +727,7 @@ def main():
                     "d2h_bytes_per_step": 8 * n},
             "gpu_launches": int(launches),
             "roofline": roofline, "roofline_fp64": fp64_alu,
+            "coarse_solve": coarse,
             "clocks": clk}
     if not args.no_batched:
         s32.close()

@@ -139,6 +139,21 @@ int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* element
  * `degree` applied from zero with Jacobi scaling (degree 1 = Jacobi-PCG), chosen at setup
  * by timing; lmax = lambda_max of S A on the coarse level (FP64 Lanczos). */
 int chebmg_coarse_info(const chebmg_ctx* ctx, int* degree, double* lmax);
+/* Kernels of the SEM coarse CG (same method, same status words):
+ *   CHEBMG_COARSE_GRID    one persistent cooperative launch over up to one block per SM;
+ *                         products exchange rows through global memory with flags, grid-wide
+ *                         reductions on an arrival counter (any coarse mesh);
+ *   CHEBMG_COARSE_CLUSTER one thread-block cluster (up to 16 CTAs): box lattices at N = 1 with
+ *                         the FP32 preconditioner; the operator's FP32 copy and the exchanged
+ *                         vectors in shared memory, halos through distributed shared memory,
+ *                         hardware cluster barriers;
+ *   CHEBMG_COARSE_HOST    host-driven loop of kernels (cooperative launch unavailable). */
+enum { CHEBMG_COARSE_HOST = 0, CHEBMG_COARSE_GRID = 1, CHEBMG_COARSE_CLUSTER = 2 };
+/* Kernel chosen at setup (timed together with the degree), its thread blocks and the rows
+ * each block owns (grid: a power of two times 256; cluster: planes x lattice plane). */
+int chebmg_coarse_shape(const chebmg_ctx* ctx, int* kernel, int* blocks, int* rows_per_block);
+/* Overrides the coarse kernel (GRID or CLUSTER); EINVAL where it does not apply. */
+int chebmg_set_coarse_kernel(chebmg_ctx* ctx, int kernel);
 int chebmg_set_coarse_degree(chebmg_ctx* ctx, int degree);
 int chebmg_set_tile_choice(chebmg_ctx* ctx, int level, int dtype, int variant);
 

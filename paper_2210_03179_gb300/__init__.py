@@ -38,6 +38,9 @@ CHEBMG_FP64 = 0
 CHEBMG_FP32_SMOOTHER = 1
 CHEBMG_F64 = 0
 CHEBMG_F32 = 1
+CHEBMG_COARSE_HOST = 0
+CHEBMG_COARSE_GRID = 1
+CHEBMG_COARSE_CLUSTER = 2
 
 KINDS = {"1st": CHEBMG_CHEB_1ST, "4th": CHEBMG_CHEB_4TH, "opt4th": CHEBMG_CHEB_4TH_OPT}
 SIDED = {"symmetric": CHEBMG_SYMMETRIC, "one-sided": CHEBMG_ONE_SIDED}
@@ -86,6 +89,8 @@ _SIGNATURES = {
     "chebmg_set_coarse_precond_dtype": (c_int, [c_void_p, c_int, c_int]),
     "chebmg_lambda_min_ratio": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "chebmg_coarse_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
+    "chebmg_coarse_shape": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "chebmg_set_coarse_kernel": (c_int, [c_void_p, c_int]),
     "chebmg_set_coarse_degree": (c_int, [c_void_p, c_int]),
     "chebmg_apply_A": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "chebmg_inv_diagonal": (c_int, [c_void_p, c_int, c_int, c_void_p]),
@@ -269,6 +274,17 @@ def chebmg_coarse_info(ctx):
     m, l = c_int(), c_double()
     _check(lib().chebmg_coarse_info(ctx, byref(m), byref(l)), "chebmg_coarse_info")
     return m.value, l.value
+
+
+def chebmg_coarse_shape(ctx):
+    """(kernel, thread blocks, rows per block) of the coarse CG (CHEBMG_COARSE_* kernels)."""
+    k, g, r = c_int(), c_int(), c_int()
+    _check(lib().chebmg_coarse_shape(ctx, byref(k), byref(g), byref(r)), "chebmg_coarse_shape")
+    return k.value, g.value, r.value
+
+
+def chebmg_set_coarse_kernel(ctx, kernel: int) -> None:
+    _check(lib().chebmg_set_coarse_kernel(ctx, int(kernel)), "chebmg_set_coarse_kernel")
 
 
 def chebmg_set_coarse_degree(ctx, degree):

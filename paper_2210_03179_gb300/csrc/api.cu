@@ -129,14 +129,20 @@ struct chebmg_ctx {
   unsigned* cctl = nullptr;     // [5] control words of the persistent kernel
   unsigned* hcctl = nullptr;    // pinned host copy
   double* cpart = nullptr;      // [2][3 * coarse_grid] block partials, by generation parity
-  double* cxbuf[2] = {nullptr, nullptr};   // exchange buffers of the persistent coarse CG
-  float* cxbufF[2] = {nullptr, nullptr};   // FP32 exchange buffers (FP32 preconditioner)
+  unsigned long long* cexf[2] = {nullptr, nullptr};   // tagged exchange of the persistent coarse CG: FP32
+  unsigned long long* cexd[2] = {nullptr, nullptr};   // and FP64
+  uint64_t coarse_gen = 0;      // exchange tags used so far (advanced per launch)
   float* ell_valf = nullptr;    // FP32 copies for the FP32 preconditioner
   float* coarse_invDf = nullptr;
   bool coarse_pf32 = false;     // coarse CG preconditioner in FP32
-  unsigned* cflag = nullptr;    // [coarse_grid] exchange flags
   int coarse_rows_per_block = 0;
-  int coarse_halo = 0;
+  // coarse CG on one thread-block cluster (box lattice at N = 1, FP32 preconditioner)
+  int coarse_kernel = 0;        // 0 grid-wide persistent kernel, 1 cluster kernel
+  float* cc_val32 = nullptr;    // [14][n] symmetric stencil layout
+  double* cc_val64 = nullptr;
+  int cc_nx = 0, cc_ny = 0, cc_nz = 0, cc_ctas = 0, cc_rmax = 0;
+  size_t cc_smem = 0;
+  bool cc_ok = false;
   int coarse_degree = 1;        // 4th-kind polynomial preconditioner degree (autotuned)
   double coarse_lmax = 0.0;
   unsigned* dstat = nullptr;    // [4] device-side error flags: [0] operator wait, [1] batched coarse
@@ -364,6 +370,14 @@ void prolong_to(chebmg_ctx* c, int j, const T* zc, T* zf, int accumulate) {
   check_launch();
 }
 
+// Shape of the persistent coarse kernel: at least rpt_min rows per thread.
+void set_coarse_shape(chebmg_ctx* c, int rpt_min) {
+  int grid = 0, rb = 0;
+  coarse_pcg_shape(c->L.back().n, rpt_min, &grid, &rb);
+  c->coarse_grid = grid;
+  c->coarse_rows_per_block = rb;
+}
+
 CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
   Level& C = c->L.back();
   CoarseCG a;
@@ -374,11 +388,7 @@ CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
   a.invD = static_cast<const double*>(C.invD[CHEBMG_F64]);
   a.b = b;
   a.x = x;
-  a.xbuf[0] = c->cxbuf[0];
-  a.xbuf[1] = c->cxbuf[1];
-  a.flag = c->cflag;
   a.rows_per_block = c->coarse_rows_per_block;
-  a.halo = c->coarse_halo;
   a.part = c->cpart;
   a.ctl = c->cctl;
   a.rtol = c->o.coarse_rtol;
@@ -389,16 +399,29 @@ CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
   a.pf32 = c->coarse_pf32 ? 1 : 0;
   a.valf = c->ell_valf;
   a.invDf = c->coarse_invDf;
-  a.xbufF[0] = c->cxbufF[0];
-  a.xbufF[1] = c->cxbufF[1];
+  a.exf[0] = c->cexf[0];
+  a.exf[1] = c->cexf[1];
+  a.exd[0] = c->cexd[0];
+  a.exd[1] = c->cexd[1];
+  // exchanges one launch can make: (degree - 1) per preconditioner application, one more per
+  // CG iteration, maxit + 1 applications
+  const uint64_t tags = (uint64_t)(std::max(1, a.degree) + 1) * (uint64_t)(std::max(0, a.maxit) + 2) + 4;
+  if (tags >= 0x7fffffffull) throw Error(CHEBMG_EINVAL, "coarse degree x iterations too large");
+  if (c->coarse_gen + tags >= 0xffffffffull) {   // tags would wrap: clear the buffers, restart
+    for (int q = 0; q < 2; ++q) {
+      CK(cudaMemsetAsync(c->cexf[q], 0, sizeof(unsigned long long) * a.n, c->s));
+      CK(cudaMemsetAsync(c->cexd[q], 0, sizeof(unsigned long long) * 2 * a.n, c->s));
+    }
+    c->coarse_gen = 0;
+  }
+  a.gen0 = (unsigned)c->coarse_gen;
+  c->coarse_gen += tags;
   return a;
 }
 
-// Resets the control words and exchange flags of the persistent coarse kernel.
-void coarse_reset(chebmg_ctx* c) {
-  CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 4, c->s));
-  CK(cudaMemsetAsync(c->cflag, 0, sizeof(unsigned) * std::max(1, c->coarse_grid), c->s));
-}
+// Resets the control words of the persistent coarse kernels (the exchange needs no reset:
+// each launch takes fresh tags).
+void coarse_reset(chebmg_ctx* c) { CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 4, c->s)); }
 
 // FP64 coarse solve on the last level: FD dense inverse, SEM Jacobi-PCG.
 int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {
@@ -412,6 +435,31 @@ int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {
   }
   const double* S = static_cast<const double*>(C.invD[CHEBMG_F64]);
   double *r = c->cr, *z = c->cz, *p = c->cp, *q = c->cq;
+  if (c->coarse_kernel == 1 && c->cc_ok && c->coarse_pf32) {
+    // whole PCG on one thread-block cluster (status words as below)
+    coarse_reset(c);
+    CoarseCluster a;
+    a.nx = c->cc_nx;
+    a.ny = c->cc_ny;
+    a.nz = c->cc_nz;
+    a.ctas = c->cc_ctas;
+    a.rmax = c->cc_rmax;
+    a.val32 = c->cc_val32;
+    a.val64 = c->cc_val64;
+    a.invDf = c->coarse_invDf;
+    a.b = b;
+    a.x = x;
+    a.rtol = c->o.coarse_rtol;
+    a.maxit = c->o.coarse_maxit;
+    a.degree = c->coarse_degree;
+    a.lmax = c->coarse_lmax > 0.0 ? c->coarse_lmax : 1.0;
+    a.ctl = c->cctl;
+    cudaError_t e = cudaSuccess;
+    if (coarse_cluster_launch(a, c->cc_smem, c->s, &e)) return CHEBMG_OK;
+    cudaGetLastError();
+    c->cc_ok = false;   // cluster launch refused: grid-wide kernel from now on
+    c->coarse_kernel = 0;
+  }
   if (c->coop_ok) {
     // whole PCG in one cooperative launch; no host round trip.  Status and iterations
     // land in cctl[2..3], errors also in the sticky cctl[4].
@@ -666,21 +714,23 @@ void common_alloc(chebmg_ctx* c) {
     int coop = 0;
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev));
     int grid = 0, rb = 0;
-    coarse_pcg_shape(nc, &grid, &rb);
-    c->coarse_grid = grid;
-    c->coarse_rows_per_block = rb;
+    coarse_pcg_shape(nc, 1, &grid, &rb);   // the widest shape: buffers are sized for it
+    set_coarse_shape(c, 1);
     c->coop_ok = coop != 0 && grid > 0;
+    if (c->cc_val64)
+      c->cc_ok = coarse_cluster_plan(c->cc_nx, c->cc_ny, c->cc_nz, &c->cc_ctas, &c->cc_rmax, &c->cc_smem);
     c->cctl = dalloc<unsigned>(c, 5);
     CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 5, c->s));
     CK(cudaMallocHost(&h, sizeof(unsigned) * 5));
     c->hcctl = static_cast<unsigned*>(h);
     std::memset(c->hcctl, 0, sizeof(unsigned) * 5);
     c->cpart = dalloc<double>(c, 6 * std::max(1, grid));   // two generations of 3 partials per block
-    c->cxbuf[0] = dalloc<double>(c, nc);
-    c->cxbuf[1] = dalloc<double>(c, nc);
-    c->cxbufF[0] = dalloc<float>(c, nc);
-    c->cxbufF[1] = dalloc<float>(c, nc);
-    c->cflag = dalloc<unsigned>(c, std::max(1, grid));
+    for (int q = 0; q < 2; ++q) {   // tag 0 (zeroed words) is never used
+      c->cexf[q] = dalloc<unsigned long long>(c, nc);
+      c->cexd[q] = dalloc<unsigned long long>(c, 2 * nc);
+      CK(cudaMemsetAsync(c->cexf[q], 0, sizeof(unsigned long long) * nc, c->s));
+      CK(cudaMemsetAsync(c->cexd[q], 0, sizeof(unsigned long long) * 2 * nc, c->s));
+    }
   }
 }
 
@@ -733,8 +783,12 @@ void autotune_ax8(chebmg_ctx* c, int j) {
   CK(cudaMemsetAsync(y, 0, sizeof(T) * L.n, c->s));
 }
 
-// Picks the degree of the coarse CG's polynomial preconditioner by timing full coarse solves
-// of a seeded right-hand side (degree 1 = Jacobi-PCG).
+// Picks the coarse CG's kernel, the degree of its polynomial preconditioner and (grid-wide
+// kernel) the rows per thread by timing full coarse solves of a seeded right-hand side
+// (degree 1 = Jacobi-PCG).  More rows per thread means fewer blocks: cheaper exchanges and
+// reductions, but more FP64 work per block in each product.  The cluster kernel (box lattices,
+// FP32 preconditioner) exchanges through distributed shared memory at a fraction of the
+// grid-wide latency but has 16 SMs for the FP64 products.
 void autotune_coarse_degree(chebmg_ctx* c) {
   Level& C = c->L.back();
   const int64_t n = C.n;
@@ -745,8 +799,18 @@ void autotune_coarse_degree(chebmg_ctx* c) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_m = 1;
-  for (int m : {1, 2, 4, 8, 12, 16}) {
+  int best_m = 1, best_rpt = 1, last_rb = -1, best_kernel = 0;
+  const bool try_cluster = c->cc_ok && c->coarse_pf32;
+  for (int rpt = 1; rpt <= 2 * kCoarseMaxRowsPerThread; rpt *= 2) {
+    const bool cluster = rpt > kCoarseMaxRowsPerThread;   // last round: the cluster kernel
+    if (cluster && !try_cluster) break;
+    c->coarse_kernel = cluster ? 1 : 0;
+    if (!cluster) {
+      set_coarse_shape(c, rpt);
+      if (c->coarse_grid <= 0 || c->coarse_rows_per_block == last_rb) continue;
+      last_rb = c->coarse_rows_per_block;
+    }
+  for (int m : {1, 2, 4, 8, 12, 16, 24, 32}) {
     c->coarse_degree = m;
     float t_min = 1e30f;
     bool ok = true;
@@ -764,9 +828,14 @@ void autotune_coarse_degree(chebmg_ctx* c) {
     if (ok && t_min < best) {
       best = t_min;
       best_m = m;
+      best_rpt = rpt;
+      best_kernel = c->coarse_kernel;
     }
   }
+  }
   c->coarse_degree = best_m;
+  c->coarse_kernel = best_kernel;
+  set_coarse_shape(c, best_kernel == 1 ? 1 : best_rpt);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaMemsetAsync(c->cctl + 4, 0, sizeof(unsigned), c->s));
@@ -1746,6 +1815,44 @@ int group_solve(chebmg_group* g, const double* const* B, double* const* U, doubl
 
 // Uploads the host-built SEM levels (finest first) and assembles the coarsest level's ELL
 // form; boxed = the levels carry the box lattice (lattice kernels usable).
+// The N = 1 box operator in the symmetric 27-point stencil layout of the cluster coarse
+// kernel: row g keeps the 14 forward-half entries (slot k <-> lattice offset cc_d*(k)), each
+// the mean of A(g, g + o) and A(g + o, g).  Leaves the cluster kernel off if an entry is not
+// a lattice neighbour (cannot happen for a box).
+void stencil_layout(chebmg_ctx* c, const SemHostLevel& h, const std::vector<int>& col,
+                    const std::vector<double>& val) {
+  const int nx = h.nex + 1, ny = h.ney + 1, nz = h.nez + 1;
+  const int64_t n = h.n;
+  if ((int64_t)nx * ny * nz != n) return;
+  std::vector<double> v64((size_t)kCcSlots * n, 0.0);
+  auto slot_of = [](int dx, int dy, int dz) {
+    for (int k = 0; k < kCcSlots; ++k)
+      if (cc_dx(k) == dx && cc_dy(k) == dy && cc_dz(k) == dz) return k;
+    return -1;
+  };
+  for (int64_t g = 0; g < n; ++g) {
+    const int gx = (int)(g % nx), gy = (int)((g / nx) % ny), gz = (int)(g / ((int64_t)nx * ny));
+    for (int s = 0; s < c->nslot; ++s) {
+      const int64_t cc = col[(size_t)s * n + g];
+      const double v = val[(size_t)s * n + g];
+      const int dx = (int)(cc % nx) - gx, dy = (int)((cc / nx) % ny) - gy,
+                dz = (int)(cc / ((int64_t)nx * ny)) - gz;
+      if (std::abs(dx) > 1 || std::abs(dy) > 1 || std::abs(dz) > 1) {
+        if (v != 0.0) return;
+        continue;
+      }
+      const int kf = slot_of(dx, dy, dz), kb = slot_of(-dx, -dy, -dz);
+      if (kf >= 0) v64[(size_t)kf * n + g] += 0.5 * v;       // stored in row g
+      if (kb >= 0) v64[(size_t)kb * n + cc] += 0.5 * v;      // stored in row cc (mirror)
+    }
+  }
+  c->cc_val64 = upload<double>(c, v64);
+  c->cc_val32 = upload<float>(c, v64);
+  c->cc_nx = nx;
+  c->cc_ny = ny;
+  c->cc_nz = nz;
+}
+
 void upload_sem_levels(chebmg_ctx* c, std::vector<SemHostLevel>& H, bool boxed) {
   const int nlevels = (int)H.size();
   for (int j = 0; j < nlevels; ++j) {
@@ -1788,16 +1895,7 @@ void upload_sem_levels(chebmg_ctx* c, std::vector<SemHostLevel>& H, bool boxed) 
       std::vector<int> col;
       std::vector<double> val;
       assemble_ell(h, c->nslot, col, val);
-      int grid = 0, rb = 0;
-      coarse_pcg_shape(h.n, &grid, &rb);
-      int halo = 0;
-      if (rb > 0)
-        for (int64_t g = 0; g < h.n; ++g)
-          for (int k = 0; k < c->nslot; ++k) {
-            const int64_t cc = col[(size_t)k * h.n + g];
-            halo = std::max<int>(halo, (int)std::llabs(cc / rb - g / rb));
-          }
-      c->coarse_halo = halo;
+      if (boxed && h.N == 1) stencil_layout(c, h, col, val);
       c->ell_col = dalloc<int>(c, (int64_t)col.size());
       CK(cudaMemcpy(c->ell_col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
       c->ell_val = upload<double>(c, val);
@@ -1998,6 +2096,35 @@ int chebmg_coarse_info(const chebmg_ctx* c, int* degree, double* lmax) {
   return CHEBMG_OK;
 }
 
+int chebmg_coarse_shape(const chebmg_ctx* c, int* kernel, int* blocks, int* rows_per_block) {
+  if (!c || !kernel || !blocks || !rows_per_block) return CHEBMG_EINVAL;
+  const bool sem = c->L.back().type == TYPE_SEM && c->ell_col;
+  const bool cluster = sem && c->coarse_kernel == 1 && c->cc_ok && c->coarse_pf32;
+  const bool grid = sem && !cluster && c->coop_ok;
+  *kernel = cluster ? CHEBMG_COARSE_CLUSTER : grid ? CHEBMG_COARSE_GRID : CHEBMG_COARSE_HOST;
+  *blocks = cluster ? c->cc_ctas : grid ? c->coarse_grid : 0;
+  *rows_per_block = cluster ? c->cc_rmax : grid ? c->coarse_rows_per_block : 0;
+  return CHEBMG_OK;
+}
+
+int chebmg_set_coarse_kernel(chebmg_ctx* c, int kernel) {
+  return guard([&]() -> int {
+    enter(c);
+    if (kernel == CHEBMG_COARSE_CLUSTER) {
+      if (!c->cc_ok || !c->coarse_pf32)
+        throw Error(CHEBMG_EINVAL, "cluster coarse kernel needs a box lattice at N = 1 and an FP32 preconditioner");
+      c->coarse_kernel = 1;
+    } else if (kernel == CHEBMG_COARSE_GRID) {
+      if (!c->coop_ok) throw Error(CHEBMG_EINVAL, "no grid-wide persistent coarse kernel in this context");
+      c->coarse_kernel = 0;
+    } else {
+      throw Error(CHEBMG_EINVAL, "bad coarse kernel");
+    }
+    drop_graphs(c);
+    return CHEBMG_OK;
+  });
+}
+
 int chebmg_lambda_min_ratio(chebmg_ctx* c, int order, double* ratio) {
   return guard([&]() -> int {
     if (!c || !ratio || order < 1 || order > 256) throw Error(CHEBMG_EINVAL, "bad arguments");
@@ -2012,6 +2139,7 @@ int chebmg_set_coarse_precond_dtype(chebmg_ctx* c, int dtype, int retune) {
     if (dtype != CHEBMG_F64 && dtype != CHEBMG_F32) throw Error(CHEBMG_EINVAL, "bad dtype");
     if (!c->ell_col) throw Error(CHEBMG_EINVAL, "no SEM coarse CG in this context");
     c->coarse_pf32 = dtype == CHEBMG_F32;
+    if (!c->coarse_pf32) c->coarse_kernel = 0;   // the cluster kernel has an FP32 preconditioner only
     if (retune && c->coop_ok) autotune_coarse_degree(c);
     drop_graphs(c);
     CK(cudaStreamSynchronize(c->s));
@@ -2020,7 +2148,7 @@ int chebmg_set_coarse_precond_dtype(chebmg_ctx* c, int dtype, int retune) {
 }
 
 int chebmg_set_coarse_degree(chebmg_ctx* c, int degree) {
-  if (!c || degree < 1 || degree > 64) return CHEBMG_EINVAL;
+  if (!c || degree < 1 || degree > kCoarseMaxDegree) return CHEBMG_EINVAL;
   c->coarse_degree = degree;
   c->bcoarse_degree = degree;
   drop_graphs(c);

@@ -286,6 +286,10 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
     cb_spmv<NS, RPT>(a, sv, y);
   };
   const double c0 = 4.0 / (3.0 * a.lmax);
+  __shared__ CoarseCoef coef;
+  __shared__ double s_alpha, s_beta;
+  coarse_coef_fill(coef, a.degree, a.lmax);
+  __syncthreads();
   // the same polynomial on FP32 copies (the vector of each product in the same shared memory)
   auto precond_f = [&]() {
     float* svf = reinterpret_cast<float*>(sv);
@@ -307,8 +311,7 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
         if (live[q]) svf[threadIdx.x + q * kCBThreads] = df[q];
       __syncthreads();
       cb_spmv_f<NS, RPT>(a, svf, yf);
-      const float c1 = (float)((2.0 * i - 1.0) / (2.0 * i + 3.0));
-      const float c2 = (float)((8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax));
+      const float c1 = coef.c1f[i], c2 = coef.c2f[i];
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         rf[q] -= yf[q];
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
 #pragma unroll
       for (int q = 0; q < RPT; ++q) z[q] += d[q];
       product(d);
-      const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0), c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax);
+      const double c1 = coef.c1[i], c2 = coef.c2[i];
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         rp[q] -= y[q];
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
       finish(CS_BREAKDOWN, it);
       return;
     }
-    const double alpha = gam / pq;
+    const double alpha = block_div(&s_alpha, gam, pq);
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       ro[q] = r[q];
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(kCBThreads) k_coarse_block(CoarseBlock a) {
       finish(CS_OK, it);
       return;
     }
-    const double beta = PF32 ? (gnew - u1) / gam : gnew / gam;   // flexible beta for FP32
+    const double beta = block_div(&s_beta, PF32 ? gnew - u1 : gnew, gam);   // flexible beta for FP32
     gam = gnew;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) p[q] = fma(beta, p[q], z[q]);

@@ -154,10 +154,7 @@ struct CoarseCG {
   const double* invD;
   const double* b;
   double* x;
-  double* xbuf[2];       // vector exchanged for the next product, double-buffered by generation parity
-  unsigned* flag;        // [gridDim] last generation each block has published
   int rows_per_block;    // block q owns rows [q * rows_per_block, (q + 1) * rows_per_block)
-  int halo;              // block q reads rows owned by blocks q - halo .. q + halo (symmetric)
   double* part;          // [2][3 * gridDim] block partials, double-buffered by reduction parity
   unsigned* ctl;         // [5], ctl[0] (monotonic arrival counter) zero at launch
   double rtol;
@@ -172,15 +169,84 @@ struct CoarseCG {
   int pf32;
   const float* valf;     // ELL values, FP32
   const float* invDf;    // Jacobi diagonal, FP32
-  float* xbufF[2];       // FP32 exchange buffers
+  // Products exchange the vector they read through tagged words: each value travels with its
+  // exchange tag in one 64-bit word (single-copy atomic; FP64 values as two such words), so a
+  // reader needs no flag and no fence -- it reloads the words whose tag is not there yet.
+  // Buffers alternate with the parity of the kernel's exchange counter; the tags of one launch
+  // are gen0 + 1, gen0 + 2, ..., and the host moves gen0 past every tag a launch can use, so
+  // words left by an earlier launch never match.
+  unsigned long long* exf[2];   // [n] FP32 values
+  unsigned long long* exd[2];   // [2 n] FP64 values
+  unsigned gen0;
 };
+// Step coefficients of the coarse CG's polynomial preconditioner (Algorithm 2, beta = 1):
+// step i (1 <= i < degree) updates d = c1[i] d + c2[i] S r.  The coarse kernels fill this table
+// once per launch, one thread per entry, instead of dividing in every thread at every step:
+// FP64 runs at a small fraction of the FP32 rate on this GPU, and a block-wide FP64 division
+// costs about as much as a short product.
+constexpr int kCoarseMaxDegree = 64;
+struct CoarseCoef {
+  double c1[kCoarseMaxDegree], c2[kCoarseMaxDegree];
+  float c1f[kCoarseMaxDegree], c2f[kCoarseMaxDegree];
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ void coarse_coef_fill(CoarseCoef& t, int degree, double lmax) {
+  for (int i = threadIdx.x; i < degree && i < kCoarseMaxDegree; i += blockDim.x) {
+    const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0), c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lmax);
+    t.c1[i] = c1;
+    t.c2[i] = c2;
+    t.c1f[i] = (float)c1;
+    t.c2f[i] = (float)c2;
+  }
+}
+// num / den divided by one thread and shared with the block through *slot.  The caller must
+// not write *slot again before a later block barrier.
+__device__ __forceinline__ double block_div(double* slot, double num, double den) {
+  if (threadIdx.x == 0) *slot = num / den;
+  __syncthreads();
+  return *slot;
+}
+#endif
+
 // Rows per thread the persistent coarse kernel can keep in registers.
 constexpr int kCoarseMaxRowsPerThread = 8;
 constexpr int kCoarseThreadsPerBlock = 256;
 // Returns false (nothing launched) if a cooperative launch is not possible.
 bool coarse_pcg_launch(const CoarseCG& a, int grid, cudaStream_t s, cudaError_t* err);
-// Grid size (blocks) and rows per block for a coarse problem of n rows; grid 0 = not possible.
-void coarse_pcg_shape(int64_t n, int* grid, int* rows_per_block);
+// Grid size (blocks) and rows per block for a coarse problem of n rows, at least rpt_min rows
+// per thread (a power of two up to kCoarseMaxRowsPerThread); grid 0 = not possible.
+void coarse_pcg_shape(int64_t n, int rpt_min, int* grid, int* rows_per_block);
+
+// ---- coarse CG on one thread-block cluster (coarse_cluster.cu; box lattice at N = 1) ----
+// Forward half of the 27-point lattice stencil, slot k -> offset (dx, dy, dz): slot 0 the
+// diagonal, 1-4 the in-plane neighbours (1,0), (-1,1), (0,1), (1,1), 5-13 the plane above
+// with (dx, dy) in {-1,0,1}^2, dx fastest.  The other half is the mirror image: A is
+// symmetric, so entry (i, i - o) is stored as entry (i - o, i) in row i - o.
+__host__ __device__ constexpr int cc_dx(int k) {
+  return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? -1 : k <= 4 ? k - 3 : (k - 5) % 3 - 1;
+}
+__host__ __device__ constexpr int cc_dy(int k) { return k <= 1 ? 0 : k <= 4 ? 1 : (k - 5) / 3 - 1; }
+__host__ __device__ constexpr int cc_dz(int k) { return k <= 4 ? 0 : 1; }
+constexpr int kCcSlots = 14;
+struct CoarseCluster {
+  int nx, ny, nz;        // node lattice (boundary planes and rings included; they are Dirichlet)
+  int ctas;              // cluster size: interior planes 1 .. nz-2 split over the CTAs
+  int rmax;              // rows of the largest CTA (planes x nx x ny)
+  const float* val32;    // [14][n] stencil values (symmetrised), FP32, lattice numbering
+  const double* val64;   // [14][n] FP64
+  const float* invDf;    // Jacobi diagonal, 0 on Dirichlet nodes
+  const double* b;
+  double* x;
+  double rtol;
+  int maxit;
+  int degree;
+  double lmax;
+  unsigned* ctl;         // as CoarseCG::ctl ([2] status, [3] iterations, [4] sticky error)
+};
+// Cluster size, largest CTA and shared memory for an nx x ny x nz lattice; false if the
+// problem does not fit one cluster on this device (nothing changed then).
+bool coarse_cluster_plan(int nx, int ny, int nz, int* ctas, int* rmax, size_t* smem);
+bool coarse_cluster_launch(const CoarseCluster& a, size_t smem, cudaStream_t s, cudaError_t* err);
 
 // ---- batched Krylov (batched.cu): nb right-hand sides at leading dimension ld ----
 // Per right-hand side: scal[q * S_NSLOTS + slot] and stat[q * 4 + {0 active, 1 iterations,

@@ -649,101 +649,180 @@ __device__ __forceinline__ bool allreduce3(unsigned* ctl, unsigned& gen, unsigne
   c = C;
   return ok;
 }
-__device__ __forceinline__ void publish_rows(const CoarseCG& a, unsigned gen, const double* v, int rpt,
-                                             int64_t base) {
-  double* buf = a.xbuf[gen & 1u];
-  for (int q = 0; q < rpt; ++q) {
-    const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
-    if (g < a.n && g < base + a.rows_per_block) buf[g] = v[q];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicExch(&a.flag[blockIdx.x], gen);
-  }
+// ---- tagged-word exchange ----
+__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned long long w) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
-__device__ __forceinline__ void publish_rows_f(const CoarseCG& a, unsigned gen, const float* v, int rpt,
-                                               int64_t base) {
-  float* buf = a.xbufF[gen & 1u];
-  for (int q = 0; q < rpt; ++q) {
-    const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
-    if (g < a.n && g < base + a.rows_per_block) buf[g] = v[q];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicExch(&a.flag[blockIdx.x], gen);
-  }
+__device__ __forceinline__ void st_tagged2(unsigned long long* p, unsigned long long w0, unsigned long long w1) {
+  asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(w0), "l"(w1) : "memory");
 }
-__device__ __forceinline__ bool wait_neighbours(const CoarseCG& a, unsigned gen) {
-  const int lo = max(0, (int)blockIdx.x - a.halo);
-  const int hi = min((int)gridDim.x - 1, (int)blockIdx.x + a.halo);
-  int ok = 1;
-  for (int t = threadIdx.x; t <= hi - lo && ok; t += blockDim.x) {   // halos wider than a block too
-    const unsigned* f = &a.flag[lo + t];
-    if (*(volatile const unsigned*)f < gen) {
-      const uint64_t t0 = global_ns();
-      for (unsigned it = 1; *(volatile const unsigned*)f < gen; ++it) {
-        __nanosleep(20);
-        if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) {
-          atomicMax((int*)&a.ctl[4], (int)CS_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-  }
-  if ((int)threadIdx.x <= hi - lo) __threadfence();
-  return __syncthreads_and(ok) != 0;
+__device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long* p) {
+  unsigned long long w;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
 }
-template <int NS, int RPT>
-__device__ __forceinline__ void coarse_spmv(const CoarseCG& a, unsigned gen, int64_t base, double (&y)[RPT]) {
-  const double* v = a.xbuf[gen & 1u];
-  const int64_t n = a.n;
-  const int ns = NS > 0 ? NS : a.nslot;
+__device__ __forceinline__ void ld_tagged2(const unsigned long long* p, unsigned long long& w0,
+                                           unsigned long long& w1) {
+  asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(p) : "memory");
+}
+// Column index load that the compiler may not merge with an earlier one (keeps the reload
+// loop from holding all column indices in registers).
+__device__ __forceinline__ int ld_col(const int* p) {
+  int v;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+// One exchanged value: FP32 in one tagged word, FP64 as two (high and low halves, loaded
+// and stored together; each half carries the tag, so a torn pair is never accepted).
+template <typename V>
+struct Tagged;
+template <>
+struct Tagged<float> {
+  struct W {
+    unsigned long long w;
+  };
+  static __device__ __forceinline__ unsigned long long* buf(const CoarseCG& a, unsigned gx) {
+    return a.exf[gx & 1u];
+  }
+  static __device__ __forceinline__ void store(unsigned long long* b, int64_t g, unsigned tag, float v) {
+    st_tagged(b + g, ((unsigned long long)tag << 32) | __float_as_uint(v));
+  }
+  static __device__ __forceinline__ W load(const unsigned long long* b, int64_t g) { return {ld_tagged(b + g)}; }
+  static __device__ __forceinline__ bool ready(const W& w, unsigned tag) { return (unsigned)(w.w >> 32) == tag; }
+  static __device__ __forceinline__ float value(const W& w) { return __uint_as_float((unsigned)w.w); }
+  static __device__ __forceinline__ float coef(const CoarseCG& a, int64_t i) { return __ldg(&a.valf[i]); }
+};
+template <>
+struct Tagged<double> {
+  struct W {
+    unsigned long long hi, lo;
+  };
+  static __device__ __forceinline__ unsigned long long* buf(const CoarseCG& a, unsigned gx) {
+    return a.exd[gx & 1u];
+  }
+  static __device__ __forceinline__ void store(unsigned long long* b, int64_t g, unsigned tag, double v) {
+    const unsigned long long t = (unsigned long long)tag << 32;
+    st_tagged2(b + 2 * g, t | (unsigned)__double2hiint(v), t | (unsigned)__double2loint(v));
+  }
+  static __device__ __forceinline__ W load(const unsigned long long* b, int64_t g) {
+    W w;
+    ld_tagged2(b + 2 * g, w.hi, w.lo);
+    return w;
+  }
+  static __device__ __forceinline__ bool ready(const W& w, unsigned tag) {
+    return (unsigned)(w.hi >> 32) == tag && (unsigned)(w.lo >> 32) == tag;
+  }
+  static __device__ __forceinline__ double value(const W& w) {
+    return __hiloint2double((int)(unsigned)w.hi, (int)(unsigned)w.lo);
+  }
+  static __device__ __forceinline__ double coef(const CoarseCG& a, int64_t i) { return __ldg(&a.val[i]); }
+};
+
+// Publishes this block's rows under exchange gx.  No barrier first: every product ends with
+// a block barrier, so this block has finished reading the buffer it overwrites (two exchanges
+// ago), and a neighbour only moves on to it after reading values this block published after
+// that barrier.
+template <typename V, int RPT>
+__device__ __forceinline__ void publish_tagged(const CoarseCG& a, unsigned gx, const V (&v)[RPT], int64_t base) {
+  unsigned long long* b = Tagged<V>::buf(a, gx);
+  const unsigned tag = a.gen0 + gx;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
-    double acc = 0.0;
-    if (g < n && g < base + a.rows_per_block) {
-      if (NS > 0) {
-#pragma unroll
-        for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
-          acc += __ldg(&a.val[k * n + g]) * __ldcg(&v[__ldg(&a.col[k * n + g])]);
-      } else {
-        for (int k = 0; k < ns; ++k) acc += __ldg(&a.val[k * n + g]) * __ldcg(&v[__ldg(&a.col[k * n + g])]);
-      }
-    }
-    y[q] = acc;
+    if (g < a.n && g < base + a.rows_per_block) Tagged<V>::store(b, g, tag, v[q]);
   }
 }
 
-template <int NS, int RPT>
-__device__ __forceinline__ void coarse_spmv_f(const CoarseCG& a, unsigned gen, int64_t base, float (&y)[RPT]) {
-  const float* v = a.xbufF[gen & 1u];
+// y = A v on this block's rows, v read from exchange gx: all column indices first, then all
+// words, then every word whose tag is not there yet reloaded in the next round (one L2 round
+// trip per round).  Ends with a block barrier; false in every thread if a wait ran out.
+template <typename V, int NS, int RPT>
+__device__ __forceinline__ bool coarse_spmv_tagged(const CoarseCG& a, unsigned gx, int64_t base, V (&y)[RPT]) {
+  using TW = typename Tagged<V>::W;
+  const unsigned long long* b = Tagged<V>::buf(a, gx);
+  const unsigned tag = a.gen0 + gx;
   const int64_t n = a.n;
-  const int ns = NS > 0 ? NS : a.nslot;
+  bool ok = true;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
-    float acc = 0.f;
+    V acc = V(0);
     if (g < n && g < base + a.rows_per_block) {
-      if (NS > 0) {
+      if constexpr (NS > 0) {
+        // FP64 words come in pairs: a third of the slots at a time keeps them in registers
+        constexpr int CH = sizeof(V) == 4 ? NS : (NS + 2) / 3;
+        static_assert(CH <= 32, "miss mask is 32 bits");
 #pragma unroll
-        for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
-          acc = fmaf(__ldg(&a.valf[k * n + g]), __ldcg(&v[__ldg(&a.col[k * n + g])]), acc);
+        for (int k0 = 0; k0 < NS; k0 += CH) {
+          TW w[CH];
+          {
+            int c[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k)
+              if (k0 + k < NS) c[k] = ld_col(&a.col[(k0 + k) * n + g]);
+#pragma unroll
+            for (int k = 0; k < CH; ++k)
+              if (k0 + k < NS) w[k] = Tagged<V>::load(b, c[k]);
+          }
+          unsigned miss = 0;
+#pragma unroll
+          for (int k = 0; k < CH; ++k)
+            if (k0 + k < NS && !Tagged<V>::ready(w[k], tag)) miss |= 1u << k;
+          if (miss && ok) {
+            const uint64_t t0 = global_ns();
+            for (unsigned it = 1; miss; ++it) {
+              if (it > 16) __nanosleep(32);
+              int c[CH];
+#pragma unroll
+              for (int k = 0; k < CH; ++k)
+                if (miss >> k & 1u) c[k] = ld_col(&a.col[(k0 + k) * n + g]);
+#pragma unroll
+              for (int k = 0; k < CH; ++k)
+                if (miss >> k & 1u) w[k] = Tagged<V>::load(b, c[k]);
+              unsigned still = 0;
+#pragma unroll
+              for (int k = 0; k < CH; ++k)
+                if ((miss >> k & 1u) && !Tagged<V>::ready(w[k], tag)) still |= 1u << k;
+              miss = still;
+              if (miss && (it & 63u) == 0 && global_ns() - t0 > kWaitNs) {
+                atomicMax((int*)&a.ctl[4], (int)CS_TIMEOUT);
+                ok = false;
+                break;
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < CH; ++k)
+            if (k0 + k < NS) acc = fma(Tagged<V>::coef(a, (k0 + k) * n + g), Tagged<V>::value(w[k]), acc);
+        }
       } else {
-        for (int k = 0; k < ns; ++k) acc = fmaf(__ldg(&a.valf[k * n + g]), __ldcg(&v[__ldg(&a.col[k * n + g])]), acc);
+        for (int k = 0; k < a.nslot && ok; ++k) {
+          const int c = __ldg(&a.col[k * n + g]);
+          TW w = Tagged<V>::load(b, c);
+          const uint64_t t0 = global_ns();
+          for (unsigned it = 1; !Tagged<V>::ready(w, tag); ++it) {
+            if (it > 16) __nanosleep(32);
+            w = Tagged<V>::load(b, c);
+            if ((it & 63u) == 0 && !Tagged<V>::ready(w, tag) && global_ns() - t0 > kWaitNs) {
+              atomicMax((int*)&a.ctl[4], (int)CS_TIMEOUT);
+              ok = false;
+              break;
+            }
+          }
+          acc = fma(Tagged<V>::coef(a, k * n + g), Tagged<V>::value(w), acc);
+        }
       }
     }
     y[q] = acc;
   }
+  return __syncthreads_and(ok) != 0;
 }
 
 // Persistent preconditioned CG on the assembled coarse operator.  The preconditioner is one
 // application of Algorithm 2 (4th kind, beta = 1) of degree m from a zero guess, Jacobi-
 // scaled -- SPD for every m, and for m = 1 simply Jacobi.  Per CG iteration: m products,
-// each needing only the neighbouring blocks' rows (flag exchange), and two grid-wide
+// each reading the neighbouring blocks' rows through tagged words (no flags, no fences), and two grid-wide
 // reductions (reduce-then-release barrier).  Owned rows live in registers.
 template <int NS, int RPT, bool PF32>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
@@ -763,6 +842,10 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     x[q] = p[q] = 0.0;
   }
   const double c0 = 4.0 / (3.0 * a.lmax);
+  __shared__ CoarseCoef coef;
+  __shared__ double s_alpha, s_beta;
+  coarse_coef_fill(coef, a.degree, a.lmax);
+  __syncthreads();
   // z = M r in FP32 (same recurrence on FP32 copies)
   auto precond_f = [&]() -> bool {
     float df[RPT], rf[RPT], zf[RPT], yf[RPT], sf[RPT];
@@ -778,11 +861,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     for (int i = 1; i < a.degree; ++i) {
 #pragma unroll
       for (int q = 0; q < RPT; ++q) zf[q] += df[q];
-      publish_rows_f(a, ++gx, df, RPT, base);
-      if (!wait_neighbours(a, gx)) return false;
-      coarse_spmv_f<NS, RPT>(a, gx, base, yf);
-      const float c1 = (float)((2.0 * i - 1.0) / (2.0 * i + 3.0));
-      const float c2 = (float)((8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax));
+      publish_tagged<float, RPT>(a, ++gx, df, base);
+      if (!coarse_spmv_tagged<float, NS, RPT>(a, gx, base, yf)) return false;
+      const float c1 = coef.c1f[i], c2 = coef.c2f[i];
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         rf[q] -= yf[q];
@@ -795,29 +876,31 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
   };
   // z = M r: Algorithm 2 from a zero guess; returns false on a failed exchange
   auto precond = [&]() -> bool {
-    if (PF32) return precond_f();
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      rp[q] = r[q];
-      d[q] = c0 * S[q] * rp[q];
-      z[q] = 0.0;
-    }
-    for (int i = 1; i < a.degree; ++i) {
-#pragma unroll
-      for (int q = 0; q < RPT; ++q) z[q] += d[q];
-      publish_rows(a, ++gx, d, RPT, base);
-      if (!wait_neighbours(a, gx)) return false;
-      coarse_spmv<NS, RPT>(a, gx, base, y);
-      const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0), c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * a.lmax);
+    if constexpr (PF32) {
+      return precond_f();
+    } else {
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
-        rp[q] -= y[q];
-        d[q] = c1 * d[q] + c2 * S[q] * rp[q];
+        rp[q] = r[q];
+        d[q] = c0 * S[q] * rp[q];
+        z[q] = 0.0;
       }
-    }
+      for (int i = 1; i < a.degree; ++i) {
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) z[q] += d[q];
-    return true;
+        for (int q = 0; q < RPT; ++q) z[q] += d[q];
+        publish_tagged<double, RPT>(a, ++gx, d, base);
+        if (!coarse_spmv_tagged<double, NS, RPT>(a, gx, base, y)) return false;
+        const double c1 = coef.c1[i], c2 = coef.c2[i];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          rp[q] -= y[q];
+          d[q] = c1 * d[q] + c2 * S[q] * rp[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) z[q] += d[q];
+      return true;
+    }
   };
   auto finish = [&](int status, int it) {
 #pragma unroll
@@ -847,10 +930,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     return;
   }
   const double tol2 = a.rtol * a.rtol * bb;
-  publish_rows(a, ++gx, p, RPT, base);
+  publish_tagged<double, RPT>(a, ++gx, p, base);
   for (int it = 1; it <= a.maxit; ++it) {
-    if (!wait_neighbours(a, gx)) return;
-    coarse_spmv<NS, RPT>(a, gx, base, y);
+    if (!coarse_spmv_tagged<double, NS, RPT>(a, gx, base, y)) return;
     double pq = 0.0, z1 = 0.0, z2 = 0.0;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) pq += p[q] * y[q];
@@ -861,7 +943,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
       finish(CS_BREAKDOWN, it);
       return;
     }
-    const double alpha = gam / pq_tot;
+    const double alpha = block_div(&s_alpha, gam, pq_tot);
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       ro[q] = r[q];
@@ -890,11 +972,11 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_pcg(CoarseCG a) {
     }
     // Fletcher-Reeves for the exact (symmetric) FP64 preconditioner; Polak-Ribiere
     // (z_new, r_new - r_old) / (z_old, r_old) for the FP32 one
-    const double beta = PF32 ? (gam_new - z1) / gam : gam_new / gam;
+    const double beta = block_div(&s_beta, PF32 ? gam_new - z1 : gam_new, gam);
     gam = gam_new;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) p[q] = fma(beta, p[q], z[q]);
-    publish_rows(a, ++gx, p, RPT, base);
+    publish_tagged<double, RPT>(a, ++gx, p, base);
   }
   finish(CS_NOTCONV, a.maxit);
 }
@@ -909,7 +991,7 @@ static const void* coarse_kernel(int rpt) {
   }
 }
 
-void coarse_pcg_shape(int64_t n, int* grid, int* rows_per_block) {
+void coarse_pcg_shape(int64_t n, int rpt_min, int* grid, int* rows_per_block) {
   static int sms = -1;
   if (sms < 0) {
     int dev = 0;
@@ -918,6 +1000,7 @@ void coarse_pcg_shape(int64_t n, int* grid, int* rows_per_block) {
   }
   const int64_t per_block_min = (n + sms - 1) / sms;
   int rpt = 1;
+  while (rpt < rpt_min && rpt < kCoarseMaxRowsPerThread) rpt *= 2;
   while ((int64_t)rpt * kCoarseThreads < per_block_min && rpt < kCoarseMaxRowsPerThread) rpt *= 2;
   const int64_t rb = (int64_t)rpt * kCoarseThreads;
   const int64_t g = (n + rb - 1) / rb;
