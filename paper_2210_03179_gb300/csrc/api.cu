@@ -2307,16 +2307,33 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
       if (relres) *relres = 0.0;
       return CHEBMG_OK;
     }
-    int rc = vcycle_top(c, r, z);
+    // Mixed form: the V-cycle reads an FP32 copy of r, written by the x/r update, and its FP32
+    // output z32 feeds the dots and the p update directly (no FP64 copy of z).  The flexible
+    // (Polak-Ribiere) beta uses r_new - r_old = -alpha A p, so no copy of r_old is kept.
+    (void)ro;
+    const bool mixed = c->fp32 && c->L.size() > 1;
+    float* r32 = mixed ? vec<float>(L, VB) : nullptr;
+    float* z32 = mixed ? vec<float>(L, VX) : nullptr;
+    auto precondition = [&](bool r32_ready) -> int {
+      if (!mixed) return vcycle_top(c, r, z);
+      if (!r32_ready) cast<double, float>(n, r, r32, c->s);
+      return vcycle_level<float>(c, 0, r32, z32);
+    };
+    int rc = precondition(false);
     if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
-    CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
-    dot2(n, z, r, nullptr, nullptr, S_ZR, -1, POST_SET_RZ_FROM_ZR, c->partial, c->scal, c->s);
+    if (mixed) {
+      update_p_from<float>(n, z32, p, c->scal, true, c->s);
+      dot_zr_zq<float>(n, z32, r, nullptr, POST_SET_RZ_FROM_ZR, c->partial, c->scal, c->s);
+    } else {
+      update_p_from<double>(n, z, p, c->scal, true, c->s);
+      dot_zr_zq<double>(n, z, r, nullptr, POST_SET_RZ_FROM_ZR, c->partial, c->scal, c->s);
+    }
     double rel = 1.0;
     for (int it = 1; it <= maxit; ++it) {
       zero<double>(c, q, n);
       apply_into<double>(c, 0, p, q);
       dot2(n, p, q, nullptr, nullptr, S_PQ, -1, POST_ALPHA, c->partial, c->scal, c->s);
-      fcg_update_xr(n, u, r, ro, p, q, c->partial, c->scal, c->s);
+      fcg_update_xr32(n, u, r, r32, p, q, c->partial, c->scal, c->s);
       read_scal(c);
       const double pq = c->hscal[S_PQ], rr = c->hscal[S_RR];
       const int crc = coarse_sticky_error(c);
@@ -2336,10 +2353,15 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
       if (iters) *iters = it;
       if (relres) *relres = rel;
       if (rel <= rtol) return CHEBMG_OK;
-      rc = vcycle_top(c, r, z);
+      rc = precondition(true);
       if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
-      dot2(n, z, r, z, ro, S_ZR, S_ZRO, POST_BETA_FLEX, c->partial, c->scal, c->s);
-      update_p(n, z, p, c->scal, c->s);
+      if (mixed) {
+        dot_zr_zq<float>(n, z32, r, q, POST_BETA_FLEX_Q, c->partial, c->scal, c->s);
+        update_p_from<float>(n, z32, p, c->scal, false, c->s);
+      } else {
+        dot_zr_zq<double>(n, z, r, q, POST_BETA_FLEX_Q, c->partial, c->scal, c->s);
+        update_p_from<double>(n, z, p, c->scal, false, c->s);
+      }
       check_launch();
     }
     g_last_error = "FCG did not reach the tolerance";

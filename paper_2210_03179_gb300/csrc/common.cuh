@@ -24,9 +24,10 @@ enum Slot {
   S_BETA,
   S_T0,          // scratch
   S_T1,
+  S_ZQ,          // (z_new, q) with q = A p of the same iteration
   S_NSLOTS
 };
-enum PostOp { POST_NONE = 0, POST_ALPHA, POST_BETA_FLEX, POST_BETA_CG, POST_SET_RZ_FROM_ZR };
+enum PostOp { POST_NONE = 0, POST_ALPHA, POST_BETA_FLEX, POST_BETA_CG, POST_SET_RZ_FROM_ZR, POST_BETA_FLEX_Q };
 
 constexpr int kRedBlocks = 592;    // 152 SMs x 4: partial sums per reduction pass
 
@@ -137,6 +138,17 @@ void fcg_update_xr(int64_t n, double* x, double* r, double* rold, const double* 
                    const double* q, double* partial, double* scal, cudaStream_t s);
 // p = z + scal[BETA] p
 void update_p(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s);
+// The flexible CG loop's fused forms.  FCG: x += alpha p; r -= alpha q; partial (r, r) ->
+// scal[RR]; r32 (if not NULL) = FP32 copy of the new r (the V-cycle's right-hand side).
+void fcg_update_xr32(int64_t n, double* x, double* r, float* r32, const double* p, const double* q,
+                     double* partial, double* scal, cudaStream_t s);
+// scal[ZR] = (z, r), scal[ZQ] = (z, q), then post (z in FP32 or FP64)
+template <typename Tz>
+void dot_zr_zq(int64_t n, const Tz* z, const double* r, const double* q, int post, double* partial, double* scal,
+               cudaStream_t s);
+// p = z + scal[BETA] p, or p = z (first)
+template <typename Tz>
+void update_p_from(int64_t n, const Tz* z, double* p, const double* scal, bool first, cudaStream_t s);
 // CG (coarse): x += alpha p; r -= alpha q; z = S r; partials (r, r) and (r, z)
 void cg_update(int64_t n, double* x, double* r, double* z, const double* p, const double* q,
                const double* invD, double* partial, double* scal, cudaStream_t s);

@@ -424,6 +424,10 @@ __device__ void apply_post(int post, double* scal) {
       scal[S_RZ] = scal[S_ZR];
       break;
     case POST_SET_RZ_FROM_ZR: scal[S_RZ] = scal[S_ZR]; break;
+    case POST_BETA_FLEX_Q:   // the same Polak-Ribiere beta with r_new - r_old = -alpha q
+      scal[S_BETA] = -scal[S_ALPHA] * scal[S_ZQ] / scal[S_RZ];
+      scal[S_RZ] = scal[S_ZR];
+      break;
     default: break;
   }
 }
@@ -478,6 +482,78 @@ void fcg_update_xr(int64_t n, double* x, double* r, double* rold, const double* 
   k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, -1, POST_NONE, scal);
   g_launches.fetch_add(2, std::memory_order_relaxed);
 }
+
+__global__ void __launch_bounds__(kRedThreads)
+k_fcg_update_xr32(int64_t n, double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
+                  const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ partial,
+                  const double* __restrict__ scal) {
+  const double alpha = scal[S_ALPHA];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    x[g] += alpha * p[g];
+    const double rn = r[g] - alpha * q[g];
+    r[g] = rn;
+    if (r32) r32[g] = (float)rn;
+    s0 += rn * rn;
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s0;
+    partial[kRedBlocks + blockIdx.x] = 0.0;
+  }
+}
+
+void fcg_update_xr32(int64_t n, double* x, double* r, float* r32, const double* p, const double* q,
+                     double* partial, double* scal, cudaStream_t s) {
+  k_fcg_update_xr32<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, r32, p, q, partial, scal);
+  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, -1, POST_NONE, scal);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+template <typename Tz>
+__global__ void __launch_bounds__(kRedThreads)
+k_dot_zr_zq(int64_t n, const Tz* __restrict__ z, const double* __restrict__ r, const double* __restrict__ q,
+            double* __restrict__ partial) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double zv = (double)z[g];
+    s0 += zv * r[g];
+    if (q) s1 += zv * q[g];
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s0;
+    partial[kRedBlocks + blockIdx.x] = s1;
+  }
+}
+
+template <typename Tz>
+void dot_zr_zq(int64_t n, const Tz* z, const double* r, const double* q, int post, double* partial, double* scal,
+               cudaStream_t s) {
+  k_dot_zr_zq<Tz><<<kRedBlocks, kRedThreads, 0, s>>>(n, z, r, q, partial);
+  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_ZR, q ? S_ZQ : -1, post, scal);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+template void dot_zr_zq<float>(int64_t, const float*, const double*, const double*, int, double*, double*,
+                               cudaStream_t);
+template void dot_zr_zq<double>(int64_t, const double*, const double*, const double*, int, double*, double*,
+                                cudaStream_t);
+
+template <typename Tz>
+__global__ void k_update_p_from(int64_t n, const Tz* __restrict__ z, double* __restrict__ p,
+                                const double* __restrict__ scal, int first) {
+  const double beta = first ? 0.0 : scal[S_BETA];
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    p[g] = first ? (double)z[g] : (double)z[g] + beta * p[g];
+}
+
+template <typename Tz>
+void update_p_from(int64_t n, const Tz* z, double* p, const double* scal, bool first, cudaStream_t s) {
+  k_update_p_from<Tz><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, z, p, scal, first ? 1 : 0);
+  count();
+}
+template void update_p_from<float>(int64_t, const float*, double*, const double*, bool, cudaStream_t);
+template void update_p_from<double>(int64_t, const double*, double*, const double*, bool, cudaStream_t);
 
 __global__ void k_update_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                            const double* __restrict__ scal) {
