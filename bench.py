@@ -482,12 +482,15 @@ def main():
                          "range 'smooth' and exit")
     ap.add_argument("--tile", type=int, default=None,
                     help="profiling runs only: force this order-7 kernel variant on the fine level")
+    ap.add_argument("--profile-outer", choices=["fp64", "f32x2"], default=None,
+                    help="apply only the outer operator (FP64 or FP32 pairs) twice, the second inside an "
+                         "NVTX range 'outer' (for ncu)")
     ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
                     help="set up, warm up, run one solve inside the NVTX range 'solve' and exit "
                          "(for ncu --nvtx-include solve/)")
     args = ap.parse_args()
 
-    if args.profile_solve or args.profile_smoother:
+    if args.profile_solve or args.profile_smoother or args.profile_outer:
         NE = args.ne
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -579,6 +582,22 @@ def main():
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile_smoother": args.profile_smoother,
                           "elements_per_block": cm.chebmg_tile_choice(s.ctx, 0, dt)}))
+        s32.close()
+        s64.close()
+        return 0
+
+    if args.profile_outer:
+        if args.profile_outer == "f32x2":
+            cm.chebmg_set_outer_operator(s32.ctx, cm.CHEBMG_OUTER_F32X2)
+        xo = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+        yo = torch.zeros_like(xo)
+        cm.chebmg_apply_outer(s32.ctx, xo, yo)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("outer")
+        cm.chebmg_apply_outer(s32.ctx, xo, yo)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_outer": args.profile_outer}))
         s32.close()
         s64.close()
         return 0
@@ -711,6 +730,21 @@ def main():
 
     coarse = {"mixed": coarse_time(s32), "fp64": coarse_time(s64)}
 
+    # ---- opt-in: the outer product in FP64-class arithmetic on FP32 pairs ----
+    xo = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    yo = torch.zeros_like(xo)
+    t_op64, _ = timed(lambda: cm.chebmg_apply_outer(s32.ctx, xo, yo), 5)
+    cm.chebmg_set_outer_operator(s32.ctx, cm.CHEBMG_OUTER_F32X2)
+    cm.chebmg_apply_outer(s32.ctx, xo, yo)
+    t_opx2, _ = timed(lambda: cm.chebmg_apply_outer(s32.ctx, xo, yo), 5)
+    solve(s32)
+    t32x2, it32x2 = timed(lambda: solve(s32), args.steps)
+    cm.chebmg_set_outer_operator(s32.ctx, cm.CHEBMG_OUTER_FP64)
+    outer = {"fp64_us": t_op64 * 1e6, "f32x2_us": t_opx2 * 1e6,
+             "note": "opt-in CHEBMG_OUTER_F32X2: the outer product q = A p in FP64-class arithmetic on "
+                     "FP32 pairs (about 48 significant bits); the headline uses FP64; each time includes "
+                     "the zeroing of q and a host synchronisation"}
+
     world_n = world
     value = job_throughput(world_n, n, t32)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_n, "steps": args.steps,
@@ -719,8 +753,9 @@ def main():
             "config": config({"parallelism": f"replicas x{world_n}",
                               "ax8_elements_per_block": {"fp32": cm.chebmg_tile_choice(s32.ctx, 0, 1),
                                                          "fp64": cm.chebmg_tile_choice(s64.ctx, 0, 0)}}),
-            "time_to_1e8_s": {"mixed": t32, "fp64": t64},
-            "iterations": {"mixed": it32, "fp64": it64},
+            "time_to_1e8_s": {"mixed": t32, "fp64": t64, "mixed_f32x2_outer": t32x2},
+            "iterations": {"mixed": it32, "fp64": it64, "mixed_f32x2_outer": it32x2},
+            "outer_operator": outer,
             "speedup_mixed_vs_fp64": t64 / t32,
             "smoother_gdofs": {"fp32": n / step32 / 1e9, "fp64": n / step64 / 1e9},
             "e2e": {"value": job_throughput(world_n, n, te2e), "unit": UNIT, "h2d_bytes_per_step": 8 * n,

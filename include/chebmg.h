@@ -154,6 +154,22 @@ enum { CHEBMG_COARSE_HOST = 0, CHEBMG_COARSE_GRID = 1, CHEBMG_COARSE_CLUSTER = 2
 int chebmg_coarse_shape(const chebmg_ctx* ctx, int* kernel, int* blocks, int* rows_per_block);
 /* Overrides the coarse kernel (GRID or CLUSTER); EINVAL where it does not apply. */
 int chebmg_set_coarse_kernel(chebmg_ctx* ctx, int kernel);
+
+/* Arithmetic of the outer Krylov product q = A p on the finest level (chebmg_pcg_solve):
+ *   CHEBMG_OUTER_FP64   FP64 (default);
+ *   CHEBMG_OUTER_F32X2  the order-7 operator in FP64-class arithmetic on pairs of FP32 values
+ *                       (value = hi + lo, about 48 significant bits; additions carry both
+ *                       rounding errors, products use the fused-multiply-add error term), the
+ *                       geometric factors kept as such pairs (8 bytes per value).  Relative
+ *                       error near 1e-14 per application; FP32 exponent range (|values| well
+ *                       inside 1e-30 .. 1e30).  GB300 executes FP32 at a large multiple of its
+ *                       FP64 rate.  Opt-in: the first call converts the factors and times the
+ *                       kernel variants.  EINVAL unless the finest level is SEM of order 7.
+ * Everything else in the solve (residual update, dot products, preconditioner) is unchanged. */
+enum { CHEBMG_OUTER_FP64 = 0, CHEBMG_OUTER_F32X2 = 1 };
+int chebmg_set_outer_operator(chebmg_ctx* ctx, int kind);
+/* y = A x on the finest level with the context's outer operator (FP64 device vectors). */
+int chebmg_apply_outer(chebmg_ctx* ctx, const double* x, double* y);
 int chebmg_set_coarse_degree(chebmg_ctx* ctx, int degree);
 int chebmg_set_tile_choice(chebmg_ctx* ctx, int level, int dtype, int variant);
 

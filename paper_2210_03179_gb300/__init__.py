@@ -41,6 +41,8 @@ CHEBMG_F32 = 1
 CHEBMG_COARSE_HOST = 0
 CHEBMG_COARSE_GRID = 1
 CHEBMG_COARSE_CLUSTER = 2
+CHEBMG_OUTER_FP64 = 0
+CHEBMG_OUTER_F32X2 = 1
 
 KINDS = {"1st": CHEBMG_CHEB_1ST, "4th": CHEBMG_CHEB_4TH, "opt4th": CHEBMG_CHEB_4TH_OPT}
 SIDED = {"symmetric": CHEBMG_SYMMETRIC, "one-sided": CHEBMG_ONE_SIDED}
@@ -91,6 +93,8 @@ _SIGNATURES = {
     "chebmg_coarse_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
     "chebmg_coarse_shape": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "chebmg_set_coarse_kernel": (c_int, [c_void_p, c_int]),
+    "chebmg_set_outer_operator": (c_int, [c_void_p, c_int]),
+    "chebmg_apply_outer": (c_int, [c_void_p, c_void_p, c_void_p]),
     "chebmg_set_coarse_degree": (c_int, [c_void_p, c_int]),
     "chebmg_apply_A": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "chebmg_inv_diagonal": (c_int, [c_void_p, c_int, c_int, c_void_p]),
@@ -285,6 +289,16 @@ def chebmg_coarse_shape(ctx):
 
 def chebmg_set_coarse_kernel(ctx, kernel: int) -> None:
     _check(lib().chebmg_set_coarse_kernel(ctx, int(kernel)), "chebmg_set_coarse_kernel")
+
+
+def chebmg_set_outer_operator(ctx, kind: int) -> None:
+    _check(lib().chebmg_set_outer_operator(ctx, int(kind)), "chebmg_set_outer_operator")
+
+
+def chebmg_apply_outer(ctx, x, y) -> None:
+    n = chebmg_level_size(ctx, 0)
+    _check(lib().chebmg_apply_outer(ctx, _ptr(x, n, CHEBMG_F64, "x"), _ptr(y, n, CHEBMG_F64, "y")),
+           "chebmg_apply_outer")
 
 
 def chebmg_set_coarse_degree(ctx, degree):

@@ -136,6 +136,10 @@ struct chebmg_ctx {
   float* coarse_invDf = nullptr;
   bool coarse_pf32 = false;     // coarse CG preconditioner in FP32
   int coarse_rows_per_block = 0;
+  // the outer Krylov product of the finest level: 0 FP64, 1 FP64-class arithmetic on FP32 pairs
+  int outer_op = 0;
+  void* G_x2 = nullptr;         // level-0 geometric factors as FP32 pairs
+  int eb_x2 = 2;                // variant of the pair-arithmetic kernel (autotuned)
   // coarse CG on one thread-block cluster (box lattice at N = 1, FP32 preconditioner)
   int coarse_kernel = 0;        // 0 grid-wide persistent kernel, 1 cluster kernel
   float* cc_val32 = nullptr;    // [14][n] symmetric stencil layout
@@ -562,6 +566,18 @@ int coarse(chebmg_ctx* c, const T* b, T* x) {
     check_launch();
     return rc;
   }
+}
+
+// q = A p on the finest level for the outer Krylov method (q zero on entry): FP64, or the
+// order-7 operator in FP64-class FP32-pair arithmetic when the context selected it.
+void apply_outer(chebmg_ctx* c, const double* p, double* q) {
+  Level& L = c->L[0];
+  if (c->outer_op == 1 && c->G_x2) {
+    sem_ax8_x2(L.E, L.gid, L.lat, c->G_x2, p, q, c->dstat, c->eb_x2, c->s);
+    check_launch();
+    return;
+  }
+  apply_into<double>(c, 0, p, q);
 }
 
 // z = V-cycle(b) from level j (Eq. 2.2), in precision T.
@@ -2177,6 +2193,65 @@ int chebmg_launch_count(const chebmg_ctx* c, int64_t* count) {
   return CHEBMG_OK;
 }
 
+int chebmg_set_outer_operator(chebmg_ctx* c, int kind) {
+  return guard([&]() -> int {
+    enter(c);
+    if (kind == CHEBMG_OUTER_FP64) {
+      c->outer_op = 0;
+      return CHEBMG_OK;
+    }
+    if (kind != CHEBMG_OUTER_F32X2) throw Error(CHEBMG_EINVAL, "bad outer operator kind");
+    Level& L = c->L[0];
+    if (L.type != TYPE_SEM || L.Q != 8) throw Error(CHEBMG_EINVAL, "FP32-pair operator needs an order-7 finest level");
+    if (!c->G_x2) {
+      c->G_x2 = dalloc<double>(c, L.E * 6 * 512);   // 8 bytes per value, like FP64
+      sem_to_x2(L.E * 6 * 512, static_cast<const double*>(L.G[CHEBMG_F64]), c->G_x2, c->s);
+      check_launch();
+      // variant: 1, 2 or 4 elements per block (box lattice ids where available), timed
+      double* x = vec<double>(L, VB);
+      double* y = vec<double>(L, VY);
+      splitmix_fill(L.n, 11ull, static_cast<const double*>(L.invD[CHEBMG_F64]), x, c->s);
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int eb : {1, 2, 4}) {
+        const int v = eb + (L.boxed ? 100 : 0);
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          CK(cudaEventRecord(e0, c->s));
+          sem_ax8_x2(L.E, L.gid, L.lat, c->G_x2, x, y, c->dstat, v, c->s);
+          CK(cudaEventRecord(e1, c->s));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          t_min = std::min(t_min, ms);
+        }
+        if (t_min < best) {
+          best = t_min;
+          c->eb_x2 = v;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      check_launch();
+    }
+    c->outer_op = 1;
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_apply_outer(chebmg_ctx* c, const double* x, double* y) {
+  return guard([&]() -> int {
+    enter(c);
+    if (!x || !y) throw Error(CHEBMG_EINVAL, "NULL vector");
+    zero<double>(c, y, c->L[0].n);
+    apply_outer(c, x, y);
+    CK(cudaStreamSynchronize(c->s));
+    return CHEBMG_OK;
+  });
+}
+
 int chebmg_apply_A(chebmg_ctx* c, int level, int dtype, const void* x, void* y) {
   return guard([&]() -> int {
     enter(c);
@@ -2331,7 +2406,7 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
     double rel = 1.0;
     for (int it = 1; it <= maxit; ++it) {
       zero<double>(c, q, n);
-      apply_into<double>(c, 0, p, q);
+      apply_outer(c, p, q);
       dot2(n, p, q, nullptr, nullptr, S_PQ, -1, POST_ALPHA, c->partial, c->scal, c->s);
       fcg_update_xr32(n, u, r, r32, p, q, c->partial, c->scal, c->s);
       read_scal(c);
