@@ -1,7 +1,7 @@
 // The order-7 element operator in FP64-class arithmetic on FP32 pairs (f32x2.cuh), for the
 // outer Krylov product of the mixed form.  GB300 executes FP32 at a large multiple of its FP64
 // rate, and the FP64 operator runs at that FP64 roof; the same operator with every
-// multiply-add on FP32 pairs (about 48 significant bits, accurate additions) costs about ten
+// multiply-add on FP32 pairs (about 48 significant bits) costs about ten
 // FP32 operations per FP64 one and runs faster, with errors near 1e-14 relative.
 //
 // Same structure as k_sem_ax8 (Sec. 1, Eq. 1.3): one element per 64 threads, line passes
@@ -43,20 +43,6 @@ __device__ __forceinline__ void line8_x2(const f32x2 (&u)[8], f32x2 (&o)[8]) {
     o[i] = x2_add(se, so);
     o[7 - i] = x2_sub(so, se);
   }
-}
-
-__device__ __forceinline__ void ld_row_x2(const f32x2* p, f32x2 (&v)[8]) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float4 a = reinterpret_cast<const float4*>(p)[q];
-    v[2 * q] = {a.x, a.y};
-    v[2 * q + 1] = {a.z, a.w};
-  }
-}
-__device__ __forceinline__ void st_row_x2(f32x2* p, const f32x2 (&v)[8]) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    reinterpret_cast<float4*>(p)[q] = make_float4(v[2 * q].hi, v[2 * q].lo, v[2 * q + 1].hi, v[2 * q + 1].lo);
 }
 
 template <int EB, bool IMPLICIT>
@@ -105,16 +91,19 @@ k_sem_ax8_x2(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const f32
   f32x2 ut[8];
   line8_x2<0>(col, ut);
   __syncthreads();
-  {
+  // r (thread (j = a, k = b) owns the row along i) and s (thread (i = a, k = b) owns the line
+  // along j) in one loop: the pair arithmetic is long, and one copy of the pass keeps the
+  // kernel's code within the instruction cache
+#pragma unroll 1
+  for (int d = 0; d < 2; ++d) {
+    const int base = d == 0 ? b * kP + a * kR : b * kP + a, stride = d == 0 ? 1 : kR;
     f32x2 v[8], o[8];
-    ld_row_x2(su + b * kP + a * kR, v);   // r: thread (j = a, k = b) owns the row along i
-    line8_x2<0>(v, o);
-    st_row_x2(sr + b * kP + a * kR, o);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = su[b * kP + j * kR + a];   // s: thread (i = a, k = b)
+    for (int j = 0; j < 8; ++j) v[j] = su[base + j * stride];
     line8_x2<0>(v, o);
+    f32x2* dst = d == 0 ? sr : ss;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) ss[b * kP + j * kR + a] = o[j];
+    for (int j = 0; j < 8; ++j) dst[base + j * stride] = o[j];
   }
   bool ok = false;
   for (uint32_t it = 0; it < kWaitLimit; ++it)
@@ -144,22 +133,20 @@ k_sem_ax8_x2(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const f32
   f32x2 yt[8];
   line8_x2<1>(wt, yt);
   __syncthreads();
-  {
-    f32x2 v[8], o[8];
-    ld_row_x2(sr + b * kP + a * kR, v);
-    line8_x2<1>(v, o);
-    st_row_x2(su + b * kP + a * kR, o);
-  }
-  __syncthreads();
-  {
+  // transposed r into su, then transposed s added to it (the s lines cross the r rows that
+  // other threads wrote: a barrier in between)
+#pragma unroll 1
+  for (int d = 0; d < 2; ++d) {
+    const int base = d == 0 ? b * kP + a * kR : b * kP + a, stride = d == 0 ? 1 : kR;
+    const f32x2* src = d == 0 ? sr : ss;
     f32x2 v[8], o[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = ss[b * kP + j * kR + a];
+    for (int j = 0; j < 8; ++j) v[j] = src[base + j * stride];
     line8_x2<1>(v, o);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) su[b * kP + j * kR + a] = x2_add(su[b * kP + j * kR + a], o[j]);
+    for (int j = 0; j < 8; ++j) su[base + j * stride] = d == 0 ? o[j] : x2_add(su[base + j * stride], o[j]);
+    __syncthreads();
   }
-  __syncthreads();
   if (valid) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
