@@ -7,6 +7,8 @@
   FP64 operator.
 * E = 16^3, N = 7 -> 3 -> 1, optimized 4th kind, one-sided (4,0): the oracle solves the
   whole problem and the iteration counts must agree within one.
+* The opt-in FP32-pair outer product at E = 32^3: sampled parity at the FP64 bar and a full
+  mixed solve to a true (FP64) 1e-8 residual within one iteration of the FP64 outer product.
 """
 import numpy as np
 import pytest
@@ -67,6 +69,12 @@ def test_sampled_operator_parity_32cubed(big):
     y = empty(n)
     cm.chebmg_apply_A(s.ctx, 0, cm.CHEBMG_F64, T(x), y)
     assert np.abs(N(y)[gs] - ref).max() <= 1e-12 * scale
+    # the opt-in FP32-pair outer product, in its launch configuration, at the FP64 bar
+    cm.chebmg_set_outer_operator(s.ctx, cm.CHEBMG_OUTER_F32X2)
+    yx = empty(n)
+    cm.chebmg_apply_outer(s.ctx, T(x), yx)
+    cm.chebmg_set_outer_operator(s.ctx, cm.CHEBMG_OUTER_FP64)
+    assert np.abs(N(yx)[gs] - ref).max() <= 1e-12 * scale
     y32 = empty(n, True)
     x32 = x.astype(np.float32)
     cm.chebmg_apply_A(s.ctx, 0, cm.CHEBMG_F32, T(x32, torch.float32), y32)
@@ -87,7 +95,12 @@ def test_full_solves_32cubed(big):
     c64, it64, rel64, _ = cm.chebmg_pcg_solve(s64.ctx, bt, u64, 1e-8, 300)
     assert c64 == cm.CHEBMG_OK and rel64 <= 1e-8
     assert abs(it32 - it64) <= 2
-    for u in (u32, u64):
+    cm.chebmg_set_outer_operator(s.ctx, cm.CHEBMG_OUTER_F32X2)
+    ux = empty(len(b))
+    cx, itx, relx, _ = cm.chebmg_pcg_solve(s.ctx, bt, ux, 1e-8, 300)
+    cm.chebmg_set_outer_operator(s.ctx, cm.CHEBMG_OUTER_FP64)
+    assert cx == cm.CHEBMG_OK and relx <= 1e-8 and abs(itx - it32) <= 1
+    for u in (u32, u64, ux):
         Au = empty(len(b))
         cm.chebmg_apply_A(s64.ctx, 0, cm.CHEBMG_F64, u, Au)
         assert float(torch.linalg.norm(bt - Au) / torch.linalg.norm(bt)) <= 1.01e-8
