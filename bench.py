@@ -240,6 +240,11 @@ def bench_batched(cm, W, torch, timed, reps):
         if name == "batched_mixed_graph":
             out["iterations"] = {"min": min(its), "max": max(its)}
             out["gpu_launches"] = (cm.chebmg_launch_count() - l0) // reps
+    # opt-in: the outer products in FP64-class arithmetic on FP32 pairs
+    cm.chebmg_set_outer_operator(s32.ctx, cm.CHEBMG_OUTER_F32X2)
+    batched(s32, True)
+    out["time_s"]["batched_mixed_graph_f32x2_outer"], _ = timed(lambda: batched(s32, True), reps)
+    cm.chebmg_set_outer_operator(s32.ctx, cm.CHEBMG_OUTER_FP64)
     tb = out["time_s"]["batched_mixed_graph"]
     out["gdofs_batched_mixed_graph"] = BATCH_NRHS * n / tb / 1e9
     out["speedup_vs_sequential_fp64"] = out["time_s"]["sequential_fp64"] / tb

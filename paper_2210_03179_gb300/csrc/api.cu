@@ -1158,7 +1158,13 @@ void bfcg_body1(chebmg_ctx* c) {
   const int nb = c->nb;
   const int64_t n = L.n, ld = ldv(c, L);
   zero<double>(c, c->kq, span(c, L));
-  apply_into<double>(c, 0, c->kp, c->kq);
+  if (c->outer_op == 1 && c->G_x2) {
+    // the FP32-pair operator with the batched FP64 kernel's elements and right-hand sides per block
+    const int v = L.beb[CHEBMG_F64];
+    sem_ax8_x2(L.E, L.gid, L.lat, c->G_x2, c->kp, c->kq, c->dstat, v % 1000, c->s, nb, ld, v / 1000);
+  } else {
+    apply_into<double>(c, 0, c->kp, c->kq);
+  }
   bdot2(n, ld, nb, c->kp, c->kq, nullptr, nullptr, BPOST_ALPHA, 0.0, c->bpart, c->bscal, c->bstat, c->s);
   bfcg_update_xr(n, ld, nb, c->kx, c->kr, c->kro, c->kp, c->kq, c->bpart, c->bscal, c->bstat, c->s);
   check_launch();
@@ -2198,6 +2204,7 @@ int chebmg_set_outer_operator(chebmg_ctx* c, int kind) {
     enter(c);
     if (kind == CHEBMG_OUTER_FP64) {
       c->outer_op = 0;
+      drop_graphs(c);
       return CHEBMG_OK;
     }
     if (kind != CHEBMG_OUTER_F32X2) throw Error(CHEBMG_EINVAL, "bad outer operator kind");
@@ -2237,6 +2244,7 @@ int chebmg_set_outer_operator(chebmg_ctx* c, int kind) {
       check_launch();
     }
     c->outer_op = 1;
+    drop_graphs(c);
     return CHEBMG_OK;
   });
 }

@@ -60,11 +60,12 @@ struct Lattice {
 };
 // The order-7 operator in FP64-class arithmetic on FP32 pairs (sem_ax8_x2.cu): G in that
 // format (sem_to_x2 converts an FP64 array of n values), u and y FP64; variant as sem_ax8's
-// non-persistent codes (1, 2, 4; +100 box lattice ids).
+// non-persistent codes (1, 2, 4; +100 box lattice ids); batches of nb vectors at stride ld,
+// rb of them per thread block (the factors staged once per block).
 cudaError_t sem_ax8_x2_set_eo(const double* eo_blocks);   // [4][4][4], as uploaded by sem_ax8_set_D
 void sem_to_x2(int64_t n, const double* in, void* out, cudaStream_t s);
 void sem_ax8_x2(int64_t E, const uint32_t* gid, const Lattice& lat, const void* G, const double* u, double* y,
-                unsigned* err, int variant, cudaStream_t s);
+                unsigned* err, int variant, cudaStream_t s, int nb = 1, int64_t ld = 0, int rb = 1);
 // variant chosen per level by a setup-time autotuner: 1, 2 or 4 elements per thread block,
 // or 12 / 14 for the persistent software-pipelined kernel with 2 / 4 elements; +100 computes
 // global ids from the box lattice instead of reading the element-to-global map.

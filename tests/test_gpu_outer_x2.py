@@ -108,3 +108,22 @@ def test_refused_where_it_does_not_apply(verts):
     with pytest.raises(cm.ChebmgError):
         cm.chebmg_set_outer_operator(s.ctx, 7)
     s.close()
+
+
+def test_batched_solve_with_pair_arithmetic_outer_product(verts):
+    H = P.sem_hierarchy(verts, (7, 3, 1), kind="opt4th", k=3, sided="one-sided")
+    s = cm.Solver("sem", verts=verts, orders=(7, 3, 1), kind="opt4th", order=3, sided="one-sided", prec="mixed",
+                  lmax=[L.lmax for L in H.levels[:-1]])
+    cm.chebmg_set_outer_operator(s.ctx, cm.CHEBMG_OUTER_F32X2)
+    A = H.levels[0].apply_A
+    bs = [W.sem_rhs(*MESH, 7, seed=q) for q in range(5)]
+    B = torch.tensor(np.stack(bs), device="cuda")
+    for graph in (True, False):
+        U = torch.zeros_like(B)
+        code, its, rel = cm.chebmg_pcg_solve_batched(s.ctx, B, U, 1e-8, 100, graph=graph)
+        assert code == cm.CHEBMG_OK and max(rel) <= 1e-8
+        for q, b in enumerate(bs):
+            _, it_ref, _ = K.fcg(A, lambda r: M.vcycle(H, r), b, 1e-8)
+            assert abs(its[q] - it_ref) <= 1, (q, its[q], it_ref)
+            assert np.linalg.norm(b - A(N(U[q]))) <= 1.01e-8 * np.linalg.norm(b)
+    s.close()
