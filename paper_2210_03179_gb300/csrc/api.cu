@@ -144,6 +144,9 @@ struct chebmg_ctx {
   int coarse_kernel = 0;        // 0 grid-wide persistent kernel, 1 cluster kernel
   float* cc_val32 = nullptr;    // [14][n] symmetric stencil layout
   double* cc_val64 = nullptr;
+  // the same operator with 27 slots in lattice order (grid-wide kernel, box lattices)
+  double* lat_val = nullptr;
+  float* lat_valf = nullptr;
   int cc_nx = 0, cc_ny = 0, cc_nz = 0, cc_ctas = 0, cc_rmax = 0;
   size_t cc_smem = 0;
   bool cc_ok = false;
@@ -403,6 +406,15 @@ CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
   a.pf32 = c->coarse_pf32 ? 1 : 0;
   a.valf = c->ell_valf;
   a.invDf = c->coarse_invDf;
+  a.lat_nx = 0;
+  a.lat_nxy = 0;
+  if (c->lat_val) {   // box lattice: values in lattice slot order, columns computed
+    a.nslot = 27;
+    a.val = c->lat_val;
+    a.valf = c->lat_valf;
+    a.lat_nx = c->cc_nx;
+    a.lat_nxy = c->cc_nx * c->cc_ny;
+  }
   a.exf[0] = c->cexf[0];
   a.exf[1] = c->cexf[1];
   a.exd[0] = c->cexd[0];
@@ -1873,6 +1885,22 @@ void stencil_layout(chebmg_ctx* c, const SemHostLevel& h, const std::vector<int>
   c->cc_nx = nx;
   c->cc_ny = ny;
   c->cc_nz = nz;
+  // 27 slots in lattice order for the grid-wide kernel: slot k <-> (dx, dy, dz) =
+  // (k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1), the ELL entry A(g, g + offset) or zero
+  std::vector<double> v27((size_t)27 * n, 0.0);
+  for (int64_t g = 0; g < n; ++g) {
+    const int gx = (int)(g % nx), gy = (int)((g / nx) % ny), gz = (int)(g / ((int64_t)nx * ny));
+    for (int s = 0; s < c->nslot; ++s) {
+      const int64_t cc = col[(size_t)s * n + g];
+      const double v = val[(size_t)s * n + g];
+      if (v == 0.0) continue;
+      const int dx = (int)(cc % nx) - gx, dy = (int)((cc / nx) % ny) - gy,
+                dz = (int)(cc / ((int64_t)nx * ny)) - gz;
+      v27[(size_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) * n + g] = v;
+    }
+  }
+  c->lat_val = upload<double>(c, v27);
+  c->lat_valf = upload<float>(c, v27);
 }
 
 void upload_sem_levels(chebmg_ctx* c, std::vector<SemHostLevel>& H, bool boxed) {

@@ -189,6 +189,10 @@ struct CoarseCG {
   int pf32;
   const float* valf;     // ELL values, FP32
   const float* invDf;    // Jacobi diagonal, FP32
+  // Box lattice (lat_nx > 0): 27 slots in lattice order, slot k of row g the entry for column
+  // g + (k / 9 - 1) lat_nxy + ((k / 3) % 3 - 1) lat_nx + (k % 3 - 1), so no column indices are
+  // read; rows with a zero Jacobi entry (the lattice boundary) are skipped.
+  int lat_nx, lat_nxy;
   // Products exchange the vector they read through tagged words: each value travels with its
   // exchange tag in one 64-bit word (single-copy atomic; FP64 values as two such words), so a
   // reader needs no flag and no fence -- it reloads the words whose tag is not there yet.

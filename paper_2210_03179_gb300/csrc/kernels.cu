@@ -819,12 +819,34 @@ __device__ __forceinline__ bool coarse_spmv_tagged(const CoarseCG& a, unsigned g
   const unsigned long long* b = Tagged<V>::buf(a, gx);
   const unsigned tag = a.gen0 + gx;
   const int64_t n = a.n;
+  const bool lat = NS == 27 && a.lat_nx > 0;
+  // column of slot k: read from the ELL, or (box lattice) the row plus the slot's offset
+  auto column = [&](int k, int64_t g) -> int {
+    if (lat) return (int)g + (k / 9 - 1) * a.lat_nxy + ((k / 3) % 3 - 1) * a.lat_nx + (k % 3 - 1);
+    return ld_col(&a.col[k * n + g]);
+  };
+  // Box lattice: slots whose column is a lattice-boundary (Dirichlet) node are absent, as in the
+  // ELL, where those columns were removed.  Reading them would make a row depend on a node that
+  // reads nothing in turn, and the exchange's double buffering relies on blocks that read each
+  // other's rows doing so both ways.  Bit d of pmask[axis] is set when offset d - 1 along that
+  // axis stays inside the interior.
+  auto slot_present = [&](int k, const unsigned (&pm)[3]) -> bool {
+    return ((pm[0] >> (k % 3)) & (pm[1] >> ((k / 3) % 3)) & (pm[2] >> (k / 9)) & 1u) != 0;
+  };
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int64_t g = base + threadIdx.x + (int64_t)q * blockDim.x;
     V acc = V(0);
-    if (g < n && g < base + a.rows_per_block) {
+    if (g < n && g < base + a.rows_per_block && (!lat || __ldg(&a.invD[g]) != 0.0)) {
+      unsigned pm[3] = {7u, 7u, 7u};
+      if (lat) {
+        const int gi = (int)g, nz = (int)(n / a.lat_nxy);
+        const int gz = gi / a.lat_nxy, rem = gi - gz * a.lat_nxy, gy = rem / a.lat_nx, gxx = rem - gy * a.lat_nx;
+        const int c3[3] = {gxx, gy, gz}, e3[3] = {a.lat_nx, a.lat_nxy / a.lat_nx, nz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) pm[d] = (c3[d] - 1 >= 1 ? 1u : 0u) | 2u | (c3[d] + 1 <= e3[d] - 2 ? 4u : 0u);
+      }
       if constexpr (NS > 0) {
         // FP64 words come in pairs: a third of the slots at a time keeps them in registers
         constexpr int CH = sizeof(V) == 4 ? NS : (NS + 2) / 3;
@@ -832,19 +854,23 @@ __device__ __forceinline__ bool coarse_spmv_tagged(const CoarseCG& a, unsigned g
 #pragma unroll
         for (int k0 = 0; k0 < NS; k0 += CH) {
           TW w[CH];
+          unsigned absent = 0;   // slots not read (their coefficient is zero)
           {
             int c[CH];
 #pragma unroll
             for (int k = 0; k < CH; ++k)
-              if (k0 + k < NS) c[k] = ld_col(&a.col[(k0 + k) * n + g]);
+              if (k0 + k < NS) {
+                if (lat && !slot_present(k0 + k, pm)) absent |= 1u << k;
+                c[k] = column(k0 + k, g);
+              }
 #pragma unroll
             for (int k = 0; k < CH; ++k)
-              if (k0 + k < NS) w[k] = Tagged<V>::load(b, c[k]);
+              if (k0 + k < NS) w[k] = (absent >> k & 1u) ? TW{} : Tagged<V>::load(b, c[k]);
           }
           unsigned miss = 0;
 #pragma unroll
           for (int k = 0; k < CH; ++k)
-            if (k0 + k < NS && !Tagged<V>::ready(w[k], tag)) miss |= 1u << k;
+            if (k0 + k < NS && !(absent >> k & 1u) && !Tagged<V>::ready(w[k], tag)) miss |= 1u << k;
           if (miss && ok) {
             const uint64_t t0 = global_ns();
             for (unsigned it = 1; miss; ++it) {
@@ -852,7 +878,7 @@ __device__ __forceinline__ bool coarse_spmv_tagged(const CoarseCG& a, unsigned g
               int c[CH];
 #pragma unroll
               for (int k = 0; k < CH; ++k)
-                if (miss >> k & 1u) c[k] = ld_col(&a.col[(k0 + k) * n + g]);
+                if (miss >> k & 1u) c[k] = column(k0 + k, g);
 #pragma unroll
               for (int k = 0; k < CH; ++k)
                 if (miss >> k & 1u) w[k] = Tagged<V>::load(b, c[k]);

@@ -109,3 +109,30 @@ def test_mixed_solve_through_the_cluster_kernel():
     assert code == cm.CHEBMG_OK and rel <= 1e-8 and abs(it - it_ref) <= 1, (it, it_ref)
     assert np.linalg.norm(b - H.levels[0].apply_A(N(u))) <= 1.01e-8 * np.linalg.norm(b)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_grid_kernel_on_a_many_block_lattice(prec):
+    # E = 16^3 at N = 1: 17^3 nodes over 20 blocks, the coarse operator in lattice slot order.
+    # Every degree must reach 1e-10 within one iteration of the oracle, repeatedly (a block that
+    # ran two exchanges ahead of a neighbour would show up as a timeout or a wrong count).
+    v = W.sem_box_vertices(16, 16, 16)
+    s = cm.Solver("sem", verts=v, orders=(2, 1), prec=prec, lmax=[1.0])
+    cm.chebmg_set_coarse_kernel(s.ctx, cm.CHEBMG_COARSE_GRID)
+    kern, blocks, _ = cm.chebmg_coarse_shape(s.ctx)
+    assert kern == cm.CHEBMG_COARSE_GRID and blocks > 1
+    Lc = SemLevel(v, 1)
+    Lc.invD = Lc.inv_diagonal()
+    _, lc = cm.chebmg_coarse_info(s.ctx)
+    rng = np.random.default_rng(5)
+    for deg in (1, 8, 16):
+        cm.chebmg_set_coarse_degree(s.ctx, deg)
+        r = rng.uniform(-1, 1, Lc.n)      # Dirichlet entries included: the solver ignores them
+        _, it_ref = K.pcg_cheb4(Lc.apply_A, Lc.invD, np.where(Lc.dirichlet, 0.0, r), lc, deg, 1e-10)
+        for rep in range(3):
+            z = empty(Lc.n)
+            iters = cm.chebmg_coarse_solve(s.ctx, T(r), z)
+            rr = np.where(Lc.dirichlet, 0.0, r)
+            assert np.linalg.norm(rr - Lc.apply_A(N(z))) <= 1.01e-10 * np.linalg.norm(rr)
+            assert abs(iters - it_ref) <= 1, (prec, deg, iters, it_ref)
+    s.close()
