@@ -668,6 +668,20 @@ def main():
     clk = clocks.stop()
     t64, it64 = timed(lambda: solve(s64), max(1, min(args.steps, 3)))
 
+    # ---- the paper's statistic as well: the fastest of 20 individually timed solves ----
+    def best_of(fn, trials=20):
+        best = float("inf")
+        for _ in range(trials):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return slowest(best)
+
+    best20 = {"mixed": best_of(lambda: solve(s32)), "fp64": best_of(lambda: solve(s64))}
+
     # ---- end to end through the host-buffer entry point (pinned host memory) ----
     bh = torch.tensor(b_np).pin_memory()
     uh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -759,6 +773,7 @@ def main():
                               "ax8_elements_per_block": {"fp32": cm.chebmg_tile_choice(s32.ctx, 0, 1),
                                                          "fp64": cm.chebmg_tile_choice(s64.ctx, 0, 0)}}),
             "time_to_1e8_s": {"mixed": t32, "fp64": t64, "mixed_f32x2_outer": t32x2},
+            "time_to_1e8_s_min_of_20": best20,
             "iterations": {"mixed": it32, "fp64": it64, "mixed_f32x2_outer": it32x2},
             "outer_operator": outer,
             "speedup_mixed_vs_fp64": t64 / t32,

@@ -116,7 +116,7 @@ struct chebmg_ctx {
   double* cpartial = nullptr;
   double* cscal = nullptr;
   double* hcscal = nullptr;
-  double *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr, *kro = nullptr;
+  double *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr;
   double *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr, *cb = nullptr, *cx = nullptr;
   double* cinv = nullptr;       // FD coarsest dense inverse
   int last_coarse_iters = 0;
@@ -730,7 +730,6 @@ void common_alloc(chebmg_ctx* c) {
   c->kz = dalloc<double>(c, n0);
   c->kp = dalloc<double>(c, n0);
   c->kq = dalloc<double>(c, n0);
-  c->kro = dalloc<double>(c, n0);
   const int64_t nc = c->L.back().n;
   c->cr = dalloc<double>(c, nc);
   c->cz = dalloc<double>(c, nc);
@@ -1027,7 +1026,7 @@ void reserve_batch(chebmg_ctx* c, int nrhs) {
         for (int w = 0; w < NV; ++w)
           if (L.v[dt][w]) replace_alloc(c, L.v[dt][w], (dt == CHEBMG_F64 ? 8 : 4) * (size_t)cap * L.ld);
     const int64_t ld0 = c->L[0].ld, ldc = c->L.back().ld;
-    for (double** p : {&c->kr, &c->kz, &c->kp, &c->kq, &c->kro}) replace_vec(c, *p, (int64_t)cap * ld0);
+    for (double** p : {&c->kr, &c->kz, &c->kp, &c->kq}) replace_vec(c, *p, (int64_t)cap * ld0);
     for (double** p : {&c->cb, &c->cx}) replace_vec(c, *p, (int64_t)cap * ldc);
   }
   const int64_t ld0 = c->L[0].ld;
@@ -1148,6 +1147,19 @@ void autotune_batch(chebmg_ctx* c, int nrhs) {
 }
 
 // ---- batched flexible CG, split into launch sequences without host decisions ----
+// Mixed form: the V-cycle reads the FP32 copy of r that the x/r update writes, and its FP32
+// output feeds the dots and the p update directly (as in the single solve).
+bool bfcg_mixed(const chebmg_ctx* c) { return c->fp32 && c->L.size() > 1; }
+
+int bfcg_precondition(chebmg_ctx* c, bool r32_ready) {
+  if (!bfcg_mixed(c)) return vcycle_top(c, c->kr, c->kz);
+  Level& L = c->L[0];
+  float* r32 = vec<float>(L, VB);
+  const int64_t ld = ldv(c, L);
+  if (!r32_ready) cast<double, float>(L.n, c->kr, r32, c->s, c->nb, ld, ld);
+  return vcycle_level<float>(c, 0, r32, vec<float>(L, VX));
+}
+
 void bfcg_start(chebmg_ctx* c, const double* B, int64_t ldb, double rtol) {
   Level& L = c->L[0];
   const int nb = c->nb;
@@ -1157,10 +1169,16 @@ void bfcg_start(chebmg_ctx* c, const double* B, int64_t ldb, double rtol) {
   masked_copy(n, B, S, c->kr, c->s, nb, ldb, ld);
   zero<double>(c, c->kx, span(c, L));
   bdot2(n, ld, nb, c->kr, c->kr, nullptr, nullptr, BPOST_INIT, rtol, c->bpart, c->bscal, c->bstat, c->s);
-  const int rc = vcycle_top(c, c->kr, c->kz);
+  const int rc = bfcg_precondition(c, false);
   if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) throw Error(rc, "V-cycle failed");
-  CK(cudaMemcpyAsync(c->kp, c->kz, sizeof(double) * span(c, L), cudaMemcpyDeviceToDevice, c->s));
-  bdot2(n, ld, nb, c->kz, c->kr, nullptr, nullptr, BPOST_SET_RZ, 0.0, c->bpart, c->bscal, c->bstat, c->s);
+  if (bfcg_mixed(c)) {
+    const float* z32 = vec<float>(L, VX);
+    bupdate_p_from<float>(n, ld, nb, z32, c->kp, c->bscal, true, c->s);
+    bdot_zr_zq<float>(n, ld, nb, z32, c->kr, nullptr, BPOST_SET_RZ, c->bpart, c->bscal, c->bstat, c->s);
+  } else {
+    bupdate_p_from<double>(n, ld, nb, c->kz, c->kp, c->bscal, true, c->s);
+    bdot_zr_zq<double>(n, ld, nb, c->kz, c->kr, nullptr, BPOST_SET_RZ, c->bpart, c->bscal, c->bstat, c->s);
+  }
   check_launch();
 }
 
@@ -1178,7 +1196,8 @@ void bfcg_body1(chebmg_ctx* c) {
     apply_into<double>(c, 0, c->kp, c->kq);
   }
   bdot2(n, ld, nb, c->kp, c->kq, nullptr, nullptr, BPOST_ALPHA, 0.0, c->bpart, c->bscal, c->bstat, c->s);
-  bfcg_update_xr(n, ld, nb, c->kx, c->kr, c->kro, c->kp, c->kq, c->bpart, c->bscal, c->bstat, c->s);
+  bfcg_update_xr32(n, ld, nb, c->kx, c->kr, bfcg_mixed(c) ? vec<float>(L, VB) : nullptr, c->kp, c->kq, c->bpart,
+                   c->bscal, c->bstat, c->s);
   check_launch();
 }
 
@@ -1187,10 +1206,16 @@ void bfcg_body2(chebmg_ctx* c) {
   Level& L = c->L[0];
   const int nb = c->nb;
   const int64_t n = L.n, ld = ldv(c, L);
-  const int rc = vcycle_top(c, c->kr, c->kz);
+  const int rc = bfcg_precondition(c, true);
   if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) throw Error(rc, "V-cycle failed");
-  bdot2(n, ld, nb, c->kz, c->kr, c->kz, c->kro, BPOST_BETA, 0.0, c->bpart, c->bscal, c->bstat, c->s);
-  bupdate_p(n, ld, nb, c->kz, c->kp, c->bscal, c->s);
+  if (bfcg_mixed(c)) {
+    const float* z32 = vec<float>(L, VX);
+    bdot_zr_zq<float>(n, ld, nb, z32, c->kr, c->kq, BPOST_BETA_Q, c->bpart, c->bscal, c->bstat, c->s);
+    bupdate_p_from<float>(n, ld, nb, z32, c->kp, c->bscal, false, c->s);
+  } else {
+    bdot_zr_zq<double>(n, ld, nb, c->kz, c->kr, c->kq, BPOST_BETA_Q, c->bpart, c->bscal, c->bstat, c->s);
+    bupdate_p_from<double>(n, ld, nb, c->kz, c->kp, c->bscal, false, c->s);
+  }
   check_launch();
 }
 
@@ -2404,7 +2429,7 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
     Level& L = c->L[0];
     const int64_t n = L.n;
     const double* S = static_cast<const double*>(L.invD[CHEBMG_F64]);
-    double *r = c->kr, *z = c->kz, *p = c->kp, *q = c->kq, *ro = c->kro;
+    double *r = c->kr, *z = c->kz, *p = c->kp, *q = c->kq;
     if (iters) *iters = 0;
     reset_coarse_sticky(c);
     masked_copy(n, b, S, r, c->s);
@@ -2421,7 +2446,6 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
     // Mixed form: the V-cycle reads an FP32 copy of r, written by the x/r update, and its FP32
     // output z32 feeds the dots and the p update directly (no FP64 copy of z).  The flexible
     // (Polak-Ribiere) beta uses r_new - r_old = -alpha A p, so no copy of r_old is kept.
-    (void)ro;
     const bool mixed = c->fp32 && c->L.size() > 1;
     float* r32 = mixed ? vec<float>(L, VB) : nullptr;
     float* z32 = mixed ? vec<float>(L, VX) : nullptr;

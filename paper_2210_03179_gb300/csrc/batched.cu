@@ -114,11 +114,11 @@ __device__ void bpost(int post, double s0, double s1, double* sc, int* st, doubl
         }
       }
       break;
-    case BPOST_BETA:   // s0 = (z, r_new), s1 = (z, r_old)
+    case BPOST_BETA_Q:   // s0 = (z, r_new), s1 = (z, A p): (z, r_new - r_old) = -alpha (z, A p)
       if (st[0]) {
         sc[S_ZR] = s0;
-        sc[S_ZRO] = s1;
-        sc[S_BETA] = (s0 - s1) / sc[S_RZ];
+        sc[S_ZQ] = s1;
+        sc[S_BETA] = -sc[S_ALPHA] * s1 / sc[S_RZ];
         sc[S_RZ] = s0;
       } else {
         sc[S_BETA] = 0.0;
@@ -142,20 +142,19 @@ k_bdot2_finish(int nblk, int post, const double* __restrict__ part, double* __re
   if (threadIdx.x == 0) bpost(post, s0, s1, scal + q * S_NSLOTS, stat + q * 4, rtol);
 }
 
-// rold = r; x += alpha p; r -= alpha q; partial (r, r)   (alpha of each right-hand side)
+// x += alpha p; r -= alpha q; r32 = FP32 copy of r (if given); partial (r, r)
 __global__ void __launch_bounds__(kThreads)
-k_bfcg_update_xr(int64_t n, int64_t ld, int nblk, double* __restrict__ x, double* __restrict__ r,
-                 double* __restrict__ rold, const double* __restrict__ p, const double* __restrict__ q,
-                 double* __restrict__ part, const double* __restrict__ scal) {
+k_bfcg_update_xr32(int64_t n, int64_t ld, int nblk, double* __restrict__ x, double* __restrict__ r,
+                   float* __restrict__ r32, const double* __restrict__ p, const double* __restrict__ q,
+                   double* __restrict__ part, const double* __restrict__ scal) {
   const int64_t off = (int64_t)blockIdx.y * ld;
   const double alpha = scal[blockIdx.y * S_NSLOTS + S_ALPHA];
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n; g += (int64_t)nblk * kThreads) {
-    const double rv = r[g];
-    rold[g] = rv;
     x[g] += alpha * p[g];
-    const double rn = rv - alpha * q[g];
+    const double rn = r[g] - alpha * q[g];
     r[g] = rn;
+    if (r32) r32[g] = (float)rn;
     s0 += rn * rn;
   }
   bsum2(s0, s1);
@@ -165,14 +164,33 @@ k_bfcg_update_xr(int64_t n, int64_t ld, int nblk, double* __restrict__ x, double
   }
 }
 
+template <typename Tz>
 __global__ void __launch_bounds__(kThreads)
-k_bupdate_p(int64_t n, int64_t ld, const double* __restrict__ z, double* __restrict__ p,
-            const double* __restrict__ scal) {
+k_bdot_zr_zq(int64_t n, int64_t ld, int nblk, const Tz* __restrict__ z, const double* __restrict__ r,
+             const double* __restrict__ q, double* __restrict__ part) {
   const int64_t off = (int64_t)blockIdx.y * ld;
-  const double beta = scal[blockIdx.y * S_NSLOTS + S_BETA];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n; g += (int64_t)nblk * kThreads) {
+    const double zv = (double)z[g];
+    s0 += zv * r[g];
+    if (q) s1 += zv * q[g];
+  }
+  bsum2(s0, s1);
+  if (threadIdx.x == 0) {
+    part[(2 * (int64_t)blockIdx.y) * nblk + blockIdx.x] = s0;
+    part[(2 * (int64_t)blockIdx.y + 1) * nblk + blockIdx.x] = s1;
+  }
+}
+
+template <typename Tz>
+__global__ void __launch_bounds__(kThreads)
+k_bupdate_p_from(int64_t n, int64_t ld, const Tz* __restrict__ z, double* __restrict__ p,
+                 const double* __restrict__ scal, int first) {
+  const int64_t off = (int64_t)blockIdx.y * ld;
+  const double beta = first ? 0.0 : scal[blockIdx.y * S_NSLOTS + S_BETA];
   for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n;
        g += (int64_t)gridDim.x * kThreads)
-    p[g] = z[g] + beta * p[g];
+    p[g] = first ? (double)z[g] : (double)z[g] + beta * p[g];
 }
 
 // ---------------------------------------------------------------------------
@@ -441,20 +459,38 @@ void bdot2(int64_t n, int64_t ld, int nb, const double* a0, const double* b0, co
   g_launches.fetch_add(2, std::memory_order_relaxed);
 }
 
-void bfcg_update_xr(int64_t n, int64_t ld, int nb, double* x, double* r, double* rold, const double* p,
-                    const double* q, double* part, double* scal, int* stat, cudaStream_t s) {
+void bfcg_update_xr32(int64_t n, int64_t ld, int nb, double* x, double* r, float* r32, const double* p,
+                      const double* q, double* part, double* scal, int* stat, cudaStream_t s) {
   const int nblk = bred_blocks(n);
-  k_bfcg_update_xr<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, x, r, rold, p, q, part, scal);
+  k_bfcg_update_xr32<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, x, r, r32, p, q, part, scal);
   k_bdot2_finish<<<nb, kThreads, 0, s>>>(nblk, BPOST_CHECK, part, scal, stat, 0.0);
   g_launches.fetch_add(2, std::memory_order_relaxed);
 }
 
-void bupdate_p(int64_t n, int64_t ld, int nb, const double* z, double* p, const double* scal, cudaStream_t s) {
+template <typename Tz>
+void bdot_zr_zq(int64_t n, int64_t ld, int nb, const Tz* z, const double* r, const double* q, int post,
+                double* part, double* scal, int* stat, cudaStream_t s) {
+  const int nblk = bred_blocks(n);
+  k_bdot_zr_zq<Tz><<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, z, r, q, part);
+  k_bdot2_finish<<<nb, kThreads, 0, s>>>(nblk, post, part, scal, stat, 0.0);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+template void bdot_zr_zq<float>(int64_t, int64_t, int, const float*, const double*, const double*, int, double*,
+                                double*, int*, cudaStream_t);
+template void bdot_zr_zq<double>(int64_t, int64_t, int, const double*, const double*, const double*, int, double*,
+                                 double*, int*, cudaStream_t);
+
+template <typename Tz>
+void bupdate_p_from(int64_t n, int64_t ld, int nb, const Tz* z, double* p, const double* scal, bool first,
+                    cudaStream_t s) {
   int64_t g = (n + kThreads - 1) / kThreads;
   if (g > 1024) g = 1024;
-  k_bupdate_p<<<dim3((unsigned)g, nb), kThreads, 0, s>>>(n, ld, z, p, scal);
+  k_bupdate_p_from<Tz><<<dim3((unsigned)g, nb), kThreads, 0, s>>>(n, ld, z, p, scal, first ? 1 : 0);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
+template void bupdate_p_from<float>(int64_t, int64_t, int, const float*, double*, const double*, bool, cudaStream_t);
+template void bupdate_p_from<double>(int64_t, int64_t, int, const double*, double*, const double*, bool,
+                                     cudaStream_t);
 
 bool coarse_block_supported(int64_t n) { return n >= 1 && n <= (int64_t)kCBThreads * kCBMaxRows; }
 

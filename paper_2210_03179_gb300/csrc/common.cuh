@@ -27,7 +27,7 @@ enum Slot {
   S_ZQ,          // (z_new, q) with q = A p of the same iteration
   S_NSLOTS
 };
-enum PostOp { POST_NONE = 0, POST_ALPHA, POST_BETA_FLEX, POST_BETA_CG, POST_SET_RZ_FROM_ZR, POST_BETA_FLEX_Q };
+enum PostOp { POST_NONE = 0, POST_ALPHA, POST_BETA_CG, POST_SET_RZ_FROM_ZR, POST_BETA_FLEX_Q };
 
 constexpr int kRedBlocks = 592;    // 152 SMs x 4: partial sums per reduction pass
 
@@ -141,9 +141,6 @@ void dot2(int64_t n, const double* a0, const double* b0, const double* a1, const
           int slot0, int slot1, int post, double* partial, double* scal, cudaStream_t s);
 
 // ---- Krylov vector updates with device scalars ----
-// FCG: alpha = scal[ALPHA]; rold = r; x += alpha p; r -= alpha q; partial (r, r) -> scal[RR]
-void fcg_update_xr(int64_t n, double* x, double* r, double* rold, const double* p,
-                   const double* q, double* partial, double* scal, cudaStream_t s);
 // p = z + scal[BETA] p
 void update_p(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s);
 // The flexible CG loop's fused forms.  FCG: x += alpha p; r -= alpha q; partial (r, r) ->
@@ -282,17 +279,24 @@ enum BatchPost {
   BPOST_SET_RZ,    // s0 = (z, r): ZR = RZ = s0
   BPOST_ALPHA,     // s0 = (p, A p): ALPHA = RZ / PQ while active (breakdown freezes), else 0
   BPOST_CHECK,     // s0 = (r, r): iteration count, converged when RR <= S_T0
-  BPOST_BETA       // s0 = (z, r), s1 = (z, r_old): Polak-Ribiere BETA while active, else 0
+  BPOST_BETA_Q     // s0 = (z, r), s1 = (z, A p): Polak-Ribiere BETA while active (else 0), with
+                   // r_new - r_old = -ALPHA A p
 };
 int bred_blocks(int64_t n);
 // part needs 2 * nb * bred_blocks(n) doubles
 void bdot2(int64_t n, int64_t ld, int nb, const double* a0, const double* b0, const double* a1, const double* b1,
            int post, double rtol, double* part, double* scal, int* stat, cudaStream_t s);
-// rold = r; x += alpha p; r -= alpha q, then BPOST_CHECK on (r, r)
-void bfcg_update_xr(int64_t n, int64_t ld, int nb, double* x, double* r, double* rold, const double* p,
-                    const double* q, double* part, double* scal, int* stat, cudaStream_t s);
-// p = z + beta p
-void bupdate_p(int64_t n, int64_t ld, int nb, const double* z, double* p, const double* scal, cudaStream_t s);
+// Fused forms of the batched flexible CG: x += alpha p; r -= alpha q; r32 (if not NULL) = FP32
+// copy of r, then BPOST_CHECK; (z, r) and (z, q) with z in FP32 or FP64, then post; p = z +
+// beta p (first: p = z).
+void bfcg_update_xr32(int64_t n, int64_t ld, int nb, double* x, double* r, float* r32, const double* p,
+                      const double* q, double* part, double* scal, int* stat, cudaStream_t s);
+template <typename Tz>
+void bdot_zr_zq(int64_t n, int64_t ld, int nb, const Tz* z, const double* r, const double* q, int post,
+                double* part, double* scal, int* stat, cudaStream_t s);
+template <typename Tz>
+void bupdate_p_from(int64_t n, int64_t ld, int nb, const Tz* z, double* p, const double* scal, bool first,
+                    cudaStream_t s);
 
 // Coarse PCG with one thread block per right-hand side (no grid-wide synchronisation).
 struct CoarseBlock {

@@ -415,10 +415,6 @@ k_dot2_partial(int64_t n, const double* __restrict__ a0, const double* __restric
 __device__ void apply_post(int post, double* scal) {
   switch (post) {
     case POST_ALPHA: scal[S_ALPHA] = scal[S_RZ] / scal[S_PQ]; break;
-    case POST_BETA_FLEX:   // Polak-Ribiere: beta = (z_new, r_new - r_old) / (z_old, r_old)
-      scal[S_BETA] = (scal[S_ZR] - scal[S_ZRO]) / scal[S_RZ];
-      scal[S_RZ] = scal[S_ZR];
-      break;
     case POST_BETA_CG:     // Fletcher-Reeves for the coarse CG: beta = rz_new / rz_old
       scal[S_BETA] = scal[S_ZR] / scal[S_RZ];
       scal[S_RZ] = scal[S_ZR];
@@ -452,34 +448,6 @@ void dot2(int64_t n, const double* a0, const double* b0, const double* a1, const
           int slot1, int post, double* partial, double* scal, cudaStream_t s) {
   k_dot2_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a0, b0, a1, b1, partial);
   k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, slot0, a1 ? slot1 : -1, post, scal);
-  g_launches.fetch_add(2, std::memory_order_relaxed);
-}
-
-__global__ void __launch_bounds__(kRedThreads)
-k_fcg_update_xr(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ rold,
-                const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ partial,
-                const double* __restrict__ scal) {
-  const double alpha = scal[S_ALPHA];
-  double s0 = 0.0, s1 = 0.0;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const double rv = r[g];
-    rold[g] = rv;
-    x[g] += alpha * p[g];
-    const double rn = rv - alpha * q[g];
-    r[g] = rn;
-    s0 += rn * rn;
-  }
-  block_sum2(s0, s1);
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = s0;
-    partial[kRedBlocks + blockIdx.x] = 0.0;
-  }
-}
-
-void fcg_update_xr(int64_t n, double* x, double* r, double* rold, const double* p, const double* q,
-                   double* partial, double* scal, cudaStream_t s) {
-  k_fcg_update_xr<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, rold, p, q, partial, scal);
-  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, -1, POST_NONE, scal);
   g_launches.fetch_add(2, std::memory_order_relaxed);
 }
 
