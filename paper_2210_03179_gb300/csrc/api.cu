@@ -326,13 +326,16 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
     const double* beta = (c->o.kind == CHEBMG_CHEB_4TH_OPT) ? kBeta[order - 1] : nullptr;
     if (!c->beta_ovr.empty() && (int)c->beta_ovr.size() == order) beta = c->beta_ovr.data();
     cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), x_zero ? 1 : 0, c->s, nb, ld);
+    const double beta_k = beta ? beta[order - 1] : 1.0;
     for (int i = 1; i < order; ++i) {
       apply_into<T>(c, j, d, y);
       const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0);
       const double c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lmax);
-      cheb4_step<T>(n, x, r, d, y, S, beta ? beta[i - 1] : 1.0, c1, c2, c->s, nb, ld);
+      // the last step also applies the final update x += beta_k d_k (one pass fewer)
+      cheb4_step<T>(n, x, r, d, y, S, beta ? beta[i - 1] : 1.0, c1, c2, c->s, nb, ld,
+                    i + 1 == order ? beta_k : 0.0);
     }
-    axpy<T>(n, beta ? beta[order - 1] : 1.0, d, x, c->s, nb, ld);
+    if (order == 1 || beta_k == 0.0) axpy<T>(n, beta_k, d, x, c->s, nb, ld);
   }
   check_launch();
 }
@@ -605,7 +608,7 @@ int vcycle_level(chebmg_ctx* c, int j, const T* b, T* x) {
   }
   T* y = vec<T>(L, VY);
   T* r = vec<T>(L, VR);
-  zero<T>(c, y, span(c, L));
+  if (c->pre == 0) zero<T>(c, y, span(c, L));   // the smoothers leave y = 0
   apply_into<T>(c, j, x, y);
   residual<T>(L.n, b, y, r, c->s, c->nb, ldv(c, L));
   restrict_to<T>(c, j, r, vec<T>(C, VB));

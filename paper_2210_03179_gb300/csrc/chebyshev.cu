@@ -59,13 +59,14 @@ struct V16<double> {
 };
 
 template <typename T>
-__device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T c1, T c2) {
+__device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T c1, T c2, T beta_next) {
   const T dv = d;
   const T rv = r - y;
   x += beta * dv;
   r = rv;
   d = c1 * dv + c2 * s * rv;
   y = T(0);
+  if (beta_next != T(0)) x += beta_next * d;   // last step: the final update x += beta_k d_k
 }
 
 // x += beta d; r -= y; d = c1 d + c2 S r; y = 0 -- 16-byte vector accesses over the aligned
@@ -101,7 +102,8 @@ __device__ __forceinline__ void st16(VT* p, const VT& val, uint64_t pol) {
 
 template <typename T, bool VEC>
 __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
-                             T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, int64_t ld) {
+                             T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, T beta_next,
+                             int64_t ld) {
   { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
   using VT = typename V16<T>::type;
   constexpr int L = V16<T>::L;
@@ -119,13 +121,14 @@ __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
     T* ys = reinterpret_cast<T*>(&yv);
     const T* ss = reinterpret_cast<const T*>(&sv);
 #pragma unroll
-    for (int l = 0; l < L; ++l) cheb4_one(xs[l], rs[l], ds[l], ys[l], ss[l], beta, c1, c2);
+    for (int l = 0; l < L; ++l) cheb4_one(xs[l], rs[l], ds[l], ys[l], ss[l], beta, c1, c2, beta_next);
     st16(reinterpret_cast<VT*>(x) + q, xv, first);
     st16(reinterpret_cast<VT*>(r) + q, rv, first);
     st16(reinterpret_cast<VT*>(d) + q, dv, last);
     st16(reinterpret_cast<VT*>(y) + q, yv, last);
   }
-  for (int64_t g = nv * L + tid; g < n; g += stride) cheb4_one(x[g], r[g], d[g], y[g], invD[g], beta, c1, c2);
+  for (int64_t g = nv * L + tid; g < n; g += stride)
+    cheb4_one(x[g], r[g], d[g], y[g], invD[g], beta, c1, c2, beta_next);
 }
 
 template <typename T>
@@ -204,15 +207,15 @@ void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, do
 }
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
-                cudaStream_t s, int nb, int64_t ld) {
+                cudaStream_t s, int nb, int64_t ld, double beta_next) {
   if (!ld) ld = n;
   const uintptr_t align = (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
   if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
     k_cheb4_step<T, true><<<dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), kVecThreads, 0, s>>>(
-        n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, ld);
+        n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
   else
-    k_cheb4_step<T, false><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)beta,
-                                                                                     (T)c1, (T)c2, ld);
+    k_cheb4_step<T, false><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(
+        n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
   count();
 }
 template <typename T>
@@ -257,7 +260,7 @@ void masked_copy(int64_t n, const double* in, const double* invD, double* out, c
   template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t, int,   \
-                              int64_t);                                                                 \
+                              int64_t, double);                                                         \
   template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t, int, int64_t); \

@@ -110,10 +110,11 @@ void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream
 template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0,
                 int x_is_zero, cudaStream_t s, int nb = 1, int64_t ld = 0);
-// 4th kind step: x += beta d; r -= y; d = c1 d + c2 S r; y = 0.
+// 4th kind step: x += beta d; r -= y; d = c1 d + c2 S r; y = 0; then, if beta_next != 0 (the
+// last step), the final update x += beta_next d with the new d.
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1,
-                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0);
+                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0, double beta_next = 0.0);
 // 1st kind init: r = S (b - y) (or S b), d = r / theta, y = 0 (x = 0 if x_is_zero).
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
