@@ -134,18 +134,37 @@ def sample_desc(r):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class Clocks:
+    """nvidia-smi samples every 100 ms.  The sampler is started and its first row awaited before
+    the timed region opens (mark()), and only rows written after the mark are kept; a timed
+    region shorter than one interval keeps the last row before it and says so."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.start_row = 0
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        t0 = time.time()
+        while self.p is not None and not self._rows() and time.time() - t0 < 10 and self.p.poll() is None:
+            time.sleep(0.02)
+
+    def _rows(self):
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        return rows
+
+    def mark(self):
+        """Called just before the timed region: rows so far were taken before it."""
+        self.start_row = len(self._rows()) if self.p is not None else 0
 
     def stop(self):
         if self.p is None:
@@ -156,20 +175,23 @@ class Clocks:
         except Exception:
             self.p.kill()
         self.f.flush()
-        rows = []
-        for line in open(self.f.name):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        all_rows = self._rows()
         os.unlink(self.f.name)
+        rows = all_rows[self.start_row:]
+        before = False
+        if not rows and all_rows:
+            rows, before = all_rows[-1:], True
         if not rows:
             return None
         sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
-        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
-                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
-                "reasons": reasons, "samples": len(rows)}
+        out = {"sm_mhz": sm[len(sm) // 2] if sm else None,
+               "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+               "reasons": reasons, "samples": len(rows), "interval_ms": 100}
+        if before:
+            out["note"] = "timed region shorter than one interval: the last sample before it"
+        return out
 
 
 # ---------------------------------------------------------------------------
@@ -460,7 +482,8 @@ def main():
     global NE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 20; 5 for --impl reference, whose steps are oracle solves)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -494,6 +517,8 @@ def main():
                     help="set up, warm up, run one solve inside the NVTX range 'solve' and exit "
                          "(for ncu --nvtx-include solve/)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else 20
 
     if args.profile_solve or args.profile_smoother or args.profile_outer:
         NE = args.ne
@@ -662,6 +687,7 @@ def main():
 
     # ---- headline: mixed-precision solves, inputs resident in HBM ----
     clocks = Clocks(local)
+    clocks.mark()
     l0 = cm.chebmg_launch_count()
     t32, it32 = timed(lambda: solve(s32), args.steps)
     launches = (cm.chebmg_launch_count() - l0) // args.steps
