@@ -141,8 +141,9 @@ int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* element
 int chebmg_coarse_info(const chebmg_ctx* ctx, int* degree, double* lmax);
 /* Kernels of the SEM coarse CG (same method, same status words):
  *   CHEBMG_COARSE_GRID    one persistent cooperative launch over up to one block per SM;
- *                         products exchange rows through global memory with flags, grid-wide
- *                         reductions on an arrival counter (any coarse mesh);
+ *                         products exchange rows through global memory as 64-bit words that
+ *                         carry the value and its exchange tag together (no separate flag),
+ *                         grid-wide reductions on an arrival counter (any coarse mesh);
  *   CHEBMG_COARSE_CLUSTER one thread-block cluster (up to 16 CTAs): box lattices at N = 1 with
  *                         the FP32 preconditioner; the operator's FP32 copy and the exchanged
  *                         vectors in shared memory, halos through distributed shared memory,
@@ -155,11 +156,13 @@ int chebmg_coarse_shape(const chebmg_ctx* ctx, int* kernel, int* blocks, int* ro
 /* Overrides the coarse kernel (GRID or CLUSTER); EINVAL where it does not apply. */
 int chebmg_set_coarse_kernel(chebmg_ctx* ctx, int kernel);
 
-/* Arithmetic of the outer Krylov product q = A p on the finest level (chebmg_pcg_solve):
+/* Arithmetic of the outer Krylov product q = A p on the finest level (chebmg_pcg_solve;
+ * the operator of Sec. 1, Eq. 1.3):
  *   CHEBMG_OUTER_FP64   FP64 (default);
  *   CHEBMG_OUTER_F32X2  the order-7 operator in FP64-class arithmetic on pairs of FP32 values
- *                       (value = hi + lo, about 48 significant bits; additions carry both
- *                       rounding errors, products use the fused-multiply-add error term), the
+ *                       (value = hi + lo, about 48 significant bits; additions sum the high
+ *                       parts exactly (TwoSum) and the low parts in FP32, products use the
+ *                       fused-multiply-add error term), the
  *                       geometric factors kept as such pairs (8 bytes per value).  Relative
  *                       error near 1e-14 per application; FP32 exponent range (|values| well
  *                       inside 1e-30 .. 1e30).  GB300 executes FP32 at a large multiple of its
