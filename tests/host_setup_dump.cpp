@@ -1,0 +1,93 @@
+// Test driver for the library's host setup routines (csrc/setup_host.cpp), built and run on the
+// CPU by tests/test_host_setup.py, which compares what it writes with the oracle.
+//
+//   host_setup_dump sem <nex> <ney> <nez> <N> <verts.bin> <outdir>
+//       box level of order N: GLL x, w, D; ids with flag bits; G [E][6][NP]; assembled diagonal;
+//       Dirichlet flags -- and the same geometry handed over as a general mesh (GLL point
+//       coordinates of the trilinear map, the box's ids), whose G and diagonal it also writes
+//   host_setup_dump fd <hx> <hy> <c> <outdir>      five-point stencil and its Galerkin coarse stencil
+//   host_setup_dump lmin <k>                       the gamma^{-1}-optimal lambda_min ratio
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "../paper_2210_03179_gb300/csrc/setup_host.h"
+
+using namespace chebmg;
+
+template <typename T>
+static bool write_bin(const std::string& path, const std::vector<T>& v) {
+  FILE* f = std::fopen(path.c_str(), "wb");
+  if (!f) return false;
+  const size_t n = std::fwrite(v.data(), sizeof(T), v.size(), f);
+  std::fclose(f);
+  return n == v.size();
+}
+
+static int sem(int nex, int ney, int nez, int N, const char* vpath, const std::string& out) {
+  std::vector<double> v((size_t)(nex + 1) * (ney + 1) * (nez + 1) * 3);
+  FILE* f = std::fopen(vpath, "rb");
+  if (!f || std::fread(v.data(), sizeof(double), v.size(), f) != v.size()) return 2;
+  std::fclose(f);
+  SemHostLevel L;
+  if (!build_sem_level(nex, ney, nez, v.data(), N, L)) return 3;
+  const int NQ = N + 1, NP = NQ * NQ * NQ;
+  // the same geometry as a general mesh
+  std::vector<double> coords((size_t)L.E * NP * 3);
+  std::vector<int64_t> gid((size_t)L.E * NP);
+  for (int64_t e = 0; e < L.E; ++e) {
+    const int ex = (int)(e % nex), ey = (int)((e / nex) % ney), ez = (int)(e / ((int64_t)nex * ney));
+    for (int k = 0; k < NQ; ++k)
+      for (int j = 0; j < NQ; ++j)
+        for (int i = 0; i < NQ; ++i) {
+          const double r = (L.x[i] + 1) / 2, s = (L.x[j] + 1) / 2, t = (L.x[k] + 1) / 2;
+          const size_t p = (size_t)e * NP + (k * NQ + j) * NQ + i;
+          for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+            for (int dz = 0; dz < 2; ++dz)
+              for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx)
+                  acc += (dx ? r : 1 - r) * (dy ? s : 1 - s) * (dz ? t : 1 - t) *
+                         v[(((size_t)(ez + dz) * (ney + 1) + ey + dy) * (nex + 1) + ex + dx) * 3 + c];
+            coords[p * 3 + c] = acc;
+          }
+          gid[p] = L.gid[p] & kGidMask;
+        }
+  }
+  SemMeshInput in;
+  in.E = L.E;
+  in.N = N;
+  in.coords = coords.data();
+  in.gid = gid.data();
+  in.n = L.n;
+  in.dirichlet = L.dirichlet.data();
+  SemHostLevel M;
+  std::string err;
+  if (!build_sem_level_mesh(in, N, M, err)) return 4;
+  const bool ok = write_bin(out + "/x.bin", L.x) && write_bin(out + "/w.bin", L.w) &&
+                  write_bin(out + "/D.bin", L.Dm) && write_bin(out + "/gid.bin", L.gid) &&
+                  write_bin(out + "/G.bin", L.G) && write_bin(out + "/diag.bin", L.diag) &&
+                  write_bin(out + "/dirichlet.bin", L.dirichlet) && write_bin(out + "/G_mesh.bin", M.G) &&
+                  write_bin(out + "/diag_mesh.bin", M.diag);
+  std::printf("%lld %lld\n", (long long)L.E, (long long)L.n);
+  return ok ? 0 : 5;
+}
+
+int main(int argc, char** argv) {
+  if (argc >= 8 && std::string(argv[1]) == "sem")
+    return sem(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]), argv[6], argv[7]);
+  if (argc >= 6 && std::string(argv[1]) == "fd") {
+    double st[9], cs[9];
+    fd_fine_stencil(std::atof(argv[2]), std::atof(argv[3]), st);
+    fd_galerkin_stencil(st, std::atoi(argv[4]), cs);
+    std::vector<double> both(st, st + 9);
+    both.insert(both.end(), cs, cs + 9);
+    return write_bin(std::string(argv[5]) + "/stencils.bin", both) ? 0 : 5;
+  }
+  if (argc >= 3 && std::string(argv[1]) == "lmin") {
+    std::printf("%.17g\n", cheb1_optimal_lmin_ratio(std::atoi(argv[2])));
+    return 0;
+  }
+  return 1;
+}

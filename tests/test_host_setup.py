@@ -1,0 +1,128 @@
+"""The library's host setup (csrc/setup_host.cpp) against the oracle, on the CPU.
+
+The setup routines run once per context on the host (Sec. 1: setup is amortised over many
+right-hand sides) and everything the kernels read comes from them: GLL points, weights and the
+derivative matrix, the element-to-global ids with their Dirichlet and owner bits, the six
+geometric factors per point (Sec. 1, Eq. 1.3), the assembled diagonal (the Jacobi scaling of
+Sec. 2), the FD Galerkin stencils (Sec. 3) and the optimal 1st-kind lambda_min (Sec. 2.4).  A
+small driver (tests/host_setup_dump.cpp) is compiled with the product's source, under the
+address and undefined-behaviour sanitizers where the compiler has them, and its output is
+compared with the oracle's independent constructions.  The library computes the box's
+geometric factors from the analytic trilinear Jacobian and the general-mesh factors by
+differentiating GLL coordinates; the oracle differentiates coordinates and inverts numerically.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize_scalar
+
+import workloads as W
+from oracle import fd as F
+from oracle import theory as TH
+from oracle.gll import derivative_matrix, gll_nodes_weights
+from oracle.sem import SemLevel
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GID_DIRICHLET, GID_OWNER, GID_MASK = 0x80000000, 0x40000000, 0x3FFFFFFF
+
+pytestmark = pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    d = tmp_path_factory.mktemp("host_setup")
+    exe = str(d / "host_setup_dump")
+    src = [os.path.join(ROOT, "tests", "host_setup_dump.cpp"),
+           os.path.join(ROOT, "paper_2210_03179_gb300", "csrc", "setup_host.cpp")]
+    base = ["g++", "-std=c++17", "-O1", "-g", "-o", exe] + src
+    san = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer"]
+    r = subprocess.run(base + san, capture_output=True, text=True)
+    if r.returncode != 0:      # no sanitizer runtime: plain build
+        r = subprocess.run(base, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0:abort_on_error=1", UBSAN_OPTIONS="halt_on_error=1")
+
+    def run(*args):
+        out = subprocess.run([exe] + [str(a) for a in args], capture_output=True, text=True, env=env, timeout=300)
+        assert out.returncode == 0, (args, out.stdout[-2000:], out.stderr[-3000:])
+        return out.stdout
+    return run, d
+
+
+def _read(path, dtype):
+    return np.fromfile(path, dtype=dtype)
+
+
+@pytest.mark.parametrize("mesh,N", [((3, 2, 4), 1), ((3, 2, 4), 3), ((2, 3, 2), 5), ((2, 2, 3), 7)])
+def test_sem_level_matches_the_oracle(driver, tmp_path, mesh, N):
+    run, _ = driver
+    nex, ney, nez = mesh
+    v = W.sem_box_vertices(nex, ney, nez)
+    vpath = tmp_path / "verts.bin"
+    np.ascontiguousarray(v, dtype=np.float64).tofile(vpath)
+    E, n = (int(t) for t in run("sem", nex, ney, nez, N, vpath, tmp_path).split())
+    O = SemLevel(v, N)
+    NQ = N + 1
+    assert (E, n) == (O.E, O.n)
+    # GLL data
+    x, w = gll_nodes_weights(N)
+    np.testing.assert_allclose(_read(tmp_path / "x.bin", np.float64), x, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(_read(tmp_path / "w.bin", np.float64), w, rtol=1e-14)
+    D = derivative_matrix(x)
+    np.testing.assert_allclose(_read(tmp_path / "D.bin", np.float64).reshape(NQ, NQ), D, rtol=0,
+                               atol=1e-13 * np.abs(D).max())
+    # ids: lattice numbering, Dirichlet bit, exactly one owner copy per global node
+    gid = _read(tmp_path / "gid.bin", np.uint32).astype(np.int64)
+    ids = gid & GID_MASK
+    np.testing.assert_array_equal(ids, O.gid.reshape(-1))
+    np.testing.assert_array_equal((gid & GID_DIRICHLET) != 0, O.dirichlet[ids])
+    owners = np.bincount(ids[(gid & GID_OWNER) != 0], minlength=n)
+    assert np.all(owners == 1)
+    np.testing.assert_array_equal(_read(tmp_path / "dirichlet.bin", np.uint8) != 0, O.dirichlet)
+    # geometric factors [E][6][NP] and the assembled diagonal, box and general-mesh routes
+    Gref = O.G.reshape(E, 6, -1)
+    dref = O.diagonal()
+    for gname, dname in (("G.bin", "diag.bin"), ("G_mesh.bin", "diag_mesh.bin")):
+        G = _read(tmp_path / gname, np.float64).reshape(E, 6, -1)
+        assert np.abs(G - Gref).max() <= 1e-12 * np.abs(Gref).max(), gname
+        d = _read(tmp_path / dname, np.float64)
+        assert np.abs(d - dref).max() <= 1e-12 * np.abs(dref).max(), dname
+        assert np.all(d[O.dirichlet] == 0.0)
+
+
+def _interior_stencil(A, mx, i, j):
+    A = A.tocsr()
+    row = j * mx + i
+    st = np.zeros(9)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            st[(a + 1) * 3 + (b + 1)] = A[row, (j + a) * mx + (i + b)]
+    return st
+
+
+@pytest.mark.parametrize("Lx,c", [(1.0, 2), (8.0, 2), (1.0, 8)])
+def test_fd_stencils_match_the_oracle(driver, tmp_path, Lx, c):
+    run, _ = driver
+    m = 63 if c == 2 else 127
+    levels, _ = F.fd_levels(m, Lx=Lx, Ly=1.0, c=c, coarsest=7 if c == 2 else 15)
+    hx, hy = Lx / (m + 1), 1.0 / (m + 1)
+    run("fd", repr(hx), repr(hy), c, tmp_path)
+    both = _read(tmp_path / "stencils.bin", np.float64)
+    fine, coarse = both[:9], both[9:]
+    L0, L1 = levels[0], levels[1]
+    ref0 = _interior_stencil(L0.A, L0.mx, L0.mx // 2, L0.my // 2)
+    ref1 = _interior_stencil(L1.A, L1.mx, L1.mx // 2, L1.my // 2)
+    np.testing.assert_allclose(fine, ref0, rtol=1e-14, atol=1e-14 * np.abs(ref0).max())
+    np.testing.assert_allclose(coarse, ref1, rtol=1e-12, atol=1e-12 * np.abs(ref1).max())
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 6, 10])
+def test_optimal_lambda_min_matches_the_oracle_maximiser(driver, k):
+    run, _ = driver
+    ratio = float(run("lmin", k))
+    res = minimize_scalar(lambda lm: -TH.gamma_inv("1st", k, lmin_ratio=lm), bounds=(1e-3, 0.6),
+                          method="bounded", options={"xatol": 1e-7})
+    assert abs(ratio - res.x) <= 1e-5 * res.x
