@@ -5,6 +5,8 @@
 //       box level of order N: GLL x, w, D; ids with flag bits; G [E][6][NP]; assembled diagonal;
 //       Dirichlet flags -- and the same geometry handed over as a general mesh (GLL point
 //       coordinates of the trilinear map, the box's ids), whose G and diagonal it also writes
+//   host_setup_dump ell <nex> <ney> <nez> <N> <verts.bin> <outdir>
+//       the assembled operator of the box level in ELL form (slot count, columns, values)
 //   host_setup_dump fd <hx> <hy> <c> <outdir>      five-point stencil and its Galerkin coarse stencil
 //   host_setup_dump lmin <k>                       the gamma^{-1}-optimal lambda_min ratio
 #include <cstdio>
@@ -74,7 +76,24 @@ static int sem(int nex, int ney, int nez, int N, const char* vpath, const std::s
   return ok ? 0 : 5;
 }
 
+static int ell(int nex, int ney, int nez, int N, const char* vpath, const std::string& out) {
+  std::vector<double> v((size_t)(nex + 1) * (ney + 1) * (nez + 1) * 3);
+  FILE* f = std::fopen(vpath, "rb");
+  if (!f || std::fread(v.data(), sizeof(double), v.size(), f) != v.size()) return 2;
+  std::fclose(f);
+  SemHostLevel L;
+  if (!build_sem_level(nex, ney, nez, v.data(), N, L)) return 3;
+  int nslot = 0;
+  std::vector<int> col;
+  std::vector<double> val;
+  assemble_ell(L, nslot, col, val);
+  std::printf("%d %lld\n", nslot, (long long)L.n);
+  return write_bin(out + "/col.bin", col) && write_bin(out + "/val.bin", val) ? 0 : 5;
+}
+
 int main(int argc, char** argv) {
+  if (argc >= 8 && std::string(argv[1]) == "ell")
+    return ell(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]), argv[6], argv[7]);
   if (argc >= 8 && std::string(argv[1]) == "sem")
     return sem(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]), argv[6], argv[7]);
   if (argc >= 6 && std::string(argv[1]) == "fd") {

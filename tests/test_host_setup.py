@@ -93,6 +93,38 @@ def test_sem_level_matches_the_oracle(driver, tmp_path, mesh, N):
         assert np.all(d[O.dirichlet] == 0.0)
 
 
+@pytest.mark.parametrize("mesh,N", [((3, 2, 4), 1), ((2, 2, 2), 2)])
+def test_assembled_ell_matches_the_dense_oracle(driver, tmp_path, mesh, N):
+    # the coarse CG's matrix: rows and columns of Dirichlet nodes removed (empty rows padded
+    # with their own column and zero), every other entry the oracle's assembled A
+    run, _ = driver
+    v = W.sem_box_vertices(*mesh)
+    vpath = tmp_path / "verts.bin"
+    np.ascontiguousarray(v, dtype=np.float64).tofile(vpath)
+    nslot, n = (int(t) for t in run("ell", *mesh, N, vpath, tmp_path).split())
+    O = SemLevel(v, N)
+    assert n == O.n
+    col = _read(tmp_path / "col.bin", np.int32).reshape(nslot, n)
+    val = _read(tmp_path / "val.bin", np.float64).reshape(nslot, n)
+    A = np.zeros((n, n))
+    for s_ in range(nslot):
+        np.add.at(A, (np.arange(n), col[s_]), val[s_])
+    live = ~O.dirichlet
+    Aref = O.dense()
+    Aref[~live, :] = 0.0
+    Aref[:, ~live] = 0.0
+    assert np.abs(A - Aref).max() <= 1e-12 * np.abs(Aref).max()
+    assert np.all(col[:, ~live] == np.arange(n)[~live]) and np.all(val[:, ~live] == 0.0)
+    # the rows hold exactly the oracle's nonzeros, one slot per column; the width is at most the
+    # (2N+1)^3 nodes of the elements around a vertex (27 lattice neighbours at N = 1)
+    nnz = (val != 0).sum(axis=0)
+    np.testing.assert_array_equal(nnz, (Aref != 0).sum(axis=1))
+    for g in np.flatnonzero(live)[:50]:
+        used = col[:, g][val[:, g] != 0]
+        assert len(set(used.tolist())) == len(used)
+    assert nnz.max() <= nslot <= (2 * N + 1) ** 3 and np.all((col >= 0) & (col < n))
+
+
 def _interior_stencil(A, mx, i, j):
     A = A.tocsr()
     row = j * mx + i
