@@ -8,6 +8,9 @@
 //   host_setup_dump ell <nex> <ney> <nez> <N> <verts.bin> <outdir>
 //       the assembled operator of the box level in ELL form (slot count, columns, values)
 //   host_setup_dump fd <hx> <hy> <c> <outdir>      five-point stencil and its Galerkin coarse stencil
+//   host_setup_dump fdinv <m> <Lx> <c> <coarsest> <outdir>
+//       the stencil chain from the m x m grid down to coarsest x coarsest (Galerkin, factor c)
+//       and the dense inverse of the coarsest operator
 //   host_setup_dump lmin <k>                       the gamma^{-1}-optimal lambda_min ratio
 #include <cstdio>
 #include <cstdlib>
@@ -103,6 +106,22 @@ int main(int argc, char** argv) {
     std::vector<double> both(st, st + 9);
     both.insert(both.end(), cs, cs + 9);
     return write_bin(std::string(argv[5]) + "/stencils.bin", both) ? 0 : 5;
+  }
+  if (argc >= 7 && std::string(argv[1]) == "fdinv") {
+    const int m0 = std::atoi(argv[2]), c = std::atoi(argv[4]), coarsest = std::atoi(argv[5]);
+    const double Lx = std::atof(argv[3]);
+    double st[9], cs[9];
+    fd_fine_stencil(Lx / (m0 + 1), 1.0 / (m0 + 1), st);
+    int m = m0;
+    while (m > coarsest) {
+      fd_galerkin_stencil(st, c, cs);
+      for (int q = 0; q < 9; ++q) st[q] = cs[q];
+      m = (m + 1) / c - 1;
+    }
+    std::vector<double> inv;
+    if (!fd_dense_inverse(st, m, m, inv)) return 6;
+    std::printf("%d\n", m);
+    return write_bin(std::string(argv[6]) + "/inv.bin", inv) ? 0 : 5;
   }
   if (argc >= 3 && std::string(argv[1]) == "lmin") {
     std::printf("%.17g\n", cheb1_optimal_lmin_ratio(std::atoi(argv[2])));

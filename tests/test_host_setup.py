@@ -151,6 +151,19 @@ def test_fd_stencils_match_the_oracle(driver, tmp_path, Lx, c):
     np.testing.assert_allclose(coarse, ref1, rtol=1e-12, atol=1e-12 * np.abs(ref1).max())
 
 
+@pytest.mark.parametrize("m,Lx,c,coarsest", [(63, 1.0, 2, 7), (63, 8.0, 2, 7), (127, 1.0, 8, 15)])
+def test_fd_coarse_dense_inverse(driver, tmp_path, m, Lx, c, coarsest):
+    # the coarsest FD solve: the inverse of the repeated-Galerkin operator (Cholesky on the host)
+    run, _ = driver
+    mc = int(run("fdinv", m, repr(Lx), c, coarsest, tmp_path))
+    levels, _ = F.fd_levels(m, Lx=Lx, Ly=1.0, c=c, coarsest=coarsest)
+    Ac = levels[-1].A.toarray()
+    assert Ac.shape == (mc * mc, mc * mc)
+    inv = _read(tmp_path / "inv.bin", np.float64).reshape(mc * mc, mc * mc)
+    np.testing.assert_allclose(inv, np.linalg.inv(Ac), rtol=1e-10, atol=1e-12 * np.abs(inv).max())
+    assert np.abs(inv @ Ac - np.eye(mc * mc)).max() < 1e-11
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 6, 10])
 def test_optimal_lambda_min_matches_the_oracle_maximiser(driver, k):
     run, _ = driver
