@@ -5,6 +5,9 @@
 //       box level of order N: GLL x, w, D; ids with flag bits; G [E][6][NP]; assembled diagonal;
 //       Dirichlet flags -- and the same geometry handed over as a general mesh (GLL point
 //       coordinates of the trilinear map, the box's ids), whose G and diagonal it also writes
+//   host_setup_dump coarse <nex> <ney> <nez> <N> <Nt> <verts.bin> <outdir>
+//       the order-Nt level twice: from the box (lattice numbering) and from the order-N general
+//       mesh (coordinates interpolated, nodes numbered from the topology): ids, G, diagonal
 //   host_setup_dump ell <nex> <ney> <nez> <N> <verts.bin> <outdir>
 //       the assembled operator of the box level in ELL form (slot count, columns, values)
 //   host_setup_dump fd <hx> <hy> <c> <outdir>      five-point stencil and its Galerkin coarse stencil
@@ -30,17 +33,22 @@ static bool write_bin(const std::string& path, const std::vector<T>& v) {
   return n == v.size();
 }
 
-static int sem(int nex, int ney, int nez, int N, const char* vpath, const std::string& out) {
-  std::vector<double> v((size_t)(nex + 1) * (ney + 1) * (nez + 1) * 3);
+static bool read_verts(int nex, int ney, int nez, const char* vpath, std::vector<double>& v) {
+  v.assign((size_t)(nex + 1) * (ney + 1) * (nez + 1) * 3, 0.0);
   FILE* f = std::fopen(vpath, "rb");
-  if (!f || std::fread(v.data(), sizeof(double), v.size(), f) != v.size()) return 2;
+  if (!f) return false;
+  const bool ok = std::fread(v.data(), sizeof(double), v.size(), f) == v.size();
   std::fclose(f);
-  SemHostLevel L;
-  if (!build_sem_level(nex, ney, nez, v.data(), N, L)) return 3;
-  const int NQ = N + 1, NP = NQ * NQ * NQ;
-  // the same geometry as a general mesh
-  std::vector<double> coords((size_t)L.E * NP * 3);
-  std::vector<int64_t> gid((size_t)L.E * NP);
+  return ok;
+}
+
+// The box level L handed over as a general mesh: GLL point coordinates of the trilinear map and
+// the box's ids (flag bits cleared).
+static void as_mesh(const SemHostLevel& L, int nex, int ney, const std::vector<double>& v,
+                    std::vector<double>& coords, std::vector<int64_t>& gid) {
+  const int N = L.N, NQ = N + 1, NP = NQ * NQ * NQ;
+  coords.assign((size_t)L.E * NP * 3, 0.0);
+  gid.assign((size_t)L.E * NP, 0);
   for (int64_t e = 0; e < L.E; ++e) {
     const int ex = (int)(e % nex), ey = (int)((e / nex) % ney), ez = (int)(e / ((int64_t)nex * ney));
     for (int k = 0; k < NQ; ++k)
@@ -60,6 +68,16 @@ static int sem(int nex, int ney, int nez, int N, const char* vpath, const std::s
           gid[p] = L.gid[p] & kGidMask;
         }
   }
+}
+
+static int sem(int nex, int ney, int nez, int N, const char* vpath, const std::string& out) {
+  std::vector<double> v;
+  if (!read_verts(nex, ney, nez, vpath, v)) return 2;
+  SemHostLevel L;
+  if (!build_sem_level(nex, ney, nez, v.data(), N, L)) return 3;
+  std::vector<double> coords;
+  std::vector<int64_t> gid;
+  as_mesh(L, nex, ney, v, coords, gid);
   SemMeshInput in;
   in.E = L.E;
   in.N = N;
@@ -79,11 +97,35 @@ static int sem(int nex, int ney, int nez, int N, const char* vpath, const std::s
   return ok ? 0 : 5;
 }
 
+static int coarse(int nex, int ney, int nez, int N, int Nt, const char* vpath, const std::string& out) {
+  std::vector<double> v;
+  if (!read_verts(nex, ney, nez, vpath, v)) return 2;
+  SemHostLevel L, B, M;
+  if (!build_sem_level(nex, ney, nez, v.data(), N, L) || !build_sem_level(nex, ney, nez, v.data(), Nt, B))
+    return 3;
+  std::vector<double> coords;
+  std::vector<int64_t> gid;
+  as_mesh(L, nex, ney, v, coords, gid);
+  SemMeshInput in;
+  in.E = L.E;
+  in.N = N;
+  in.coords = coords.data();
+  in.gid = gid.data();
+  in.n = L.n;
+  in.dirichlet = L.dirichlet.data();
+  std::string err;
+  if (!build_sem_level_mesh(in, Nt, M, err)) return 4;
+  std::printf("%lld %lld\n", (long long)B.n, (long long)M.n);
+  const bool ok = write_bin(out + "/box_gid.bin", B.gid) && write_bin(out + "/box_G.bin", B.G) &&
+                  write_bin(out + "/box_diag.bin", B.diag) && write_bin(out + "/mesh_gid.bin", M.gid) &&
+                  write_bin(out + "/mesh_G.bin", M.G) && write_bin(out + "/mesh_diag.bin", M.diag) &&
+                  write_bin(out + "/mesh_dirichlet.bin", M.dirichlet);
+  return ok ? 0 : 5;
+}
+
 static int ell(int nex, int ney, int nez, int N, const char* vpath, const std::string& out) {
-  std::vector<double> v((size_t)(nex + 1) * (ney + 1) * (nez + 1) * 3);
-  FILE* f = std::fopen(vpath, "rb");
-  if (!f || std::fread(v.data(), sizeof(double), v.size(), f) != v.size()) return 2;
-  std::fclose(f);
+  std::vector<double> v;
+  if (!read_verts(nex, ney, nez, vpath, v)) return 2;
   SemHostLevel L;
   if (!build_sem_level(nex, ney, nez, v.data(), N, L)) return 3;
   int nslot = 0;
@@ -95,6 +137,9 @@ static int ell(int nex, int ney, int nez, int N, const char* vpath, const std::s
 }
 
 int main(int argc, char** argv) {
+  if (argc >= 9 && std::string(argv[1]) == "coarse")
+    return coarse(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]), std::atoi(argv[6]),
+                  argv[7], argv[8]);
   if (argc >= 8 && std::string(argv[1]) == "ell")
     return ell(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]), argv[6], argv[7]);
   if (argc >= 8 && std::string(argv[1]) == "sem")

@@ -93,6 +93,42 @@ def test_sem_level_matches_the_oracle(driver, tmp_path, mesh, N):
         assert np.all(d[O.dirichlet] == 0.0)
 
 
+@pytest.mark.parametrize("mesh,N,Nt", [((3, 2, 4), 7, 3), ((3, 2, 4), 3, 1), ((2, 3, 2), 7, 5), ((2, 2, 3), 5, 1)])
+def test_general_mesh_coarse_level_is_the_box_level_relabelled(driver, tmp_path, mesh, N, Nt):
+    # the order-Nt level of a general mesh (coordinates interpolated from order N, nodes numbered
+    # from the mesh topology) must be the box's order-Nt level under a relabelling of its nodes:
+    # one bijection between the two numberings maps every element copy, the Dirichlet flags, the
+    # assembled diagonal, and the geometric factors agree point by point
+    run, _ = driver
+    v = W.sem_box_vertices(*mesh)
+    vpath = tmp_path / "verts.bin"
+    np.ascontiguousarray(v, dtype=np.float64).tofile(vpath)
+    nb, nm = (int(t) for t in run("coarse", *mesh, N, Nt, vpath, tmp_path).split())
+    assert nb == nm
+    bg = _read(tmp_path / "box_gid.bin", np.uint32).astype(np.int64)
+    mg = _read(tmp_path / "mesh_gid.bin", np.uint32).astype(np.int64)
+    bi, mi = bg & GID_MASK, mg & GID_MASK
+    perm = np.full(nb, -1)
+    perm[bi] = mi
+    assert np.all(perm >= 0) and len(np.unique(perm)) == nb       # a bijection of the nodes
+    np.testing.assert_array_equal(perm[bi], mi)                   # consistent on every copy
+    np.testing.assert_array_equal((bg & GID_DIRICHLET) != 0, (mg & GID_DIRICHLET) != 0)
+    np.testing.assert_array_equal(_read(tmp_path / "mesh_dirichlet.bin", np.uint8)[mi] != 0,
+                                  (bg & GID_DIRICHLET) != 0)
+    owners = np.bincount(mi[(mg & GID_OWNER) != 0], minlength=nm)
+    assert np.all(owners == 1)
+    Gb = _read(tmp_path / "box_G.bin", np.float64)
+    Gm = _read(tmp_path / "mesh_G.bin", np.float64)
+    assert np.abs(Gb - Gm).max() <= 1e-12 * np.abs(Gb).max()
+    db = _read(tmp_path / "box_diag.bin", np.float64)
+    dm = _read(tmp_path / "mesh_diag.bin", np.float64)
+    assert np.abs(dm[perm] - db).max() <= 1e-12 * np.abs(db).max()
+    # and the box level itself is the oracle's order-Nt level
+    O = SemLevel(v, Nt)
+    np.testing.assert_array_equal(bi, O.gid.reshape(-1))
+    assert np.abs(Gb.reshape(O.G.shape[0], 6, -1) - O.G.reshape(O.G.shape[0], 6, -1)).max() <= 1e-12 * np.abs(O.G).max()
+
+
 @pytest.mark.parametrize("mesh,N", [((3, 2, 4), 1), ((2, 2, 2), 2)])
 def test_assembled_ell_matches_the_dense_oracle(driver, tmp_path, mesh, N):
     # the coarse CG's matrix: rows and columns of Dirichlet nodes removed (empty rows padded
