@@ -8,6 +8,9 @@
 //   host_setup_dump coarse <nex> <ney> <nez> <N> <Nt> <verts.bin> <outdir>
 //       the order-Nt level twice: from the box (lattice numbering) and from the order-N general
 //       mesh (coordinates interpolated, nodes numbered from the topology): ids, G, diagonal
+//   host_setup_dump meshfile <E> <N> <n> <Nt> <indir> <outdir>
+//       a general mesh read from indir (coords.bin E*(N+1)^3*3 doubles, gid.bin E*(N+1)^3 int64,
+//       dirichlet.bin n bytes); writes its order-Nt level's ids, diagonal and Dirichlet flags
 //   host_setup_dump ell <nex> <ney> <nez> <N> <verts.bin> <outdir>
 //       the assembled operator of the box level in ELL form (slot count, columns, values)
 //   host_setup_dump fd <hx> <hy> <c> <outdir>      five-point stencil and its Galerkin coarse stencil
@@ -123,6 +126,43 @@ static int coarse(int nex, int ney, int nez, int N, int Nt, const char* vpath, c
   return ok ? 0 : 5;
 }
 
+template <typename T>
+static bool read_bin(const std::string& path, std::vector<T>& v) {
+  FILE* f = std::fopen(path.c_str(), "rb");
+  if (!f) return false;
+  const bool ok = std::fread(v.data(), sizeof(T), v.size(), f) == v.size();
+  std::fclose(f);
+  return ok;
+}
+
+static int meshfile(int64_t E, int N, int64_t n, int Nt, const std::string& in_dir, const std::string& out) {
+  const int64_t NP = (int64_t)(N + 1) * (N + 1) * (N + 1);
+  std::vector<double> coords((size_t)(E * NP * 3));
+  std::vector<int64_t> gid((size_t)(E * NP));
+  std::vector<uint8_t> dir((size_t)n);
+  if (!read_bin(in_dir + "/coords.bin", coords) || !read_bin(in_dir + "/gid.bin", gid) ||
+      !read_bin(in_dir + "/dirichlet.bin", dir))
+    return 2;
+  SemMeshInput in;
+  in.E = E;
+  in.N = N;
+  in.coords = coords.data();
+  in.gid = gid.data();
+  in.n = n;
+  in.dirichlet = dir.data();
+  SemHostLevel M;
+  std::string err;
+  if (!build_sem_level_mesh(in, Nt, M, err)) {
+    std::printf("%s\n", err.c_str());
+    return 4;
+  }
+  std::printf("%lld\n", (long long)M.n);
+  return write_bin(out + "/gid_t.bin", M.gid) && write_bin(out + "/diag_t.bin", M.diag) &&
+                 write_bin(out + "/dirichlet_t.bin", M.dirichlet)
+             ? 0
+             : 5;
+}
+
 static int ell(int nex, int ney, int nez, int N, const char* vpath, const std::string& out) {
   std::vector<double> v;
   if (!read_verts(nex, ney, nez, vpath, v)) return 2;
@@ -137,6 +177,8 @@ static int ell(int nex, int ney, int nez, int N, const char* vpath, const std::s
 }
 
 int main(int argc, char** argv) {
+  if (argc >= 8 && std::string(argv[1]) == "meshfile")
+    return meshfile(std::atoll(argv[2]), std::atoi(argv[3]), std::atoll(argv[4]), std::atoi(argv[5]), argv[6], argv[7]);
   if (argc >= 9 && std::string(argv[1]) == "coarse")
     return coarse(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]), std::atoi(argv[6]),
                   argv[7], argv[8]);

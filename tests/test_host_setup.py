@@ -129,6 +129,72 @@ def test_general_mesh_coarse_level_is_the_box_level_relabelled(driver, tmp_path,
     assert np.abs(Gb.reshape(O.G.shape[0], 6, -1) - O.G.reshape(O.G.shape[0], 6, -1)).max() <= 1e-12 * np.abs(O.G).max()
 
 
+def _rotations():
+    """The 24 orientation-preserving relabellings of an element's (k, j, i) axes: an axis
+    permutation with an even total count of (odd permutation, flipped axes)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        odd = sum(1 for a in range(3) for b in range(a + 1, 3) if perm[a] > perm[b]) % 2
+        for flips in itertools.product((0, 1), repeat=3):
+            if (odd + sum(flips)) % 2 == 0:
+                out.append((perm, flips))
+    return out
+
+
+def _rotate(A, rot):
+    perm, flips = rot
+    B = np.transpose(A, perm + tuple(range(3, A.ndim)))
+    for ax in range(3):
+        if flips[ax]:
+            B = np.flip(B, axis=ax)
+    return np.ascontiguousarray(B)
+
+
+@pytest.mark.parametrize("mesh,N,Nt", [((3, 2, 4), 7, 3), ((2, 3, 2), 5, 1), ((2, 2, 3), 3, 3)])
+def test_shuffled_rotated_mesh_gives_the_box_levels(driver, tmp_path, mesh, N, Nt):
+    # the box handed over as a general mesh with its global ids permuted at random and every
+    # element's local axes turned by one of the 24 rotations: its order-Nt level must be the
+    # oracle's order-Nt box level under one node relabelling (ids consistent on every element
+    # copy, Dirichlet set, assembled diagonal); at Nt = N the caller's ids are kept as given
+    run, _ = driver
+    v = W.sem_box_vertices(*mesh)
+    O = SemLevel(v, N)
+    rng = np.random.default_rng(17)
+    pi = rng.permutation(O.n)
+    rots = _rotations()
+    pick = rng.integers(0, len(rots), O.E)
+    coords = np.stack([_rotate(O.coords[e], rots[pick[e]]) for e in range(O.E)])
+    gid = np.stack([_rotate(pi[O.gid[e]], rots[pick[e]]) for e in range(O.E)])
+    dirichlet = np.zeros(O.n, dtype=np.uint8)
+    dirichlet[pi] = O.dirichlet
+    d_in = tmp_path / "in"
+    d_in.mkdir()
+    coords.astype(np.float64).tofile(d_in / "coords.bin")
+    gid.astype(np.int64).tofile(d_in / "gid.bin")
+    dirichlet.tofile(d_in / "dirichlet.bin")
+    nt = int(run("meshfile", O.E, N, O.n, Nt, d_in, tmp_path).split()[0])
+    T = SemLevel(v, Nt)
+    assert nt == T.n
+    mg = _read(tmp_path / "gid_t.bin", np.uint32).astype(np.int64).reshape(T.gid.shape)
+    mi = mg & GID_MASK
+    bi = np.stack([_rotate(T.gid[e], rots[pick[e]]) for e in range(T.E)])
+    perm = np.full(T.n, -1)
+    perm[bi] = mi
+    assert np.all(perm >= 0) and len(np.unique(perm)) == T.n
+    np.testing.assert_array_equal(perm[bi], mi)
+    if Nt == N:
+        np.testing.assert_array_equal(mi, gid)
+    dm = _read(tmp_path / "dirichlet_t.bin", np.uint8) != 0
+    np.testing.assert_array_equal(dm[perm], T.dirichlet)
+    np.testing.assert_array_equal((mg & GID_DIRICHLET) != 0, T.dirichlet[bi])
+    owners = np.bincount(mi[(mg & GID_OWNER) != 0], minlength=T.n)
+    assert np.all(owners == 1)
+    diag = _read(tmp_path / "diag_t.bin", np.float64)
+    dref = T.diagonal()
+    assert np.abs(diag[perm] - dref).max() <= 1e-12 * np.abs(dref).max()
+
+
 @pytest.mark.parametrize("mesh,N", [((3, 2, 4), 1), ((2, 2, 2), 2)])
 def test_assembled_ell_matches_the_dense_oracle(driver, tmp_path, mesh, N):
     # the coarse CG's matrix: rows and columns of Dirichlet nodes removed (empty rows padded
