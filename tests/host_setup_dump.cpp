@@ -17,6 +17,8 @@
 //   host_setup_dump fdinv <m> <Lx> <c> <coarsest> <outdir>
 //       the stencil chain from the m x m grid down to coarsest x coarsest (Galerkin, factor c)
 //       and the dense inverse of the coarsest operator
+//   host_setup_dump interp <Nc> <Nf> <outdir>      Lagrange basis of the order-Nc GLL points at
+//                                                  the order-Nf GLL points (p-MG interpolation)
 //   host_setup_dump lmin <k>                       the gamma^{-1}-optimal lambda_min ratio
 #include <cstdio>
 #include <cstdlib>
@@ -209,6 +211,13 @@ int main(int argc, char** argv) {
     if (!fd_dense_inverse(st, m, m, inv)) return 6;
     std::printf("%d\n", m);
     return write_bin(std::string(argv[6]) + "/inv.bin", inv) ? 0 : 5;
+  }
+  if (argc >= 5 && std::string(argv[1]) == "interp") {
+    std::vector<double> xc, wc, xf, wf, J;
+    gll_rule(std::atoi(argv[2]), xc, wc);
+    gll_rule(std::atoi(argv[3]), xf, wf);
+    lagrange_interp(xc, xf, J);
+    return write_bin(std::string(argv[4]) + "/J.bin", J) ? 0 : 5;
   }
   if (argc >= 3 && std::string(argv[1]) == "lmin") {
     std::printf("%.17g\n", cheb1_optimal_lmin_ratio(std::atoi(argv[2])));

@@ -266,6 +266,17 @@ def test_fd_coarse_dense_inverse(driver, tmp_path, m, Lx, c, coarsest):
     assert np.abs(inv @ Ac - np.eye(mc * mc)).max() < 1e-11
 
 
+@pytest.mark.parametrize("Nf,Nc", [(7, 3), (3, 1), (7, 5), (5, 3), (9, 5)])
+def test_pmg_interpolation_matches_the_oracle(driver, tmp_path, Nf, Nc):
+    from oracle.gll import interpolation_matrix
+    run, _ = driver
+    run("interp", Nc, Nf, tmp_path)
+    J = _read(tmp_path / "J.bin", np.float64).reshape(Nf + 1, Nc + 1)
+    xc, _ = gll_nodes_weights(Nc)
+    xf, _ = gll_nodes_weights(Nf)
+    np.testing.assert_allclose(J, interpolation_matrix(xc, xf), rtol=0, atol=1e-14)
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 6, 10])
 def test_optimal_lambda_min_matches_the_oracle_maximiser(driver, k):
     run, _ = driver
