@@ -125,7 +125,7 @@ def test_batched_solve_sem_matches_oracle(verts, graph, prec):
     assert code == cm.CHEBMG_OK
     for q in range(4):
         _, it_ref, _ = K.fcg(A, lambda r: M.vcycle(H, r), B[q], 1e-8)
-        assert abs(its[q] - it_ref) <= (1 if prec == "fp64" else 2)
+        assert abs(its[q] - it_ref) <= 1
         assert rel[q] <= 1e-8
         assert np.linalg.norm(B[q] - A(N(U[q]))) <= 1.01e-8 * np.linalg.norm(B[q])
     assert its[4] == 0 and rel[4] == 0.0 and float(U[4].abs().max()) == 0.0

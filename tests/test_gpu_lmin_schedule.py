@@ -81,6 +81,6 @@ def test_sem_schedule_7531(prec):
     _, it_ref, _ = K.fcg(A, lambda q: M.vcycle(H, q), b, 1e-8)
     u = torch.zeros_like(z)
     code, it, rel, _ = cm.chebmg_pcg_solve(s.ctx, T(b), u, 1e-8, 200)
-    assert code == cm.CHEBMG_OK and abs(it - it_ref) <= (1 if prec == "fp64" else 2) and rel <= 1e-8
+    assert code == cm.CHEBMG_OK and abs(it - it_ref) <= 1 and rel <= 1e-8
     assert np.linalg.norm(b - A(N(u))) <= 1.01e-8 * np.linalg.norm(b)
     s.close()
