@@ -43,7 +43,10 @@ extern "C" {
 #define CHEBMG_ECUDA -2       /* a CUDA runtime call failed */
 #define CHEBMG_ENOTCONV -3    /* tolerance not reached within maxit; outputs valid */
 #define CHEBMG_EBREAKDOWN -4  /* p^T A p <= 0, NaN/Inf residual, or Lanczos breakdown */
-#define CHEBMG_ETIMEOUT -5    /* a bounded device wait gave up; context still usable */
+#define CHEBMG_ETIMEOUT -5    /* a bounded device wait gave up; context still usable, but
+                                 every output of that call is undefined (a copy may still
+                                 have landed late): re-run the call from its inputs.  The
+                                 solvers zero u before returning it. */
 #define CHEBMG_ENOMEM -6      /* device allocation failed */
 #define CHEBMG_EMESH -7       /* mesh with a non-positive Jacobian */
 
@@ -175,6 +178,21 @@ int chebmg_set_outer_operator(chebmg_ctx* ctx, int kind);
 int chebmg_apply_outer(chebmg_ctx* ctx, const double* x, double* y);
 int chebmg_set_coarse_degree(chebmg_ctx* ctx, int degree);
 int chebmg_set_tile_choice(chebmg_ctx* ctx, int level, int dtype, int variant);
+
+/* Fused smoother on order-7 box-lattice levels (Algorithms 1 and 2 with the operator of
+ * Sec. 1, Eq. 1.3): every step of a smoother application -- element operator with
+ * gather-scatter, Chebyshev recurrence with the Jacobi scaling, residual update -- and, in a
+ * V-cycle, the restriction residual r = b - A x (Eq. 2.2) run in one persistent launch that
+ * takes work items (elements of one element plane, or nodes of one plane range) in dependency
+ * order, instead of two kernels per step.  Variant per level and dtype, chosen at setup by
+ * timing against the separate kernels: 0 = separate kernels, 1 = FP32 (2 elements per block,
+ * the next item's geometric factors prefetched), 2 = FP64 (1 element per block), 3 = FP64
+ * with prefetch.  Single right-hand side only (batches run the separate kernels).  Same
+ * results as the separate kernels up to the order of the atomic sums. */
+int chebmg_fused_smoother(const chebmg_ctx* ctx, int level, int dtype, int* variant);
+/* Overrides that choice; EINVAL on other levels (not order 7, not a box lattice, the
+ * coarsest) or a variant that does not match dtype. */
+int chebmg_set_fused_smoother(chebmg_ctx* ctx, int level, int dtype, int variant);
 
 /* ---- per-level operators (device vectors, dtype as above) ---------------- */
 
@@ -346,20 +364,23 @@ int chebmg_selftest_coarse_timeout(chebmg_ctx* ctx, int* status);
  * whose device memory belongs entirely to that application's pool, or a real-time loop in
  * which cudaMalloc/cudaFree are forbidden because they may synchronise the device).
  *
- * Applies one smoother of the given kind and order (Algorithm 1 with lambda_min =
- * lmin_ratio * lmax, or Algorithm 2 with beta_i = 1 / the optimized table) to the
- * five-point operator on an m x m interior grid of [0,Lx] x [0,Ly] (spacing L/(m+1)),
- * x updated in place as by chebmg_smooth on level 0 of an FD context; lmax is lambda_max
- * of S A supplied by the caller.  b, x: caller-owned FP64 device vectors of m*m entries,
- * x fastest.  No context, no device or host allocation.
+ * Runs the same smoother as chebmg_smooth on level 0 of an FD context, without a context:
+ * kind CHEBMG_CHEB_1ST (lambda_min = lmin_ratio * lmax), CHEBMG_CHEB_4TH or
+ * CHEBMG_CHEB_4TH_OPT (order <= 16, the library's weight table) of the given order, on the
+ * five-point operator of an m x m interior grid of [0,Lx] x [0,Ly] (spacing L/(m+1)), x
+ * updated in place; lmax is lambda_max of S A supplied by the caller.  b, x: caller-owned
+ * FP64 device vectors of m*m entries, x fastest.  No context, no device or host allocation:
+ * the call makes no cudaMalloc, cudaFree or other allocating call.
  *
  * Limits and sharing: the work vectors live in one static device array of 4 x 262144
  * doubles (8 MiB) that every device which loads the library reserves until the process
- * exits; m*m > 262144 returns CHEBMG_EINVAL.  All calls on a device share that array, so
- * calls whose work may overlap on the GPU (different streams, or host threads) race and
- * must be serialised by the caller.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Returns EINVAL on bad arguments, ECUDA on a CUDA error. */
+ * exits; m*m > 262144 returns CHEBMG_EINVAL.  All calls on a device share that array and
+ * each call overwrites what the previous one left there, so calls whose work may overlap
+ * on the GPU (different streams, or host threads) race and must be serialised by the
+ * caller.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, and looks it up again after the
+ * device's context changes (a device reset); make that first call before any stream
+ * capture.  Returns EINVAL on bad arguments, ECUDA on a CUDA error. */
 int chebmg_fd_smooth_noalloc(int m, double Lx, double Ly, int kind, int order, double lmax,
                              double lmin_ratio, const double* b, double* x, int x_is_zero,
                              void* stream);

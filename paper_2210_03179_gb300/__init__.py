@@ -88,6 +88,8 @@ _SIGNATURES = {
     "chebmg_launch_count": (c_int, [c_void_p, POINTER(c_int64)]),
     "chebmg_tile_choice": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
     "chebmg_set_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "chebmg_fused_smoother": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
+    "chebmg_set_fused_smoother": (c_int, [c_void_p, c_int, c_int, c_int]),
     "chebmg_set_coarse_precond_dtype": (c_int, [c_void_p, c_int, c_int]),
     "chebmg_lambda_min_ratio": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "chebmg_coarse_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
@@ -307,6 +309,17 @@ def chebmg_set_coarse_degree(ctx, degree):
 
 def chebmg_set_tile_choice(ctx, level, dtype, variant):
     _check(lib().chebmg_set_tile_choice(ctx, int(level), int(dtype), int(variant)), "chebmg_set_tile_choice")
+
+
+def chebmg_fused_smoother(ctx, level, dtype) -> int:
+    """Fused-smoother variant of `level` in `dtype` (0: separate kernels)."""
+    v = c_int()
+    _check(lib().chebmg_fused_smoother(ctx, int(level), int(dtype), byref(v)), "chebmg_fused_smoother")
+    return v.value
+
+
+def chebmg_set_fused_smoother(ctx, level, dtype, variant):
+    _check(lib().chebmg_set_fused_smoother(ctx, int(level), int(dtype), int(variant)), "chebmg_set_fused_smoother")
 
 
 def chebmg_apply_A(ctx, level, dtype, x, y):

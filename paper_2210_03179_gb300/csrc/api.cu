@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstdio>
 #include <cstring>
 #include <stdexcept>
@@ -95,6 +96,10 @@ struct Level {
   int beb[2] = {2002, 2002};   // variant of the batched order-7 operator (autotuned per batch size)
   Lattice lat = {0, 0, 0, 0, 0, 0};
   bool boxed = true;    // SEM: the level carries the box lattice (lattice-indexed kernels usable)
+  // fused smoother (one persistent launch per smoother application) per dtype: 0 = the separate
+  // operator and update kernels, else the sem_smooth8 variant; control words of its launches
+  int fused[2] = {0, 0};
+  unsigned* fctl = nullptr;
   int64_t ld = 0;       // leading dimension of batched vectors: n rounded up to 64
 };
 
@@ -295,9 +300,90 @@ double lmin_ratio_for(chebmg_ctx* c, int order) {
   return c->lmin_opt[order];
 }
 
+// Whether level j can run the fused smoother at all (order-7 box lattice, one right-hand side).
+bool fused_eligible(const chebmg_ctx* c, int j) {
+  const Level& L = c->L[j];
+  return L.type == TYPE_SEM && L.Q == 8 && L.boxed && L.fctl != nullptr && c->nb == 1;
+}
+
+// The smoother of smooth() -- and, with_residual, the restriction residual r = b - A x after it
+// -- as one launch of the fused kernel (sem_smooth8.cu): the same steps and coefficients as the
+// separate kernels, written as phases (operator application, then a pointwise update).  Returns
+// false, having done nothing, where the fused kernel does not apply.
+template <typename T>
+bool smooth_fused(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero, bool with_residual) {
+  Level& L = c->L[j];
+  const int dt = dt_of<T>();
+  if (!fused_eligible(c, j) || L.fused[dt] == 0 || order < 1) return false;
+  // the pointwise phases use 16-byte accesses on b and x as well (caller vectors may be views)
+  if (reinterpret_cast<uintptr_t>(b) % 16 != 0 || reinterpret_cast<uintptr_t>(x) % 16 != 0) return false;
+  FusedSmooth a{};
+  a.E = L.E;
+  a.n = L.n;
+  a.lat = L.lat;
+  a.G = L.G[dt];
+  a.S = invD_of<T>(L);
+  a.b = b;
+  a.x = x;
+  a.r = vec<T>(L, VR);
+  a.d = vec<T>(L, VD);
+  a.y = vec<T>(L, VY);
+  a.ctl = L.fctl;
+  a.err = c->dstat;
+  const double lmax = L.lmax * c->lscale;
+  int np = 0;
+  bool fits = true;
+  auto add = [&](int op, int src, double c0 = 0.0, double c1 = 0.0, double c2 = 0.0, double c3 = 0.0) {
+    if (np >= kFusedMaxPhases) {
+      fits = false;
+      return;
+    }
+    a.ph[np++] = FusedPhase{op, src, {c0, c1, c2, c3}};
+  };
+  if (!x_zero) add(FOP_ZERO_Y, FSRC_NONE);   // the first operator application accumulates into y
+  if (c->o.kind == CHEBMG_CHEB_1ST) {
+    const double lmin = lmin_ratio_for(c, order) * lmax;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    if (x_zero) add(FOP_CHEB1_INIT_B, FSRC_NONE, 1.0 / theta);
+    else add(FOP_CHEB1_INIT_BY, FSRC_X, 1.0 / theta);
+    for (int i = 1; i < order; ++i) {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      // the last step also applies the final update x += d
+      add(FOP_CHEB1_STEP, FSRC_D, 0.0, rho_new * rho, 2.0 * rho_new / delta, i + 1 == order ? 1.0 : 0.0);
+      rho = rho_new;
+    }
+    if (order == 1) add(FOP_AXPY, FSRC_NONE, 1.0);
+  } else {
+    const double* beta = (c->o.kind == CHEBMG_CHEB_4TH_OPT) ? kBeta[order - 1] : nullptr;
+    if (!c->beta_ovr.empty() && (int)c->beta_ovr.size() == order) beta = c->beta_ovr.data();
+    if (x_zero) add(FOP_CHEB4_INIT_B, FSRC_NONE, 4.0 / (3.0 * lmax));
+    else add(FOP_CHEB4_INIT_BY, FSRC_X, 4.0 / (3.0 * lmax));
+    const double beta_k = beta ? beta[order - 1] : 1.0;
+    for (int i = 1; i < order; ++i) {
+      const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0);
+      const double c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lmax);
+      add(FOP_CHEB4_STEP, FSRC_D, beta ? beta[i - 1] : 1.0, c1, c2, i + 1 == order ? beta_k : 0.0);
+    }
+    if (order == 1 || beta_k == 0.0) add(FOP_AXPY, FSRC_NONE, beta_k);
+  }
+  if (with_residual) add(FOP_RESIDUAL, FSRC_X);
+  if (!fits) return false;
+  a.nphase = np;
+  if (!fused_plan(a, L.fused[dt])) return false;
+  if (!sem_smooth8<T>(a, L.fused[dt], c->s)) {
+    cudaGetLastError();   // a refused cooperative launch leaves no other trace: separate kernels
+    return false;
+  }
+  check_launch();
+  return true;
+}
+
 // One smoother application (Algorithm 1 or 2) of the given order on level j.
 template <typename T>
 void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
+  if (smooth_fused<T>(c, j, b, x, order, x_zero, false)) return;
   Level& L = c->L[j];
   const int64_t n = L.n;
   const int nb = c->nb;
@@ -601,16 +687,21 @@ int vcycle_level(chebmg_ctx* c, int j, const T* b, T* x) {
   if (j == (int)c->L.size() - 1) return coarse<T>(c, b, x);
   Level& L = c->L[j];
   Level& C = c->L[j + 1];
+  // the fused kernel computes the restriction residual in the same launch as the pre-smoother
+  bool have_r = false;
   if (c->pre > 0) {
-    smooth<T>(c, j, b, x, c->pre, true);
+    have_r = smooth_fused<T>(c, j, b, x, c->pre, true, true);
+    if (!have_r) smooth<T>(c, j, b, x, c->pre, true);
   } else {
     zero<T>(c, x, span(c, L));
   }
   T* y = vec<T>(L, VY);
   T* r = vec<T>(L, VR);
-  if (c->pre == 0) zero<T>(c, y, span(c, L));   // the smoothers leave y = 0
-  apply_into<T>(c, j, x, y);
-  residual<T>(L.n, b, y, r, c->s, c->nb, ldv(c, L));
+  if (!have_r) {
+    if (c->pre == 0) zero<T>(c, y, span(c, L));   // the smoothers leave y = 0
+    apply_into<T>(c, j, x, y);
+    residual<T>(L.n, b, y, r, c->s, c->nb, ldv(c, L));
+  }
   restrict_to<T>(c, j, r, vec<T>(C, VB));
   int rc = vcycle_level<T>(c, j + 1, vec<T>(C, VB), vec<T>(C, VX));
   if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
@@ -871,6 +962,57 @@ void autotune_coarse_degree(chebmg_ctx* c) {
   CK(cudaMemsetAsync(c->cctl + 4, 0, sizeof(unsigned), c->s));
 }
 
+// Time of one x0 = 0 smoother application of order 4 on level j in precision T (best of 3).
+template <typename T>
+float time_smooth(chebmg_ctx* c, int j, cudaEvent_t e0, cudaEvent_t e1) {
+  Level& L = c->L[j];
+  T* b = vec<T>(L, VB);
+  T* x = vec<T>(L, VX);
+  smooth<T>(c, j, b, x, 4, true);   // warm-up, first-launch configuration
+  float t_min = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    CK(cudaEventRecord(e0, c->s));
+    smooth<T>(c, j, b, x, 4, true);
+    CK(cudaEventRecord(e1, c->s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    t_min = std::min(t_min, ms);
+  }
+  return t_min;
+}
+
+// On an order-7 box-lattice level: allocates the fused smoother's control words and picks, per
+// precision the context uses, the fused kernel (variant) or the separate kernels (0) by timing
+// a smoother application of each on the level's own data.
+void autotune_fused(chebmg_ctx* c, int j) {
+  Level& L = c->L[j];
+  if (!(L.type == TYPE_SEM && L.Q == 8 && L.boxed)) return;
+  if (!L.fctl) L.fctl = dalloc<unsigned>(c, fused_ctl_words(L.lat));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int dt : {CHEBMG_F64, CHEBMG_F32}) {
+    if (dt == CHEBMG_F32 && (!c->fp32 || !L.G[CHEBMG_F32])) continue;
+    const size_t w = dt == CHEBMG_F64 ? sizeof(double) : sizeof(float);
+    CK(cudaMemsetAsync(L.v[dt][VB], 0, w * (size_t)L.n, c->s));
+    float best = 1e30f;
+    int best_v = 0;
+    const std::vector<int> cand = dt == CHEBMG_F32 ? std::vector<int>{0, 1} : std::vector<int>{0, 2, 3};
+    for (int v : cand) {
+      L.fused[dt] = v;
+      const float t = dt == CHEBMG_F64 ? time_smooth<double>(c, j, e0, e1) : time_smooth<float>(c, j, e0, e1);
+      if (t < best) {
+        best = t;
+        best_v = v;
+      }
+    }
+    L.fused[dt] = best_v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 void finish_setup(chebmg_ctx* c) {
   const int nl = (int)c->L.size();
   for (int j = 0; j < nl; ++j) {
@@ -890,6 +1032,7 @@ void finish_setup(chebmg_ctx* c) {
     if (!(lm > 0.0) || !std::isfinite(lm)) throw Error(CHEBMG_EBREAKDOWN, "non-positive lambda_max");
     c->L[j].lmax = lm;
   }
+  for (int j = 0; j + 1 < nl; ++j) autotune_fused(c, j);
   if (c->ell_col) {
     // lambda_max of S A on the coarse level (same Lanczos), then the preconditioner degree.
     // The mixed form evaluates the coarse CG's preconditioner in FP32 as well (the CG stays
@@ -2248,6 +2391,33 @@ int chebmg_set_tile_choice(chebmg_ctx* c, int level, int dtype, int variant) {
   return CHEBMG_OK;
 }
 
+int chebmg_fused_smoother(const chebmg_ctx* c, int level, int dtype, int* variant) {
+  return guard([&]() -> int {
+    if (!c || !variant) throw Error(CHEBMG_EINVAL, "NULL argument");
+    if (level < 0 || level >= (int)c->L.size()) throw Error(CHEBMG_EINVAL, "bad level");
+    if (dtype != CHEBMG_F64 && dtype != CHEBMG_F32) throw Error(CHEBMG_EINVAL, "bad dtype");
+    *variant = c->L[level].fused[dtype];
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_set_fused_smoother(chebmg_ctx* c, int level, int dtype, int variant) {
+  return guard([&]() -> int {
+    enter(c);
+    Level& L = level_checked(c, level);
+    check_dtype(c, dtype);
+    if (variant != 0) {
+      if (!(L.type == TYPE_SEM && L.Q == 8 && L.boxed && L.fctl))
+        throw Error(CHEBMG_EINVAL, "the fused smoother needs an order-7 box-lattice level that smooths");
+      const bool ok = dtype == CHEBMG_F32 ? variant == 1 : (variant == 2 || variant == 3);
+      if (!ok) throw Error(CHEBMG_EINVAL, "fused smoother variant: 1 for FP32, 2 or 3 for FP64");
+    }
+    L.fused[dtype] = variant;
+    drop_graphs(c);
+    return CHEBMG_OK;
+  });
+}
+
 int chebmg_launch_count(const chebmg_ctx* c, int64_t* count) {
   (void)c;
   if (!count) return CHEBMG_EINVAL;
@@ -2477,7 +2647,13 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
       const int crc = coarse_sticky_error(c);
       if (crc != CHEBMG_OK) {
         if (iters) *iters = it;
-        g_last_error = "coarse solve inside the V-cycle failed";
+        if (crc == CHEBMG_ETIMEOUT) {   // the iterate may hold the output of an unfinished kernel
+          zero<double>(c, u, n);
+          CK(cudaStreamSynchronize(c->s));
+          if (relres) *relres = std::numeric_limits<double>::quiet_NaN();
+        }
+        g_last_error = crc == CHEBMG_ETIMEOUT ? "a bounded device wait ran out inside the solve; u discarded"
+                                              : "coarse solve inside the V-cycle failed";
         return crc;
       }
       if (!(pq > 0.0) || !std::isfinite(rr)) {

@@ -82,6 +82,59 @@ void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T
 template <typename T>
 bool sem_ax8_variant_fits(int eb);
 
+// ---- fused smoother on an order-7 box-lattice level (sem_smooth8.cu) ----
+// One persistent launch runs a sequence of phases; a phase is an optional element operator
+// application y += A v (v = d or x, Sec. 1 Eq. 1.3) followed by one pointwise operation over all
+// nodes that reads and zeroes y.  The pointwise operations are those of the vector kernels below,
+// with the same arithmetic.
+enum FusedOp {
+  FOP_ZERO_Y = 0,     // y = 0
+  FOP_CHEB4_INIT_B,   // x = 0, r = b, d = c0 S r, y = 0                      (Algorithm 2, x0 = 0)
+  FOP_CHEB4_INIT_BY,  // r = b - y, d = c0 S r, y = 0                         (Algorithm 2, y = A x0)
+  FOP_CHEB4_STEP,     // x += c0 d; r -= y; d = c1 d + c2 S r; y = 0; x += c3 d  (c3 = 0 except last)
+  FOP_CHEB1_INIT_B,   // x = 0, r = S b, d = c0 r, y = 0                      (Algorithm 1, x0 = 0)
+  FOP_CHEB1_INIT_BY,  // r = S (b - y), d = c0 r, y = 0                       (Algorithm 1, y = A x0)
+  FOP_CHEB1_STEP,     // x += d; r -= S y; d = c1 d + c2 r; y = 0; x += c3 d      (c3 = 0 except last)
+  FOP_AXPY,           // x += c0 d
+  FOP_RESIDUAL        // r = b - y, y = 0                                      (restriction residual)
+};
+enum FusedSrc { FSRC_NONE = 0, FSRC_D = 1, FSRC_X = 2 };
+struct FusedPhase {
+  int op;             // FusedOp
+  int src;            // FusedSrc: the vector the phase's operator application reads
+  double c[4];
+};
+constexpr int kFusedMaxPhases = 24;
+constexpr int kFusedMaxT = 700;   // queue steps: 3 (phases - 1) + element planes + 1 at most
+struct FusedSmooth {
+  int64_t E, n;
+  Lattice lat;
+  int nphase;
+  FusedPhase ph[kFusedMaxPhases];
+  const void *G, *S, *b;
+  void *x, *r, *d, *y;
+  unsigned* ctl;      // fused_ctl_words(lat) words, zeroed by the launcher
+  unsigned* err;      // set to 1 when a bounded wait runs out
+  // derived by fused_plan
+  int nslab;          // element planes (slabs)
+  int spp;            // elements per slab
+  int m1, m2;         // work items per operator task / per pointwise task
+  int chunk;          // nodes per pointwise work item
+  int tsteps;
+  uint32_t total;
+  uint32_t toff[kFusedMaxT + 1];
+};
+// Variants: 1 = FP32, 2 elements per block, geometric factors of the next item prefetched;
+// 2 = FP64, 1 element per block, no prefetch; 3 = FP64 with prefetch.
+int fused_ctl_words(const Lattice& lat);
+// Fills the derived fields; false if the level or the program is beyond the kernel's limits
+// (the caller then runs the separate kernels).
+bool fused_plan(FusedSmooth& a, int variant);
+// Launches the fused kernel (cooperative); false, with nothing launched, if that is impossible.
+template <typename T>
+bool sem_smooth8(FusedSmooth& a, int variant, cudaStream_t s);
+cudaError_t sem_smooth8_set_eo(const double* eo_blocks);   // [4][4][4], as for sem_ax8_x2_set_eo
+
 // p-multigrid transfers on the box lattice for the order pairs (7,3), (3,1), (7,5), (5,3)
 // (Q 8->4, 4->2, 8->6, 6->4).
 cudaError_t transfer_box_set_J(int Qf, int Qc, const double* J);
