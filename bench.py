@@ -95,13 +95,18 @@ for _ in range(%(reps)d):
     t = time.perf_counter()
     x, it, hist = K.fcg(H.levels[0].apply_A, lambda r: M.vcycle(H, r), b, %(rtol)r)
     times.append(time.perf_counter() - t)
+if %(save)r:
+    import numpy as np
+    np.save(%(save)r, x)
 print(json.dumps({"n": H.levels[0].n, "iters": it, "times": times}))
 """
 
 
-def run_oracle(reps: int):
+def run_oracle(reps: int, save: str = ""):
+    """Time `reps` oracle solves of the E=16^3 sample in a one-thread subprocess; with `save`,
+    the last solution is written there (numpy .npy) for the error of the GPU results."""
     code = ORACLE_SNIPPET % dict(root=ROOT, ne=SAMPLE_NE, orders=ORDERS, kind=KIND, k=K_ORDER, sided=SIDED,
-                                 N=NORDER, rtol=RTOL, reps=reps)
+                                 N=NORDER, rtol=RTOL, reps=reps, save=save)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
@@ -113,7 +118,7 @@ def run_oracle_all_cores():
     the host's whole-machine oracle throughput.  Returns (total DOFs, wall seconds, cores)."""
     cores = len(os.sched_getaffinity(0))
     code = ORACLE_SNIPPET % dict(root=ROOT, ne=SAMPLE_NE, orders=ORDERS, kind=KIND, k=K_ORDER, sided=SIDED,
-                                 N=NORDER, rtol=RTOL, reps=1)
+                                 N=NORDER, rtol=RTOL, reps=1, save="")
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     t0 = time.perf_counter()
@@ -128,6 +133,16 @@ def run_oracle_all_cores():
 def sample_desc(r):
     return (f"FP64 numpy oracle, one thread, full FCG solve of the same recipe at E={SAMPLE_NE}^3 "
             f"(n={r['n']}, {r['iters']} iterations), setup excluded")
+
+
+def sample_config(r):
+    """The configuration the oracle sample actually solves: the benchmark's recipe and cycle at
+    E = 16^3 (the rate is per DOF, so it compares with the E = 32^3 GPU rate)."""
+    return {"workload": f"SEM Poisson E={SAMPLE_NE}^3 N={NORDER}, p-MG {ORDERS}, {KIND} Chebyshev one-sided "
+                        f"({2 * K_ORDER},0), FCG to 1e-8 (bounded sample of the E={NE}^3 workload)",
+            "E": SAMPLE_NE ** 3, "N": NORDER, "n_dof": r["n"], "orders": list(ORDERS), "smoother": KIND,
+            "k": K_ORDER, "sided": SIDED, "rtol": RTOL, "iterations": r["iters"],
+            "sample_of": {"E": NE ** 3, "n_dof": (NE * NORDER + 1) ** 3}}
 
 
 # ---------------------------------------------------------------------------
@@ -349,23 +364,61 @@ TABLE1 = [  # Lx, coarsening, complexity, kind, m, n, matvecs, iterations (print
     (64, 8, 1.023, "opt4th", 18, 0, 323, 17), (128, 8, 1.023, "opt4th", 20, 0, 294, 14)]
 
 
+def table1_weights():
+    """Optimized 4th-kind weights for the smoothing orders 18 and 20 of Table 1, which Table 5
+    does not list: the gamma^{-1}-maximising weights stored beside the tests (computed once from
+    Eq. 2.14; they reproduce Table 5 for the orders it lists)."""
+    rec = json.load(open(os.path.join(ROOT, "tests", "golden", "optimal_betas.json")))
+    return {int(k): v["betas"] for k, v in rec["orders"].items()}
+
+
+def true_relres(cm, torch, s, b, u):
+    """||b - A u|| / ||b|| with the FP64 operator of the finest level (held to the oracle at 1e-12)."""
+    y = torch.zeros_like(b)
+    cm.chebmg_apply_A(s.ctx, 0, cm.CHEBMG_F64, u, y)
+    return float(torch.linalg.norm(b - y) / torch.linalg.norm(b))
+
+
+def errors_against_oracle(cm, W, torch, np, x_ref, it_ref):
+    """The mixed and FP64 GPU solutions of the E = 16^3 sample against the oracle's FCG solution of
+    the same problem: iterations, max-norm relative error and the true FP64 relative residual."""
+    ne = SAMPLE_NE
+    v = W.sem_box_vertices(ne, ne, ne)
+    b = torch.tensor(W.sem_rhs(ne, ne, ne, NORDER), device="cuda")
+    out = {"workload": f"E={ne}^3 N={NORDER}, the benchmark's recipe and cycle", "oracle_iterations": it_ref}
+    xr = torch.tensor(x_ref, device="cuda")
+    lmax = None
+    for prec in ("mixed", "fp64"):
+        s = cm.Solver("sem", verts=v, orders=ORDERS, kind=KIND, order=K_ORDER, sided=SIDED, prec=prec, lmax=lmax)
+        if lmax is None:
+            lmax = [s.lambda_max(j) for j in range(len(ORDERS) - 1)]
+        u = torch.zeros_like(b)
+        code, it, rel, _ = cm.chebmg_pcg_solve(s.ctx, b, u, RTOL, 500)
+        out[prec] = {"status": code, "iterations": it, "recursive_relres": rel,
+                     "true_relres": true_relres(cm, torch, s, b, u),
+                     "max_rel_error_vs_oracle": float((u - xr).abs().max() / xr.abs().max())}
+        s.close()
+    return out
+
+
 def bench_fd_table1(cm, torch, timed, reps):
-    """The paper's FD study on the GPU: each Table 1 row whose smoothing order has tabulated
-    weights (order <= 16; Table 5 stops there), with the GPU's own Lanczos lambda_max,
-    u = sin(3 pi x / Lx) sin(4 pi y) + g (g uniform[-1,1], seed 0), b = A u."""
+    """The paper's FD study on the GPU: all eight Table 1 rows, with the GPU's own Lanczos
+    lambda_max, u = sin(3 pi x / Lx) sin(4 pi y) + g (g uniform[-1,1], seed 0), b = A u.  Rows
+    whose smoothing order is above 16 (beyond Table 5) run the optimized 4th kind with the
+    gamma^{-1}-maximising weights of that order, set through chebmg_set_smoother_weights."""
     import numpy as np
+    betas = table1_weights()
     out = []
     for Lx, c, cx, kind, m, nn, mv, its in TABLE1:
         row = {"Lx": Lx, "coarsening": c, "kind": kind, "m": m, "n": nn,
                "paper": {"iterations": its, "matvecs": mv, "grid_complexity": cx}}
-        if m + nn > 16:
-            row["skipped"] = "smoothing order above 16: Table 5 lists no weights (the library takes them " \
-                             "through chebmg_set_smoother_weights; the GPU tests run this row)"
-            out.append(row)
-            continue
         k, sided = (m // 2, "one-sided") if nn == 0 else (m, "symmetric")
-        s = cm.Solver("fd2d", m=127, Lx=float(Lx), Ly=1.0, coarsening=c, coarsest=1, kind=kind, order=k,
-                      sided=sided)
+        order = m + nn
+        s = cm.Solver("fd2d", m=127, Lx=float(Lx), Ly=1.0, coarsening=c, coarsest=1,
+                      kind=kind if order <= 16 else "4th", order=k, sided=sided)
+        if order > 16:
+            cm.chebmg_set_smoother_weights(s.ctx, betas[order], 1.0)
+            row["weights"] = f"gamma^-1-optimal weights of order {order} (Table 5 stops at 16)"
         sizes = [int(round(s.size(j) ** 0.5)) for j in range(s.num_levels)]
         nnz = [5 * sizes[0] ** 2 - 4 * sizes[0]] + [(3 * q - 2) ** 2 for q in sizes[1:]]
         x = np.arange(1, 128) * (Lx / 128.0)
@@ -536,8 +589,9 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config(),
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc(r)},
+                "config": sample_config(r),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc(r),
+                                 "config": sample_config(r)},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
@@ -708,6 +762,15 @@ def main():
 
     best20 = {"mixed": best_of(lambda: solve(s32)), "fp64": best_of(lambda: solve(s64))}
 
+    # ---- each form's result: true FP64 residual, and the mixed solution against the FP64 one ----
+    solve(s64)
+    u64 = u.clone()
+    solve(s32)
+    results = {"mixed": {"iterations": it32, "true_relres": true_relres(cm, torch, s64, b, u)},
+               "fp64": {"iterations": it64, "true_relres": true_relres(cm, torch, s64, b, u64)},
+               "mixed_vs_fp64_max_rel_diff": float((u - u64).abs().max() / u64.abs().max())}
+    del u64
+
     # ---- end to end through the host-buffer entry point (pinned host memory) ----
     bh = torch.tensor(b_np).pin_memory()
     uh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -748,18 +811,33 @@ def main():
                 "traffic": recorded_traffic(cm.chebmg_tile_choice(s32.ctx, 0, 1)),
                 "alg_bytes_per_step": alg_bytes32, "step_us": step32 * 1e6,
                 "elements_per_block_variant": cm.chebmg_tile_choice(s32.ctx, 0, 1)}
-    flops64 = 111 * L + 8 * n
-    # FP64 denominator measured like the bf16 one: a cuBLAS DGEMM, 4096^3, best of 5
-    A64 = torch.rand(4096, 4096, dtype=torch.float64, device="cuda")
-    B64 = torch.rand_like(A64)
-    torch.matmul(A64, B64)
-    t_mm, _ = timed(lambda: torch.matmul(A64, B64), 5)
-    peak64 = 2 * 4096 ** 3 / t_mm / 1e12
-    del A64, B64
-    fp64_alu = {"bound": "alu", "kernel": "fine FP64 Chebyshev step", "achieved": flops64 / step64 / 1e12,
-                "peak": peak64, "unit": "TFLOP/s", "frac": flops64 / step64 / 1e12 / peak64,
-                "peak_source": "of measured cuBLAS DGEMM rate (4096^3) in this run; nominal GB300 FP64 1.25",
-                "step_us": step64 * 1e6}
+    # ---- the FP64 outer operator q = A p (k_sem_ax8<double>), bound by the FP64 pipe ----
+    # Executed FP64 instructions per element point, counted from the kernel source: six line
+    # passes of 44 per 8-point line (8 even-odd sums, 4 x 9 chain FMAs) = 33, the geometric
+    # factors 9 (3 x (1 mul + 2 FMA)), two additions of the transposed contributions = 44.
+    FP64_INSTR_PER_POINT = 44
+    xo64 = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    yo64 = torch.zeros_like(xo64)
+    cm.chebmg_apply_A(s32.ctx, 0, cm.CHEBMG_F64, xo64, yo64)
+    t_apply64, _ = timed(lambda: cm.chebmg_apply_A(s32.ctx, 0, cm.CHEBMG_F64, xo64, yo64), 10)
+    t_zero64, _ = timed(lambda: yo64.zero_(), 10)     # apply_A zeroes y first: take that out
+    t_op_kernel = max(t_apply64 - t_zero64, 1e-9)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    # GB300 issues 2 FP64 FMA (or add / mul) instructions per SM per clock: the unit-count rate,
+    # 2 x 152 x 2.07 GHz = 629 G instructions/s (1.26 TFLOP/s in FMAs, the nominal 1.25)
+    peak_i64 = 2 * sms * sm_mhz * 1e6 / 1e9
+    ach_i64 = FP64_INSTR_PER_POINT * L / t_op_kernel / 1e9
+    fp64_alu = {"bound": "alu", "kernel": "FP64 outer operator q = A p (k_sem_ax8<double>, element Ax + "
+                                          "gather-scatter), 40% of the mixed solve",
+                "achieved": ach_i64, "peak": peak_i64, "unit": "G FP64 instructions/s", "frac": ach_i64 / peak_i64,
+                "peak_source": f"unit count: 2 FP64 instructions / SM / clock x {sms} SMs x {sm_mhz:.0f} MHz "
+                               f"(median SM clock sampled in the timed region)",
+                "instructions_per_point": FP64_INSTR_PER_POINT, "points_per_launch": L,
+                "kernel_us": t_op_kernel * 1e6,
+                "algorithmic_tflops": (111 * L + 8 * n) / t_op_kernel / 1e12,
+                "fine_fp64_chebyshev_step_us": step64 * 1e6}
+    del xo64, yo64
 
     # ---- coarse solve (N = 1, FP64 CG to the coarse tolerance) on its own ----
     def coarse_time(s):
@@ -802,6 +880,7 @@ def main():
             "time_to_1e8_s": {"mixed": t32, "fp64": t64, "mixed_f32x2_outer": t32x2},
             "time_to_1e8_s_min_of_20": best20,
             "iterations": {"mixed": it32, "fp64": it64, "mixed_f32x2_outer": it32x2},
+            "results": results,
             "outer_operator": outer,
             "speedup_mixed_vs_fp64": t64 / t32,
             "smoother_gdofs": {"fp32": n / step32 / 1e9, "fp64": n / step64 / 1e9},
@@ -835,10 +914,14 @@ def main():
                                                     f"E={SAMPLE_NE}^3 recipe (one per core), setup included in "
                                                     f"each process, wall time {wall:.1f} s"}
     if rank == 0 and not args.no_cpu_baseline:
-        r = run_oracle(1)
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "x_oracle.npy")
+            r = run_oracle(1, save=path)
+            x_ref = np.load(path)
         t = r["times"][0]
         line["cpu_baseline"] = {"value": r["n"] / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": sample_desc(r), "seconds": t}
+                                "sample": sample_desc(r), "seconds": t, "config": sample_config(r)}
+        line["error_vs_oracle"] = errors_against_oracle(cm, W, torch, np, x_ref, r["iters"])
     s32.close()
     s64.close()
     if rank == 0:

@@ -34,7 +34,13 @@ def test_reference_arm_prints_one_line_in_the_bench_unit():
     assert "E=16^3" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == bench.config()["workload"]
+    # the config names what was solved: the benchmark's recipe and cycle at E = 16^3
+    c = d["config"]
+    assert c["E"] == 16 ** 3 and c["n_dof"] == 1_442_897 and c["N"] == bench.NORDER
+    assert c["sample_of"] == {"E": 32 ** 3, "n_dof": 11_390_625} and c["iterations"] >= 1
+    for key in ("orders", "smoother", "k", "sided", "rtol"):
+        assert c[key] == bench.config()[key]
+    assert cb["config"] == c
     # value = DOFs of the sample / seconds per solve
     assert abs(d["value"] - 1_442_897 / (d["ms_per_step"] / 1e3) / 1e9) <= 1e-9 * d["value"] + 1e-15
 
