@@ -11,6 +11,7 @@
 // scaling S) live in the file-scope device array below.  It is reserved once on every
 // device that loads the library and held until the process exits.  Limits and sharing
 // rules are stated next to the declaration in include/chebmg.h.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -26,25 +27,66 @@ constexpr int kNoAllocMaxDevices = 128;
 // r | d | y | S, 4 x 262,144 doubles = 8 MiB on every device that loads the library.
 static __device__ __align__(256) double g_noalloc_scratch[4 * kNoAllocMaxN];
 
+// Device address of the array per device, with the id of the CUDA context it was looked up
+// in.  A context id is unique for the life of the process, so after a device reset (which
+// destroys the context and unloads this module) the next call sees a new id and looks the
+// address up again instead of using a stale one.
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;
+  double* ptr = nullptr;
+};
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+ScratchSlot g_noalloc_slot[kNoAllocMaxDevices];
 
-// Device address of the scratch array on the current device, looked up on the first call
-// per device.  In host code the name g_noalloc_scratch is only a host-side stand-in: it is
-// never passed to a kernel, only the address returned by cudaGetSymbolAddress is.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the current context through the driver entry points the runtime hands out (no link
+// against the driver library needed); 0 if it cannot be had, which forces a fresh look-up.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    resolved = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device: set up (cudaGetSymbolAddress,
+// with the device current) on the first call per device and again whenever the device's
+// context has changed since.  In host code the name g_noalloc_scratch is only a host-side
+// stand-in: it is never passed to a kernel, only the address returned here is.
 cudaError_t scratch_on_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  ScratchSlot& slot = g_noalloc_slot[dev];
+  const unsigned long long id = current_context_id();   // 0 while no context is current
+  if (!slot.ptr || id == 0 || slot.ctx_id != id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);      // makes the device's context current
     if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
+    slot.ptr = static_cast<double*>(p);
+    slot.ctx_id = current_context_id();
   }
-  *out = g_noalloc_ptr[dev];
+  *out = slot.ptr;
   return cudaSuccess;
 }
 
@@ -96,7 +138,7 @@ extern "C" int chebmg_fd_smooth_noalloc(int m, double Lx, double Ly, int kind, i
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!x_is_zero) fd_apply<double>(m, m, A, x, y, s);
 
-  // Algorithm 1 (1st kind) or Algorithm 2 ((optimized) 4th kind), as in chebmg_smooth.
+  // The same smoother arithmetic as chebmg_smooth on level 0 of an FD context.
   if (kind == CHEBMG_CHEB_1ST) {
     const double lmin = lmin_ratio * lmax;
     const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
