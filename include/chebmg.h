@@ -185,10 +185,10 @@ int chebmg_set_tile_choice(chebmg_ctx* ctx, int level, int dtype, int variant);
  * V-cycle, the restriction residual r = b - A x (Eq. 2.2) run in one persistent launch that
  * takes work items (elements of one element plane, or nodes of one plane range) in dependency
  * order, instead of two kernels per step.  Variant per level and dtype, chosen at setup by
- * timing against the separate kernels: 0 = separate kernels, 1 = FP32 (2 elements per block,
- * the next item's geometric factors prefetched), 2 = FP64 (1 element per block), 3 = FP64
- * with prefetch.  Single right-hand side only (batches run the separate kernels).  Same
- * results as the separate kernels up to the order of the atomic sums. */
+ * timing against the separate kernels: 0 = separate kernels, 1 = FP32 (2 elements per work
+ * item), 2 = FP64 (1 element per work item).  Single right-hand side only (batches run the
+ * separate kernels).  Same results as the separate kernels up to the order of the atomic
+ * sums. */
 int chebmg_fused_smoother(const chebmg_ctx* ctx, int level, int dtype, int* variant);
 /* Overrides that choice; EINVAL on other levels (not order 7, not a box lattice, the
  * coarsest) or a variant that does not match dtype. */

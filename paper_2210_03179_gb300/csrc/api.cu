@@ -998,7 +998,7 @@ void autotune_fused(chebmg_ctx* c, int j) {
     CK(cudaMemsetAsync(L.v[dt][VB], 0, w * (size_t)L.n, c->s));
     float best = 1e30f;
     int best_v = 0;
-    const std::vector<int> cand = dt == CHEBMG_F32 ? std::vector<int>{0, 1} : std::vector<int>{0, 2, 3};
+    const std::vector<int> cand = dt == CHEBMG_F32 ? std::vector<int>{0, 1} : std::vector<int>{0, 2};
     for (int v : cand) {
       L.fused[dt] = v;
       const float t = dt == CHEBMG_F64 ? time_smooth<double>(c, j, e0, e1) : time_smooth<float>(c, j, e0, e1);
@@ -2409,8 +2409,8 @@ int chebmg_set_fused_smoother(chebmg_ctx* c, int level, int dtype, int variant) 
     if (variant != 0) {
       if (!(L.type == TYPE_SEM && L.Q == 8 && L.boxed && L.fctl))
         throw Error(CHEBMG_EINVAL, "the fused smoother needs an order-7 box-lattice level that smooths");
-      const bool ok = dtype == CHEBMG_F32 ? variant == 1 : (variant == 2 || variant == 3);
-      if (!ok) throw Error(CHEBMG_EINVAL, "fused smoother variant: 1 for FP32, 2 or 3 for FP64");
+      const bool ok = dtype == CHEBMG_F32 ? variant == 1 : variant == 2;
+      if (!ok) throw Error(CHEBMG_EINVAL, "fused smoother variant: 1 for FP32, 2 for FP64");
     }
     L.fused[dtype] = variant;
     drop_graphs(c);

@@ -124,8 +124,7 @@ struct FusedSmooth {
   uint32_t total;
   uint32_t toff[kFusedMaxT + 1];
 };
-// Variants: 1 = FP32, 2 elements per block, geometric factors of the next item prefetched;
-// 2 = FP64, 1 element per block, no prefetch; 3 = FP64 with prefetch.
+// Variants: 1 = FP32, 2 elements per work item; 2 = FP64, 1 element per work item.
 int fused_ctl_words(const Lattice& lat);
 // Fills the derived fields; false if the level or the program is beyond the kernel's limits
 // (the caller then runs the separate kernels).

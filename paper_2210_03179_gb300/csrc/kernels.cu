@@ -63,6 +63,18 @@ k_sem_ax(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G,
   const int64_t e = (int64_t)blockIdx.x * EPB + le;
   if (tid < Q * Q) sD[tid] = Dg[tid];
   const bool valid = e < E;
+  // the geometric factors do not depend on the gather: their loads go out first, in flight
+  // with the id and value loads instead of after them
+  T g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
+  if (valid) {
+    const T* Ge = G + (size_t)e * 6 * NP + p;
+    g00 = Ge[0];
+    g01 = Ge[NP];
+    g02 = Ge[2 * NP];
+    g11 = Ge[3 * NP];
+    g12 = Ge[4 * NP];
+    g22 = Ge[5 * NP];
+  }
   const uint32_t id = valid ? gid[e * NP + p] : kGidDirichlet;
   T* su = s_u + le * NP;
   su[p] = (id & kGidDirichlet) ? T(0) : u[id & kGidMask];
@@ -76,9 +88,6 @@ k_sem_ax(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G,
   }
   T wr = 0, ws = 0, wt = 0;
   if (valid) {
-    const T* Ge = G + (size_t)e * 6 * NP + p;
-    const T g00 = Ge[0], g01 = Ge[NP], g02 = Ge[2 * NP];
-    const T g11 = Ge[3 * NP], g12 = Ge[4 * NP], g22 = Ge[5 * NP];
     wr = g00 * ur + g01 * us + g02 * ut;
     ws = g01 * ur + g11 * us + g12 * ut;
     wt = g02 * ur + g12 * us + g22 * ut;

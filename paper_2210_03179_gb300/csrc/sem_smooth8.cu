@@ -24,17 +24,22 @@
 // takes items b, b + grid, b + 2 grid, ... in turn.  The launch is cooperative (every block
 // resident), so the oldest unfinished item is always held by a running block whose dependencies
 // are done: no deadlock.  Phase p + 1 runs three planes behind phase p, so y and the vectors are
-// read again soon after they were written.  A block knows its next item in advance: it starts
-// the TMA copy of an operator item's geometric factors into a second buffer and reads the next
-// item's dependency counters (relaxed loads) while it works on the current one, so a dependency
-// that is complete by then costs no round trip.  Every wait is bounded (2 s): on timeout the
-// block records the error and all blocks leave, after waiting (bounded) for their own copies in
-// flight.
+// read again soon after they were written.
 //
-// Vectors written in this launch are read with ld.global.cg (L2, never a stale L1 line).  A work
-// item's completion is published by a block barrier and one release increment of its task's
-// counter, and observed by relaxed or acquire loads followed by an acquire fence and a block
-// barrier.
+// Warp specialisation.  The compute warps of a block never wait on bookkeeping: one control
+// lane (its own warp) reads dependency counters, starts the TMA copy of an operator item's
+// geometric factors into one of two shared-memory buffers, hands items over through two
+// mbarrier slots and publishes completions, up to two items ahead of the compute warps.  Every
+// wait is bounded (2 s for a dependency, 4 s without progress): on timeout the error flag is
+// raised, every block stops after its current item, and copies in flight are waited for
+// (bounded) before a block leaves.
+//
+// Memory ordering.  Vectors written in this launch are read with ld.global.cg (L2, never a stale
+// L1 line).  A finished item: compute warps' writes, named barrier, mbarrier arrival (release,
+// CTA scope), the control lane's wait (acquire, CTA scope) and its release increment of the
+// task counter at GPU scope.  A dependency: relaxed load of the counter, acquire fence, the
+// descriptor written to shared memory and the slot's mbarrier arrival (release, CTA scope),
+// the compute warps' wait (acquire, CTA scope).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,12 +60,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -72,19 +71,6 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 }
 
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-// Waits until *cnt >= target (thread 0 only).  False if the error flag is raised meanwhile or
-// the wait runs out.
-__device__ bool wait_count(const unsigned* cnt, unsigned target, const unsigned* err) {
-  if (ld_acquire(cnt) >= target) return true;
-  const unsigned long long t0 = global_ns();
-  for (;;) {
-    __nanosleep(100);
-    if (ld_acquire(cnt) >= target) return true;
-    if (*(volatile const unsigned*)err) return false;
-    if (global_ns() - t0 > kFusedWaitNs) return false;
-  }
-}
 
 __device__ __forceinline__ unsigned* cnt1(const FusedSmooth& a, int p, int s) {
   return a.ctl + 2 + 2 * (p * a.nslab + s);
@@ -279,7 +265,7 @@ template <typename T, int NT>
 __device__ void pointwise(const FusedSmooth& a, const PointOp<T>& f, int64_t lo, int64_t hi) {
   using V = typename Vec16<T>::type;
   constexpr int L = Vec16<T>::L;
-  constexpr int VPT = 4;
+  constexpr int VPT = 2;
   const unsigned rd = op_reads(f.op), wr = op_writes(f.op);
   T* X = static_cast<T*>(a.x);
   T* Rv = static_cast<T*>(a.r);
@@ -333,135 +319,233 @@ __device__ void pointwise(const FusedSmooth& a, const PointOp<T>& f, int64_t lo,
   }
 }
 
-template <typename T, int EB, bool PF>
-__global__ void __launch_bounds__(64 * EB) k_sem_smooth8(const __grid_constant__ FusedSmooth a) {
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// AND of `pred` over the nthreads threads of named barrier `id` (a barrier as well).
+__device__ __forceinline__ bool named_and(int id, int nthreads, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+// Non-blocking: has the phase of the given parity completed (acquire, CTA scope)?
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Warp roles: warps 0 .. 2 EB - 1 compute (64 threads per element), the last warp controls.
+// Work items of block b: b, b + grid, b + 2 grid, ...; item j of the block goes through slot
+// j mod 2: the control lane prepares it (dependencies complete, descriptor in shared memory,
+// for an operator item the TMA copy of its geometric factors into the slot's buffer) and
+// completes ready[slot] (its arrival plus the copy's bytes); the compute warps wait on
+// ready[slot], do the item and complete done[slot]; the control lane then publishes the item's
+// completion (release increment of its task counter).  The control lane never blocks on one
+// condition: it publishes finished items and prepares the next ones as each becomes possible,
+// so an item whose dependencies include this block's own earlier items cannot stall it.
+template <typename T, int EB>
+__global__ void __launch_bounds__(64 * EB + 32, 3) k_sem_smooth8(const __grid_constant__ FusedSmooth a) {
   using C = Ax8<T, EB>;
-  constexpr int R = C::R, P = C::P, NT = 64 * EB, NBUF = PF ? 2 : 1;
+  constexpr int R = C::R, P = C::P, NC = 64 * EB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ Item sh_item[2];   // [0] the item in progress, [1] the next one
-  __shared__ int sh_ok;
-  T* sG = reinterpret_cast<T*>(smem_raw);   // [NBUF][EB * GELEM]
-  T* sU = sG + NBUF * EB * C::GELEM;
+  __shared__ __align__(8) uint64_t ready[2], done[2];
+  __shared__ Item sh_item[2];
+  T* sG = reinterpret_cast<T*>(smem_raw);   // [2][EB * GELEM], buffer = slot
+  T* sU = sG + 2 * EB * C::GELEM;
   T* sR = sU + EB * C::STAGE;
   T* sS = sR + EB * C::STAGE;
   const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&ready[q])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done[q])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (tid >= NC) {
+    // ---------------- control lane ----------------
+    if (tid != NC) return;
+    const T* G = static_cast<const T*>(a.G);
+    uint32_t w = blockIdx.x;
+    uint32_t jp = 0, jr = 0;       // next item to prepare / to publish
+    Item held[2] = {Item{0, 0, 0, 0}, Item{0, 0, 0, 0}};
+    bool ended = false;            // the terminating empty item is prepared
+    bool have_next = false;
+    Item nx{0, 0, 0, 0};
+    Deps nd{{nullptr, nullptr}, {0u, 0u}};
+    unsigned long long idle_since = global_ns(), dep_since = 0;
+    bool failed = false;
+    for (;;) {
+      bool progress = false;
+      // publish the completion of the oldest item in the compute warps' hands
+      if (jr < jp && held[jr & 1].kind != 0 && mbar_try_wait(&done[jr & 1], (jr >> 1) & 1u)) {
+        const Item& it = held[jr & 1];
+        red_release_add(it.kind == 1 ? cnt1(a, it.p, it.s) : cnt2(a, it.p, it.s), 1u);
+        ++jr;
+        progress = true;
+      }
+      // prepare the next item once its slot is free and its dependencies are complete
+      if (!ended && jp < jr + 2) {
+        if (!have_next) {
+          nx = *(volatile const unsigned*)a.err ? Item{0, 0, 0, 0} : decode(a, w);
+          w += gridDim.x;
+          nd = deps_of(a, nx);
+          have_next = true;
+          dep_since = global_ns();
+        }
+        bool ok = true;
+        for (int q = 0; q < 2; ++q)
+          if (nd.c[q] && ld_relaxed(nd.c[q]) < nd.t[q]) ok = false;
+        if (!ok && (global_ns() - dep_since > kFusedWaitNs || *(volatile const unsigned*)a.err)) {
+          failed = true;   // give up: hand the compute warps the empty item
+          nx = Item{0, 0, 0, 0};
+          ok = true;
+        }
+        if (ok) {
+          fence_acq_rel();   // acquire side of the counters observed above
+          const int slot = jp & 1;
+          sh_item[slot] = nx;
+          held[slot] = nx;
+          if (nx.kind == 1) {
+            const int64_t e0 = (int64_t)nx.s * a.spp + (int64_t)nx.k * EB;
+            const int nv = min(EB, a.spp - nx.k * EB);
+            const uint32_t bytes = (uint32_t)(nv * C::GELEM * sizeof(T));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&ready[slot])),
+                         "r"(bytes)
+                         : "memory");
+            bulk_copy_g(sG + slot * EB * C::GELEM, G + e0 * C::GELEM, bytes, &ready[slot]);
+          } else {
+            mbar_arrive(&ready[slot]);
+          }
+          if (nx.kind == 0) ended = true;
+          ++jp;
+          have_next = false;
+          progress = true;
+        }
+      }
+      // done when every prepared item is published (the empty item needs none)
+      if (ended && jr + 1 == jp) break;
+      if (progress) {
+        idle_since = global_ns();
+      } else {
+        if (global_ns() - idle_since > 2 * kFusedWaitNs) {   // the compute warps stopped answering
+          failed = true;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (failed) {
+      atomicExch(a.err, 1u);
+      // copies still in flight land before the block's shared memory is released
+      for (uint32_t j = jr; j < jp; ++j)
+        if (held[j & 1].kind == 1)
+          for (uint32_t t = 0; t < kWaitLimit; ++t)
+            if (mbar_try_wait(&ready[j & 1], (j >> 1) & 1u)) break;
+    }
+    return;
+  }
+
+  // ---------------- compute warps ----------------
   const int le = tid >> 6, tt = tid & 63, ca = tt & 7, cb = tt >> 3;
-  const T* G = static_cast<const T*>(a.G);
   T* Y = static_cast<T*>(a.y);
   T* su = sU + le * C::STAGE;
   T* sr = sR + le * C::STAGE;
   T* ss = sS + le * C::STAGE;
-
-  // thread 0: operator items decoded so far (their buffer is that count mod NBUF) and copies
-  // issued but not yet waited for
-  int p1dec = 0;
-  unsigned pend = 0;   // bit q: a copy into buffer q is in flight
-  // all threads: operator items processed so far, parity of the next wait on each buffer
-  int p1seq = 0;
-  uint32_t par = 0;
-
-  auto issue = [&](const Item& it) {   // thread 0: TMA of the item's geometric factors
-    const int buf = p1dec % NBUF;
-    ++p1dec;
-    const int64_t e0 = (int64_t)it.s * a.spp + (int64_t)it.k * EB;
-    const int nv = min(EB, a.spp - it.k * EB);
-    const uint32_t bytes = (uint32_t)(nv * C::GELEM * sizeof(T));
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[buf])), "r"(bytes)
-                 : "memory");
-    bulk_copy_g(sG + buf * EB * C::GELEM, G + e0 * C::GELEM, bytes, &bar[buf]);
-    pend |= 1u << buf;
+  // The next operator item's gather, started while the current item is worked on when that item
+  // is already handed over (its dependencies are complete, so its source values are final).
+  // Per thread: each thread gathers its own column.
+  uint32_t gn[8];
+  T cn[8];
+  bool pref = false;
+  auto gather = [&](const Item& it, uint32_t (&g)[8], T (&col)[8]) {
+    const T* src = static_cast<const T*>(a.ph[it.p].src == FSRC_X ? a.x : a.d);
+    const int64_t e = (int64_t)it.s * a.spp + (int64_t)it.k * EB + le;
+    column_ids<true>(nullptr, a.lat, e, it.k * EB + le < a.spp, ca, cb, g);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) col[k] = (g[k] & kGidDirichlet) ? T(0) : __ldcg(src + (g[k] & kGidMask));
   };
-  // thread 0: the work items of this block are blockIdx.x, blockIdx.x + gridDim.x, ... (every
-  // block is resident: cooperative launch); the next item's dependency counters are read one
-  // item ahead with relaxed loads, so a dependency that is already complete costs no round trip
-  uint32_t w = blockIdx.x;
-  Deps cd{{nullptr, nullptr}, {0u, 0u}}, nd = cd;
-  unsigned cv[2] = {0u, 0u}, nv[2] = {0u, 0u};
-  auto item_at = [&](uint32_t idx) -> Item {
-    if (*(volatile const unsigned*)a.err) return Item{0, 0, 0, 0};   // another block gave up
-    return decode(a, idx);
-  };
-
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const Item it = item_at(w);
-    sh_item[0] = it;
-    if (it.kind == 1) issue(it);
-    cd = deps_of(a, it);
-    for (int q = 0; q < 2; ++q) cv[q] = cd.c[q] ? ld_relaxed(cd.c[q]) : 0u;
-  }
-  __syncthreads();
-
-  bool failed = false;
-  for (;;) {
-    const Item cur = sh_item[0];
-    if (cur.kind == 0) break;
-    if (tid == 0) {
-      w += gridDim.x;
-      const Item nx = item_at(w);
-      sh_item[1] = nx;
-      if (PF && nx.kind == 1) issue(nx);
-      nd = deps_of(a, nx);
-      for (int q = 0; q < 2; ++q) nv[q] = nd.c[q] ? ld_relaxed(nd.c[q]) : 0u;
-      // this item's dependencies: complete when read one item ago, else poll
-      bool ok = true;
-      for (int q = 0; q < 2 && ok; ++q)
-        if (cd.c[q] && cv[q] < cd.t[q]) ok = wait_count(cd.c[q], cd.t[q], a.err);
-      fence_acq_rel();   // acquire side of the counters observed above
-      sh_ok = ok ? 1 : 0;
+  auto prefetch_next = [&](uint32_t j) {
+    const int ns = (j + 1) & 1;
+    pref = false;
+    if (mbar_test(&ready[ns], ((j + 1) >> 1) & 1u)) {
+      const Item nx = sh_item[ns];
+      if (nx.kind == 1) {
+        gather(nx, gn, cn);
+        pref = true;
+      }
     }
-    __syncthreads();
-    if (!sh_ok) {
-      failed = true;
+  };
+  for (uint32_t j = 0;; ++j) {
+    const int slot = j & 1;
+    bool ok = false;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+      if (mbar_try_wait(&ready[slot], (j >> 1) & 1u)) {
+        ok = true;
+        break;
+      }
+      if (global_ns() - t0 > 2 * kFusedWaitNs) break;
+    }
+    if (!named_and(1, NC, ok)) {
+      if (tid == 0) atomicExch(a.err, 1u);
       break;
     }
+    const Item cur = sh_item[slot];
+    if (cur.kind == 0) break;
     const FusedPhase& ph = a.ph[cur.p];
     if (cur.kind == 1) {
       // ---- operator on EB elements of plane cur.s: y += A v ----
-      const T* src = static_cast<const T*>(ph.src == FSRC_X ? a.x : a.d);
-      const int64_t e = (int64_t)cur.s * a.spp + (int64_t)cur.k * EB + le;
-      const bool valid = cur.k * EB + le < a.spp;
       uint32_t g[8];
-      column_ids<true>(nullptr, a.lat, e, valid, ca, cb, g);
       T col[8];
+      if (pref) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) col[k] = (g[k] & kGidDirichlet) ? T(0) : __ldcg(src + (g[k] & kGidMask));
+        for (int k = 0; k < 8; ++k) {
+          g[k] = gn[k];
+          col[k] = cn[k];
+        }
+      } else {
+        gather(cur, g, col);
+      }
+      prefetch_next(j);
 #pragma unroll
       for (int k = 0; k < 8; ++k) su[k * P + cb * R + ca] = col[k];
       T ut[8];
       line8<T, 0>(col, ut);
-      __syncthreads();
+      named_sync(1, NC);
       {
         T v[8], o[8];
         ld_row(su + cb * P + ca * R, v);
         line8<T, 0>(v, o);
         st_row(sr + cb * P + ca * R, o);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = su[cb * P + j * R + ca];
+        for (int jj = 0; jj < 8; ++jj) v[jj] = su[cb * P + jj * R + ca];
         line8<T, 0>(v, o);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) ss[cb * P + j * R + ca] = o[j];
+        for (int jj = 0; jj < 8; ++jj) ss[cb * P + jj * R + ca] = o[jj];
       }
-      const int buf = p1seq % NBUF;
-      const uint32_t pr = (par >> buf) & 1u;
-      bool gok = false;
-      for (uint32_t w = 0; w < kWaitLimit; ++w)
-        if (mbar_try_wait(&bar[buf], pr)) {
-          gok = true;
-          break;
-        }
-      if (!__syncthreads_and(gok ? 1 : 0)) {
-        failed = true;
-        break;
-      }
-      par ^= 1u << buf;
-      ++p1seq;
-      if (tid == 0) pend &= ~(1u << buf);
+      named_sync(1, NC);   // the r and s passes wrote points that other threads read next
       T wt[8];
-      const T* gG = sG + buf * EB * C::GELEM + le * C::GELEM;
+      const T* gG = sG + slot * EB * C::GELEM + le * C::GELEM;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int p = k * 64 + cb * 8 + ca;
@@ -475,82 +559,63 @@ __global__ void __launch_bounds__(64 * EB) k_sem_smooth8(const __grid_constant__
       }
       T yt[8];
       line8<T, 1>(wt, yt);
-      __syncthreads();
+      named_sync(1, NC);
       {
         T v[8], o[8];
         ld_row(sr + cb * P + ca * R, v);
         line8<T, 1>(v, o);
         st_row(su + cb * P + ca * R, o);
       }
-      __syncthreads();
+      named_sync(1, NC);
       {
         T v[8], o[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = ss[cb * P + j * R + ca];
+        for (int jj = 0; jj < 8; ++jj) v[jj] = ss[cb * P + jj * R + ca];
         line8<T, 1>(v, o);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) su[cb * P + j * R + ca] += o[j];
+        for (int jj = 0; jj < 8; ++jj) su[cb * P + jj * R + ca] += o[jj];
       }
-      __syncthreads();
+      named_sync(1, NC);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const T v = su[k * P + cb * R + ca] + yt[k];
         if (!(g[k] & kGidDirichlet)) atomicAdd(&Y[g[k] & kGidMask], v);
       }
-      __syncthreads();   // every thread's additions precede the release below
-      if (tid == 0) red_release_add(cnt1(a, cur.p, cur.s), 1u);
     } else {
       // ---- pointwise operation on chunk cur.k of slab cur.s's nodes ----
       const int64_t s0 = slab_start(a, cur.s), s1 = slab_start(a, cur.s + 1);
       const int64_t lo = s0 + (int64_t)cur.k * a.chunk;
       const int64_t hi = lo + a.chunk < s1 ? lo + a.chunk : s1;
+      prefetch_next(j);
       if (lo < hi) {
         PointOp<T> f{ph.op, (T)ph.c[0], (T)ph.c[1], (T)ph.c[2], (T)ph.c[3]};
-        pointwise<T, NT>(a, f, lo, hi);
+        pointwise<T, NC>(a, f, lo, hi);
       }
-      __syncthreads();   // every thread's stores precede the release below
-      if (tid == 0) red_release_add(cnt2(a, cur.p, cur.s), 1u);
     }
-    __syncthreads();   // the item is done in every thread; sh_item[1] is written
-    if (tid == 0) {
-      const Item nx = sh_item[1];
-      sh_item[0] = nx;
-      if (!PF && nx.kind == 1) issue(nx);
-      cd = nd;
-      cv[0] = nv[0];
-      cv[1] = nv[1];
-    }
-    __syncthreads();
-  }
-  if (failed && tid == 0) {
-    atomicExch(a.err, 1u);
-    // copies still in flight land before the block's shared memory is released
-    for (int q = 0; q < NBUF; ++q)
-      if (pend & (1u << q))
-        for (uint32_t w = 0; w < kWaitLimit; ++w)
-          if (mbar_try_wait(&bar[q], (par >> q) & 1u)) break;
+    named_sync(1, NC);   // the item is done in every compute thread (stage buffers free)
+    if (tid == 0) mbar_arrive(&done[slot]);
   }
 }
 
-template <typename T, int EB, bool PF>
+template <typename T, int EB>
 bool launch_fused(FusedSmooth& a, cudaStream_t s) {
   using C = Ax8<T, EB>;
-  const size_t smem = sizeof(T) * (size_t)EB * ((PF ? 2 : 1) * C::GELEM + 3 * C::STAGE);
+  const size_t smem = sizeof(T) * (size_t)EB * (2 * C::GELEM + 3 * C::STAGE);
   static int grid = 0;
   if (grid == 0) {
-    cudaFuncSetAttribute(k_sem_smooth8<T, EB, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sem_smooth8<T, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_smooth8<T, EB, PF>, 64 * EB, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_smooth8<T, EB>, 64 * EB + 32, smem);
     grid = sms * (per_sm > 0 ? per_sm : 1);
   }
   cudaMemsetAsync(a.ctl, 0, sizeof(unsigned) * (size_t)fused_ctl_words(a.lat), s);
   const unsigned blocks = (unsigned)std::min<int64_t>(grid, std::max<int64_t>(a.total, 1));
   // cooperative: every block is resident, which the static schedule's waits rely on
   void* args[] = {(void*)&a};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sem_smooth8<T, EB, PF>, dim3(blocks),
-                                                    dim3(64 * EB), args, smem, s);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sem_smooth8<T, EB>, dim3(blocks),
+                                                    dim3(64 * EB + 32), args, smem, s);
   if (e != cudaSuccess) return false;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return true;
@@ -600,13 +665,13 @@ bool fused_plan(FusedSmooth& a, int variant) {
 template <>
 bool sem_smooth8<float>(FusedSmooth& a, int variant, cudaStream_t s) {
   (void)variant;
-  return launch_fused<float, 2, true>(a, s);
+  return launch_fused<float, 2>(a, s);
 }
 
 template <>
 bool sem_smooth8<double>(FusedSmooth& a, int variant, cudaStream_t s) {
-  if (variant == 3) return launch_fused<double, 1, true>(a, s);
-  return launch_fused<double, 1, false>(a, s);
+  (void)variant;
+  return launch_fused<double, 1>(a, s);
 }
 
 cudaError_t sem_smooth8_set_eo(const double* eo) {

@@ -85,13 +85,23 @@ k_restrict_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ rf, T* _
   T* A = sA[le];
   T* B = sB[le];
   T* C = sC[le];
-  // fine values at owned, non-Dirichlet copies
-  for (int p = t; p < QF * QF * QF; p += 64) {
-    const int i = p % QF, j = (p / QF) % QF, k = p / (QF * QF);
-    bool dir, own;
-    const uint32_t g = lattice_id(Lf, NF, c, i, j, k, dir, own);
-    A[p] = (valid && own && !dir) ? rf[g] : T(0);
+  // fine values at owned, non-Dirichlet copies: every load of the thread in flight at once
+  constexpr int NP = (QF * QF * QF + 63) / 64;
+  T fv[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int p = t + 64 * q;
+    fv[q] = T(0);
+    if (p < QF * QF * QF) {
+      const int i = p % QF, j = (p / QF) % QF, k = p / (QF * QF);
+      bool dir, own;
+      const uint32_t g = lattice_id(Lf, NF, c, i, j, k, dir, own);
+      if (valid && own && !dir) fv[q] = rf[g];
+    }
   }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+    if (t + 64 * q < QF * QF * QF) A[t + 64 * q] = fv[q];
   __syncthreads();
   // along i: line (j, k) -> QC outputs
   for (int l = t; l < QF * QF; l += 64) {
@@ -199,19 +209,30 @@ k_prolong_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ zc, T* __
     T v[QC];
 #pragma unroll
     for (int k = 0; k < QC; ++k) v[k] = C[(k * QF + jF) * QF + iF];
+    // the column's ids and (accumulate) old values first: all loads in flight at once instead
+    // of one load-store round trip per output
+    uint32_t g[QF];
+    bool wr[QF], dz[QF];
+    T old[QF];
 #pragma unroll
     for (int kF = 0; kF < QF; ++kF) {
       bool dir, own;
-      const uint32_t g = lattice_id(Lf, NF, c, iF, jF, kF, dir, own);
-      if (!valid || !own) continue;
-      if (dir) {
-        if (!accumulate) zf[g] = T(0);
+      g[kF] = lattice_id(Lf, NF, c, iF, jF, kF, dir, own);
+      wr[kF] = valid && own;
+      dz[kF] = dir;
+      old[kF] = (accumulate && wr[kF] && !dir) ? zf[g[kF]] : T(0);
+    }
+#pragma unroll
+    for (int kF = 0; kF < QF; ++kF) {
+      if (!wr[kF]) continue;
+      if (dz[kF]) {
+        if (!accumulate) zf[g[kF]] = T(0);
         continue;
       }
       T acc = 0;
 #pragma unroll
       for (int k = 0; k < QC; ++k) acc += Jv<T, QF, QC>(kF, k) * v[k];
-      zf[g] = accumulate ? zf[g] + acc : acc;
+      zf[g[kF]] = accumulate ? old[kF] + acc : acc;
     }
   }
 }
