@@ -563,6 +563,8 @@ def main():
                          "range 'smooth' and exit")
     ap.add_argument("--tile", type=int, default=None,
                     help="profiling runs only: force this order-7 kernel variant on the fine level")
+    ap.add_argument("--fused", action="store_true",
+                    help="profiling runs only (--profile-smoother): force the fused smoother kernel on the fine level")
     ap.add_argument("--profile-outer", choices=["fp64", "f32x2"], default=None,
                     help="apply only the outer operator (FP64 or FP32 pairs) twice, the second inside an "
                          "NVTX range 'outer' (for ncu)")
@@ -658,6 +660,8 @@ def main():
         bb = xb.clone().uniform_(-1, 1)
         if args.tile is not None:
             cm.chebmg_set_tile_choice(s.ctx, 0, dt, args.tile)
+        if args.fused:
+            cm.chebmg_set_fused_smoother(s.ctx, 0, dt, 1 if f32 else 2)
         cm.chebmg_smooth(s.ctx, 0, dt, bb, xb, 9, True)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("smooth")
@@ -665,7 +669,8 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile_smoother": args.profile_smoother,
-                          "elements_per_block": cm.chebmg_tile_choice(s.ctx, 0, dt)}))
+                          "elements_per_block": cm.chebmg_tile_choice(s.ctx, 0, dt),
+                          "fused_variant": cm.chebmg_fused_smoother(s.ctx, 0, dt)}))
         s32.close()
         s64.close()
         return 0

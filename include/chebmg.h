@@ -133,9 +133,10 @@ int chebmg_lambda_max(const chebmg_ctx* ctx, int level, double* out);
 int chebmg_launch_count(const chebmg_ctx* ctx, int64_t* count);
 /* Variant chosen by the setup-time autotuner for the order-7 element operator on `level`
  * in `dtype`: 1, 2 or 4 elements per thread block, or 12 / 14 for the persistent pipelined
- * kernel with 2 / 4 elements per block; +100 when global ids are computed from the box
- * lattice instead of read from the element-to-global map (0 if the level does not use
- * that kernel). */
+ * kernel with 2 / 4 elements per block, or 21 / 22 for 1 / 2 elements per block with the
+ * geometric factors read from global memory where used (no shared-memory copy: more blocks
+ * per SM); +100 when global ids are computed from the box lattice instead of read from the
+ * element-to-global map (0 if the level does not use that kernel). */
 int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* elements_per_block);
 /* Overrides that choice (same codes); EINVAL for other levels or codes. */
 /* SEM coarse solver: PCG whose preconditioner is Algorithm 2 (4th kind, beta = 1) of
@@ -284,8 +285,9 @@ int chebmg_vcycle_batched(chebmg_ctx* ctx, int nrhs, const double* R, double* Z)
 
 /* Autotuned choices for batches of nrhs (allocating and tuning as the first batched solve
  * would): *variant = 1000 * right-hand sides per block + (100 if global ids come from the
- * box lattice) + elements per block of the batched order-7 operator on `level` (0 for other
- * levels or nrhs = 1); *coarse_degree = degree of the Algorithm 2 preconditioner of the
+ * box lattice) + elements per block of the batched order-7 operator on `level` (1, 2, 4; or
+ * 11, 12 for 1 or 2 elements with the right-hand sides taken two at a time through every
+ * line pass, at least 2 per block) (0 for other levels or nrhs = 1); *coarse_degree = degree of the Algorithm 2 preconditioner of the
  * per-right-hand-side coarse CG (0 if the coarsest level is not solved that way). */
 int chebmg_batch_info(chebmg_ctx* ctx, int nrhs, int level, int dtype, int* variant,
                       int* coarse_degree);

@@ -878,7 +878,7 @@ void autotune_ax8(chebmg_ctx* c, int j) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_eb = 2;
-  for (int eb : {1, 2, 4, 12, 14, 101, 102, 104, 112, 114}) {
+  for (int eb : {1, 2, 4, 12, 14, 21, 22, 101, 102, 104, 112, 114, 121, 122}) {
     if (!sem_ax8_variant_fits<T>(eb)) continue;
     if (eb >= 100 && !L.boxed) continue;   // lattice ids need the box lattice
     L.eb[dt] = eb;
@@ -1238,11 +1238,11 @@ void autotune_batch(chebmg_ctx* c, int nrhs) {
         int best_v = L.beb[dt];
         for (int rb : {1, 2, 4, 8, 16}) {
           if (rb > nrhs) break;
-          for (int eb : {1, 2, 4, 101, 102, 104}) {
+          for (int eb : {1, 2, 4, 101, 102, 104, 11, 12, 111, 112}) {
             if (eb >= 100 && !L.boxed) continue;
+            if (eb % 100 >= 10 && rb < 2) continue;   // pairs of right-hand sides
             const int v = 1000 * rb + eb;
-            if (dt == CHEBMG_F64 ? !sem_ax8_variant_fits<double>(eb % 100) : !sem_ax8_variant_fits<float>(eb % 100))
-              continue;
+            if (dt == CHEBMG_F64 ? !sem_ax8_batched_fits<double>(v) : !sem_ax8_batched_fits<float>(v)) continue;
             L.beb[dt] = v;
             const float t = time_it(
                 [&]() {
@@ -2382,7 +2382,7 @@ int chebmg_set_tile_choice(chebmg_ctx* c, int level, int dtype, int variant) {
   if (L.type != TYPE_SEM || L.Q != 8) return CHEBMG_EINVAL;
   const int base = variant % 100;
   if ((variant != base && variant != base + 100) ||
-      (base != 1 && base != 2 && base != 4 && base != 12 && base != 14))
+      (base != 1 && base != 2 && base != 4 && base != 12 && base != 14 && base != 21 && base != 22))
     return CHEBMG_EINVAL;
   const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(variant) : sem_ax8_variant_fits<float>(variant);
   if (!fits || (variant >= 100 && !L.boxed)) return CHEBMG_EINVAL;
@@ -2800,9 +2800,11 @@ int chebmg_set_batch_tile_choice(chebmg_ctx* c, int nrhs, int level, int dtype, 
     check_dtype(c, dtype);
     if (L.type != TYPE_SEM || L.Q != 8 || nrhs < 2 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "no batched variant");
     const int rb = variant / 1000, rest = variant % 1000, eb = rest % 100;
-    if (rb < 1 || rb > 64 || (rest != eb && rest != eb + 100) || (eb != 1 && eb != 2 && eb != 4))
+    const bool paired = eb == 11 || eb == 12;
+    if (rb < 1 || rb > 64 || (rest != eb && rest != eb + 100) || (eb != 1 && eb != 2 && eb != 4 && !paired) ||
+        (paired && rb < 2))
       throw Error(CHEBMG_EINVAL, "bad batched variant");
-    const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(eb) : sem_ax8_variant_fits<float>(eb);
+    const bool fits = dtype == CHEBMG_F64 ? sem_ax8_batched_fits<double>(variant) : sem_ax8_batched_fits<float>(variant);
     if (!fits || (dtype == CHEBMG_F32 && !L.G[CHEBMG_F32]) || (rest >= 100 && !L.boxed))
       throw Error(CHEBMG_EINVAL, "variant not available");
     reserve_batch(c, nrhs);

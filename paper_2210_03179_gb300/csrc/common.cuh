@@ -74,13 +74,17 @@ void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, con
              unsigned* err, int variant, cudaStream_t s);
 // Batched form: nb right-hand sides at leading dimension ld.  variant = 1000 * RB + (100 if
 // implicit ids) + EB: a block stages the geometric factors of EB elements once and applies them
-// to RB right-hand sides.
+// to RB right-hand sides; EB + 10 (EB 1 or 2) takes the right-hand sides two at a time through
+// each line pass (RB at least 2).
 template <typename T>
 void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
                      unsigned* err, int variant, int nb, int64_t ld, cudaStream_t s);
 // Whether variant `eb` fits the device's per-block shared-memory limit.
 template <typename T>
 bool sem_ax8_variant_fits(int eb);
+// The same for a batched variant code.
+template <typename T>
+bool sem_ax8_batched_fits(int variant);
 
 // ---- fused smoother on an order-7 box-lattice level (sem_smooth8.cu) ----
 // One persistent launch runs a sequence of phases; a phase is an optional element operator

@@ -144,6 +144,92 @@ k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __r
   }
 }
 
+// Variant without the shared-memory copy of the geometric factors: each point's six factors
+// are read from global memory in the step that uses them (coalesced across the element's
+// threads).  Only the three stage buffers stay in shared memory, so several times more blocks
+// are resident per SM -- for the FP64 form, bound by its FP64 issue rate, more warps ready to
+// issue while others gather or scatter.
+template <typename T, int EB_, bool IMPLICIT>
+__global__ void __launch_bounds__(64 * EB_)
+k_sem_ax8g(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
+           const T* __restrict__ u, T* __restrict__ y) {
+  using C = Ax8<T, EB_>;
+  constexpr int R = C::R, P = C::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  T* sR = sU + EB_ * C::STAGE;
+  T* sS = sR + EB_ * C::STAGE;
+  const int tid = threadIdx.x;
+  const int le = tid >> 6, t = tid & 63, a = t & 7, b = t >> 3;
+  const int64_t e = (int64_t)blockIdx.x * EB_ + le;
+  const bool valid = e < E;
+  T* su = sU + le * C::STAGE;
+  T* sr = sR + le * C::STAGE;
+  T* ss = sS + le * C::STAGE;
+  uint32_t g[8];
+  T col[8];
+  column_ids<IMPLICIT>(gid, lat, e, valid, a, b, g);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    col[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
+    su[k * P + b * R + a] = col[k];
+  }
+  T ut[8];
+  line8<T, 0>(col, ut);
+  __syncthreads();
+  {
+    T v[8], o[8];
+    ld_row(su + b * P + a * R, v);
+    line8<T, 0>(v, o);
+    st_row(sr + b * P + a * R, o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = su[b * P + j * R + a];
+    line8<T, 0>(v, o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ss[b * P + j * R + a] = o[j];
+  }
+  __syncthreads();
+  T wt[8];
+  const T* gG = G + (valid ? e : 0) * C::GELEM;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int p = k * 64 + b * 8 + a;
+    const int q = k * P + b * R + a;
+    const T ur = sr[q], us = ss[q], utk = ut[k];
+    const T g00 = __ldg(gG + p), g01 = __ldg(gG + 512 + p), g02 = __ldg(gG + 1024 + p);
+    const T g11 = __ldg(gG + 1536 + p), g12 = __ldg(gG + 2048 + p), g22 = __ldg(gG + 2560 + p);
+    sr[q] = g00 * ur + g01 * us + g02 * utk;
+    ss[q] = g01 * ur + g11 * us + g12 * utk;
+    wt[k] = g02 * ur + g12 * us + g22 * utk;
+  }
+  T yt[8];
+  line8<T, 1>(wt, yt);
+  __syncthreads();
+  {
+    T v[8], o[8];
+    ld_row(sr + b * P + a * R, v);
+    line8<T, 1>(v, o);
+    st_row(su + b * P + a * R, o);
+  }
+  __syncthreads();
+  {
+    T v[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = ss[b * P + j * R + a];
+    line8<T, 1>(v, o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) su[b * P + j * R + a] += o[j];
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const T v = su[k * P + b * R + a] + yt[k];
+      if (!(g[k] & kGidDirichlet)) atomicAdd(&y[g[k] & kGidMask], v);
+    }
+  }
+}
+
 // Persistent, software-pipelined variant: each block walks batches of EB elements
 // (blockIdx.x, blockIdx.x + gridDim.x, ...).  While it computes batch i, the TMA copy of
 // batch i+1's geometric factors runs into the second buffer and batch i+1's gather
@@ -412,6 +498,156 @@ k_sem_ax8b(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
   }
 }
 
+// Paired batched variant: like k_sem_ax8b, but every line pass works on two right-hand sides
+// at once (q and q + 1): each thread carries two independent lines through each contraction,
+// the geometric factors read from shared memory serve both, and a block barrier covers two
+// right-hand sides instead of one.  Stage buffers for both live in shared memory.
+template <typename T, int EB, bool IMPLICIT>
+__global__ void __launch_bounds__(64 * EB)
+k_sem_ax8b2(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
+            const T* __restrict__ u, T* __restrict__ y, unsigned* __restrict__ err, int nb, int64_t ld, int rb) {
+  using C = Ax8<T, EB>;
+  constexpr int R = C::R, P = C::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* sG = reinterpret_cast<T*>(smem_raw);
+  T* sStage = sG + EB * C::GELEM;   // [2 right-hand sides][3 stages][EB][STAGE]
+  const int tid = threadIdx.x;
+  const int le = tid >> 6, t = tid & 63, a = t & 7, b = t >> 3;
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((E - e0) < EB ? (E - e0) : EB);
+  const bool valid = le < nvalid;
+  const int64_t e = e0 + le;
+  const int q0 = blockIdx.y * rb;
+  const int q1 = q0 + rb < nb ? q0 + rb : nb;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t bytes = (uint32_t)(nvalid * C::GELEM * sizeof(T));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)), "r"(bytes)
+                 : "memory");
+    bulk_copy_g(sG, G + e0 * C::GELEM, bytes, &bar);
+  }
+  T* su[2];
+  T* sr[2];
+  T* ss[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    su[h] = sStage + ((h * 3 + 0) * EB + le) * C::STAGE;
+    sr[h] = sStage + ((h * 3 + 1) * EB + le) * C::STAGE;
+    ss[h] = sStage + ((h * 3 + 2) * EB + le) * C::STAGE;
+  }
+  uint32_t g[8];
+  column_ids<IMPLICIT>(gid, lat, e, valid, a, b, g);
+  auto gather = [&](int q, T (&v)[8]) {
+    const T* uq = u + (int64_t)q * ld;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (q < q1 && !(g[k] & kGidDirichlet)) ? uq[g[k] & kGidMask] : T(0);
+  };
+  T col[2][8];
+  gather(q0, col[0]);
+  gather(q0 + 1, col[1]);
+  for (int q = q0; q < q1; q += 2) {
+    T ut[2][8], cn[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) su[h][k * P + b * R + a] = col[h][k];
+      line8<T, 0>(col[h], ut[h]);
+    }
+    gather(q + 2, cn[0]);        // the next pair's loads overlap this pair's work
+    gather(q + 3, cn[1]);
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      T v[8], o[8];
+      ld_row(su[h] + b * P + a * R, v);
+      line8<T, 0>(v, o);
+      st_row(sr[h] + b * P + a * R, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = su[h][b * P + j * R + a];
+      line8<T, 0>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ss[h][b * P + j * R + a] = o[j];
+    }
+    if (q == q0) {               // geometric factors must have landed (once per block)
+      bool ok = false;
+      for (uint32_t w = 0; w < kWaitLimit; ++w)
+        if (mbar_try_wait(&bar, 0)) {
+          ok = true;
+          break;
+        }
+      if (!__syncthreads_and(ok ? 1 : 0)) {
+        if (tid == 0) atomicExch(err, 1u);
+        for (uint32_t w = 0; w < kWaitLimit; ++w)
+          if (mbar_try_wait(&bar, 0)) break;
+        return;
+      }
+    } else {
+      __syncthreads();           // the line passes above wrote points other threads read next
+    }
+    T wt[2][8];
+    const T* gG = sG + le * C::GELEM;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int p = k * 64 + b * 8 + a;
+      const int qq = k * P + b * R + a;
+      const T g00 = gG[p], g01 = gG[512 + p], g02 = gG[1024 + p];
+      const T g11 = gG[1536 + p], g12 = gG[2048 + p], g22 = gG[2560 + p];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const T ur = sr[h][qq], us = ss[h][qq], utk = ut[h][k];
+        sr[h][qq] = g00 * ur + g01 * us + g02 * utk;
+        ss[h][qq] = g01 * ur + g11 * us + g12 * utk;
+        wt[h][k] = g02 * ur + g12 * us + g22 * utk;
+      }
+    }
+    T yt[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) line8<T, 1>(wt[h], yt[h]);
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      T v[8], o[8];
+      ld_row(sr[h] + b * P + a * R, v);
+      line8<T, 1>(v, o);
+      st_row(su[h] + b * P + a * R, o);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      T v[8], o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = ss[h][b * P + j * R + a];
+      line8<T, 1>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) su[h][b * P + j * R + a] += o[j];
+    }
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (q + h >= q1) continue;
+        T* yq = y + (int64_t)(q + h) * ld;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const T v = su[h][k * P + b * R + a] + yt[h][k];
+          if (!(g[k] & kGidDirichlet)) atomicAdd(&yq[g[k] & kGidMask], v);
+        }
+      }
+    }
+    __syncthreads();             // stage buffers free for the next pair
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) col[h][k] = cn[h][k];
+  }
+}
+
 }  // namespace
 
 cudaError_t sem_ax8_set_D(const double* D) {
@@ -455,6 +691,21 @@ static void launch_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const
 }
 
 template <typename T, int EB, bool IM>
+static void launch_ax8g(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                        cudaStream_t s) {
+  using C = Ax8<T, EB>;
+  const size_t smem = sizeof(T) * (size_t)EB * 3 * C::STAGE;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_sem_ax8g<T, EB, IM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  const unsigned blocks = (unsigned)((E + EB - 1) / EB);
+  k_sem_ax8g<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+template <typename T, int EB, bool IM>
 static void launch_ax8p(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
                         unsigned* err, cudaStream_t s) {
   using C = Ax8<T, EB>;
@@ -490,6 +741,22 @@ static void launch_ax8b(int64_t E, const uint32_t* gid, const Lattice& lat, cons
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+template <typename T, int EB, bool IM>
+static void launch_ax8b2(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
+                         unsigned* err, int nb, int64_t ld, int rb, cudaStream_t s) {
+  using C = Ax8<T, EB>;
+  const size_t smem = sizeof(T) * (size_t)EB * (C::GELEM + 6 * C::STAGE);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_sem_ax8b2<T, EB, IM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  if (rb < 2) rb = 2;
+  const dim3 blocks((unsigned)((E + EB - 1) / EB), (unsigned)((nb + rb - 1) / rb));
+  k_sem_ax8b2<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y, err, nb, ld, rb);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 template <typename T>
 size_t sem_ax8_smem(int eb) {
   eb %= 100;
@@ -499,6 +766,18 @@ size_t sem_ax8_smem(int eb) {
     case 4: return sizeof(T) * 4 * (Ax8<T, 4>::GELEM + 3 * Ax8<T, 4>::STAGE);
     case 12: return sizeof(T) * 2 * (2 * Ax8<T, 2>::GELEM + 3 * Ax8<T, 2>::STAGE);
     case 14: return sizeof(T) * 4 * (2 * Ax8<T, 4>::GELEM + 3 * Ax8<T, 4>::STAGE);
+    case 21: return sizeof(T) * 1 * 3 * Ax8<T, 1>::STAGE;
+    case 22: return sizeof(T) * 2 * 3 * Ax8<T, 2>::STAGE;
+    default: return ~size_t(0);
+  }
+}
+
+// Shared memory of the paired batched variant with eb elements per block (1 or 2).
+template <typename T>
+size_t sem_ax8b2_smem(int eb) {
+  switch (eb) {
+    case 1: return sizeof(T) * 1 * (Ax8<T, 1>::GELEM + 6 * Ax8<T, 1>::STAGE);
+    case 2: return sizeof(T) * 2 * (Ax8<T, 2>::GELEM + 6 * Ax8<T, 2>::STAGE);
     default: return ~size_t(0);
   }
 }
@@ -515,6 +794,8 @@ template <typename T, bool IM>
 static void dispatch_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
                          unsigned* err, int eb, cudaStream_t s) {
   switch (eb) {
+    case 21: launch_ax8g<T, 1, IM>(E, gid, lat, G, u, y, s); break;
+    case 22: launch_ax8g<T, 2, IM>(E, gid, lat, G, u, y, s); break;
     case 1: launch_ax8<T, 1, IM>(E, gid, lat, G, u, y, err, s); break;
     case 4: launch_ax8<T, 4, IM>(E, gid, lat, G, u, y, err, s); break;
     case 12: launch_ax8p<T, 2, IM>(E, gid, lat, G, u, y, err, s); break;
@@ -535,7 +816,18 @@ void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T
                      unsigned* err, int variant, int nb, int64_t ld, cudaStream_t s) {
   const int rb = variant / 1000;
   const bool im = (variant % 1000) >= 100;
-  const int eb = variant % 100;
+  const bool pair = (variant % 100) >= 10;
+  const int eb = variant % 10;
+  if (pair) {
+    if (im) {
+      if (eb == 1) launch_ax8b2<T, 1, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+      else launch_ax8b2<T, 2, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+    } else {
+      if (eb == 1) launch_ax8b2<T, 1, false>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+      else launch_ax8b2<T, 2, false>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
+    }
+    return;
+  }
   if (im) {
     if (eb == 1) launch_ax8b<T, 1, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
     else if (eb == 4) launch_ax8b<T, 4, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
@@ -547,6 +839,18 @@ void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T
   }
 }
 
+template <typename T>
+bool sem_ax8_batched_fits(int variant) {
+  const int rest = variant % 100;
+  if (rest < 10) return sem_ax8_variant_fits<T>(rest);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return sem_ax8b2_smem<T>(rest % 10) + 256 <= (size_t)optin;
+}
+
+template bool sem_ax8_batched_fits<float>(int);
+template bool sem_ax8_batched_fits<double>(int);
 template bool sem_ax8_variant_fits<float>(int);
 template bool sem_ax8_variant_fits<double>(int);
 template void sem_ax8<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
