@@ -187,13 +187,22 @@ int chebmg_set_tile_choice(chebmg_ctx* ctx, int level, int dtype, int variant);
  * takes work items (elements of one element plane, or nodes of one plane range) in dependency
  * order, instead of two kernels per step.  Variant per level and dtype, chosen at setup by
  * timing against the separate kernels: 0 = separate kernels, 1 = FP32 (2 elements per work
- * item), 2 = FP64 (1 element per work item).  Single right-hand side only (batches run the
- * separate kernels).  Same results as the separate kernels up to the order of the atomic
- * sums. */
+ * item), 2 = FP64 (1 element per work item).  Batches have their own choice (below).  Same
+ * results as the separate kernels up to the order of the atomic sums. */
 int chebmg_fused_smoother(const chebmg_ctx* ctx, int level, int dtype, int* variant);
 /* Overrides that choice; EINVAL on other levels (not order 7, not a box lattice, the
  * coarsest) or a variant that does not match dtype. */
 int chebmg_set_fused_smoother(chebmg_ctx* ctx, int level, int dtype, int variant);
+/* The same for batches of nrhs right-hand sides (allocating and tuning as the first batched
+ * solve would): a work item of the fused kernel covers *rhs_per_item right-hand sides (the
+ * geometric factors of its elements staged once for all of them); *variant 0 = separate
+ * kernels (then *rhs_per_item = 0). */
+int chebmg_batch_fused_smoother(chebmg_ctx* ctx, int nrhs, int level, int dtype, int* variant,
+                                int* rhs_per_item);
+/* Overrides that choice for batches of nrhs (variant 0, 1 for FP32 or 2 for FP64;
+ * rhs_per_item 1..64); EINVAL as chebmg_set_fused_smoother. */
+int chebmg_set_batch_fused_smoother(chebmg_ctx* ctx, int nrhs, int level, int dtype, int variant,
+                                    int rhs_per_item);
 
 /* ---- per-level operators (device vectors, dtype as above) ---------------- */
 

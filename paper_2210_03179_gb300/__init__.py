@@ -90,6 +90,8 @@ _SIGNATURES = {
     "chebmg_set_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int]),
     "chebmg_fused_smoother": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
     "chebmg_set_fused_smoother": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "chebmg_batch_fused_smoother": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_int), POINTER(c_int)]),
+    "chebmg_set_batch_fused_smoother": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int]),
     "chebmg_set_coarse_precond_dtype": (c_int, [c_void_p, c_int, c_int]),
     "chebmg_lambda_min_ratio": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "chebmg_coarse_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
@@ -320,6 +322,19 @@ def chebmg_fused_smoother(ctx, level, dtype) -> int:
 
 def chebmg_set_fused_smoother(ctx, level, dtype, variant):
     _check(lib().chebmg_set_fused_smoother(ctx, int(level), int(dtype), int(variant)), "chebmg_set_fused_smoother")
+
+
+def chebmg_batch_fused_smoother(ctx, nrhs, level, dtype):
+    """(variant, right-hand sides per work item) of the fused smoother for batches of nrhs."""
+    v, g = c_int(), c_int()
+    _check(lib().chebmg_batch_fused_smoother(ctx, int(nrhs), int(level), int(dtype), byref(v), byref(g)),
+           "chebmg_batch_fused_smoother")
+    return v.value, g.value
+
+
+def chebmg_set_batch_fused_smoother(ctx, nrhs, level, dtype, variant, rhs_per_item=8):
+    _check(lib().chebmg_set_batch_fused_smoother(ctx, int(nrhs), int(level), int(dtype), int(variant),
+                                                 int(rhs_per_item)), "chebmg_set_batch_fused_smoother")
 
 
 def chebmg_apply_A(ctx, level, dtype, x, y):

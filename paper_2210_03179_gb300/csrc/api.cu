@@ -99,6 +99,8 @@ struct Level {
   // fused smoother (one persistent launch per smoother application) per dtype: 0 = the separate
   // operator and update kernels, else the sem_smooth8 variant; control words of its launches
   int fused[2] = {0, 0};
+  int fused_b[2] = {0, 0};     // the same for batches of the size tuned last
+  int fused_gsz[2] = {8, 8};   // right-hand sides per work item in batches
   unsigned* fctl = nullptr;
   int64_t ld = 0;       // leading dimension of batched vectors: n rounded up to 64
 };
@@ -300,10 +302,10 @@ double lmin_ratio_for(chebmg_ctx* c, int order) {
   return c->lmin_opt[order];
 }
 
-// Whether level j can run the fused smoother at all (order-7 box lattice, one right-hand side).
+// Whether level j can run the fused smoother at all (order-7 box lattice).
 bool fused_eligible(const chebmg_ctx* c, int j) {
   const Level& L = c->L[j];
-  return L.type == TYPE_SEM && L.Q == 8 && L.boxed && L.fctl != nullptr && c->nb == 1;
+  return L.type == TYPE_SEM && L.Q == 8 && L.boxed && L.fctl != nullptr;
 }
 
 // The smoother of smooth() -- and, with_residual, the restriction residual r = b - A x after it
@@ -314,7 +316,8 @@ template <typename T>
 bool smooth_fused(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero, bool with_residual) {
   Level& L = c->L[j];
   const int dt = dt_of<T>();
-  if (!fused_eligible(c, j) || L.fused[dt] == 0 || order < 1) return false;
+  const int variant = c->nb > 1 ? L.fused_b[dt] : L.fused[dt];
+  if (!fused_eligible(c, j) || variant == 0 || order < 1) return false;
   // the pointwise phases use 16-byte accesses on b and x as well (caller vectors may be views)
   if (reinterpret_cast<uintptr_t>(b) % 16 != 0 || reinterpret_cast<uintptr_t>(x) % 16 != 0) return false;
   FusedSmooth a{};
@@ -330,6 +333,9 @@ bool smooth_fused(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero
   a.y = vec<T>(L, VY);
   a.ctl = L.fctl;
   a.err = c->dstat;
+  a.nb = c->nb;
+  a.ld = ldv(c, L);
+  a.gsz = c->nb > 1 ? std::max(1, L.fused_gsz[dt]) : 1;
   const double lmax = L.lmax * c->lscale;
   int np = 0;
   bool fits = true;
@@ -371,8 +377,8 @@ bool smooth_fused(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero
   if (with_residual) add(FOP_RESIDUAL, FSRC_X);
   if (!fits) return false;
   a.nphase = np;
-  if (!fused_plan(a, L.fused[dt])) return false;
-  if (!sem_smooth8<T>(a, L.fused[dt], c->s)) {
+  if (!fused_plan(a, variant)) return false;
+  if (!sem_smooth8<T>(a, variant, c->s)) {
     cudaGetLastError();   // a refused cooperative launch leaves no other trace: separate kernels
     return false;
   }
@@ -1258,6 +1264,39 @@ void autotune_batch(chebmg_ctx* c, int nrhs) {
         }
         L.beb[dt] = best_v;
         CK(cudaMemsetAsync(y, 0, es * (size_t)nrhs * L.ld, c->s));
+      }
+    }
+  }
+  // fused smoother for this batch size: off, or on with 4, 8 or 16 right-hand sides per work
+  // item (order-7 box-lattice levels that smooth), timed on one order-4 application
+  if (nrhs > 1) {
+    for (int j = 0; j + 1 < (int)c->L.size(); ++j) {
+      Level& L = c->L[j];
+      if (!(L.type == TYPE_SEM && L.Q == 8 && L.boxed && L.fctl)) continue;
+      for (int dt : {CHEBMG_F64, CHEBMG_F32}) {
+        if (dt == CHEBMG_F32 && (!c->fp32 || !L.G[CHEBMG_F32])) continue;
+        const size_t es = dt == CHEBMG_F64 ? 8 : 4;
+        CK(cudaMemsetAsync(L.v[dt][VB], 0, es * (size_t)nrhs * L.ld, c->s));
+        float best = 1e30f;
+        int best_v = 0, best_g = 8;
+        for (int g : {0, 4, 8, 16}) {
+          if (g > nrhs) continue;
+          L.fused_b[dt] = g == 0 ? 0 : (dt == CHEBMG_F32 ? 1 : 2);
+          L.fused_gsz[dt] = g == 0 ? 8 : g;
+          const float t = time_it(
+              [&]() {
+                if (dt == CHEBMG_F64) smooth<double>(c, j, vec<double>(L, VB), vec<double>(L, VX), 4, true);
+                else smooth<float>(c, j, vec<float>(L, VB), vec<float>(L, VX), 4, true);
+              },
+              2);
+          if (t < best) {
+            best = t;
+            best_v = L.fused_b[dt];
+            best_g = L.fused_gsz[dt];
+          }
+        }
+        L.fused_b[dt] = best_v;
+        L.fused_gsz[dt] = best_g;
       }
     }
   }
@@ -2413,6 +2452,43 @@ int chebmg_set_fused_smoother(chebmg_ctx* c, int level, int dtype, int variant) 
       if (!ok) throw Error(CHEBMG_EINVAL, "fused smoother variant: 1 for FP32, 2 for FP64");
     }
     L.fused[dtype] = variant;
+    drop_graphs(c);
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_batch_fused_smoother(chebmg_ctx* c, int nrhs, int level, int dtype, int* variant, int* rhs_per_item) {
+  return guard([&]() -> int {
+    enter(c);
+    if (!variant || !rhs_per_item) throw Error(CHEBMG_EINVAL, "NULL argument");
+    Level& L = level_checked(c, level);
+    check_dtype(c, dtype);
+    if (nrhs < 2 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "batches have 2 to 65535 right-hand sides");
+    reserve_batch(c, nrhs);
+    autotune_batch(c, nrhs);
+    *variant = L.fused_b[dtype];
+    *rhs_per_item = L.fused_b[dtype] ? L.fused_gsz[dtype] : 0;
+    return CHEBMG_OK;
+  });
+}
+
+int chebmg_set_batch_fused_smoother(chebmg_ctx* c, int nrhs, int level, int dtype, int variant, int rhs_per_item) {
+  return guard([&]() -> int {
+    enter(c);
+    Level& L = level_checked(c, level);
+    check_dtype(c, dtype);
+    if (nrhs < 2 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "batches have 2 to 65535 right-hand sides");
+    if (variant != 0) {
+      if (!(L.type == TYPE_SEM && L.Q == 8 && L.boxed && L.fctl))
+        throw Error(CHEBMG_EINVAL, "the fused smoother needs an order-7 box-lattice level that smooths");
+      const bool ok = dtype == CHEBMG_F32 ? variant == 1 : variant == 2;
+      if (!ok || rhs_per_item < 1 || rhs_per_item > 64)
+        throw Error(CHEBMG_EINVAL, "fused smoother variant: 1 for FP32, 2 for FP64; 1 to 64 right-hand sides per item");
+    }
+    reserve_batch(c, nrhs);
+    autotune_batch(c, nrhs);
+    L.fused_b[dtype] = variant;
+    if (variant != 0) L.fused_gsz[dtype] = rhs_per_item;
     drop_graphs(c);
     return CHEBMG_OK;
   });

@@ -119,9 +119,13 @@ struct FusedSmooth {
   void *x, *r, *d, *y;
   unsigned* ctl;      // fused_ctl_words(lat) words, zeroed by the launcher
   unsigned* err;      // set to 1 when a bounded wait runs out
+  int nb;             // right-hand sides: vector q of x, r, d, y, b at q * ld (S shared)
+  int64_t ld;
+  int gsz;            // right-hand sides per work item
   // derived by fused_plan
   int nslab;          // element planes (slabs)
   int spp;            // elements per slab
+  int ngroups;        // right-hand-side groups: item k of a task covers group k % ngroups
   int m1, m2;         // work items per operator task / per pointwise task
   int chunk;          // nodes per pointwise work item
   int tsteps;

@@ -262,17 +262,17 @@ __device__ __forceinline__ unsigned op_writes(int op) {
 // The pointwise operation over nodes [lo, hi) (lo a multiple of 4): 16-byte accesses over the
 // aligned body, VPT vectors per thread per round, scalar tail.
 template <typename T, int NT>
-__device__ void pointwise(const FusedSmooth& a, const PointOp<T>& f, int64_t lo, int64_t hi) {
+__device__ void pointwise(const FusedSmooth& a, const PointOp<T>& f, int64_t lo, int64_t hi, int64_t off) {
   using V = typename Vec16<T>::type;
   constexpr int L = Vec16<T>::L;
   constexpr int VPT = 2;
   const unsigned rd = op_reads(f.op), wr = op_writes(f.op);
-  T* X = static_cast<T*>(a.x);
-  T* Rv = static_cast<T*>(a.r);
-  T* Dv = static_cast<T*>(a.d);
-  T* Y = static_cast<T*>(a.y);
+  T* X = static_cast<T*>(a.x) + off;   // right-hand side at offset off; S is shared
+  T* Rv = static_cast<T*>(a.r) + off;
+  T* Dv = static_cast<T*>(a.d) + off;
+  T* Y = static_cast<T*>(a.y) + off;
   const T* S = static_cast<const T*>(a.S);
-  const T* B = static_cast<const T*>(a.b);
+  const T* B = static_cast<const T*>(a.b) + off;
   const int64_t v0 = lo / L, v1 = hi / L;   // vectors [v0, v1)
   for (int64_t base = v0 + threadIdx.x; base < v1; base += (int64_t)NT * VPT) {
     V xv[VPT], rv[VPT], dv[VPT], yv[VPT], sv[VPT], bv[VPT];
@@ -334,18 +334,6 @@ __device__ __forceinline__ bool named_and(int id, int nthreads, bool pred) {
       : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
       : "memory");
   return r != 0;
-}
-// Non-blocking: has the phase of the given parity completed (acquire, CTA scope)?
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -426,8 +414,9 @@ __global__ void __launch_bounds__(64 * EB + 32, 3) k_sem_smooth8(const __grid_co
           sh_item[slot] = nx;
           held[slot] = nx;
           if (nx.kind == 1) {
-            const int64_t e0 = (int64_t)nx.s * a.spp + (int64_t)nx.k * EB;
-            const int nv = min(EB, a.spp - nx.k * EB);
+            const int bt = nx.k / a.ngroups;   // element batch of the item
+            const int64_t e0 = (int64_t)nx.s * a.spp + (int64_t)bt * EB;
+            const int nv = min(EB, a.spp - bt * EB);
             const uint32_t bytes = (uint32_t)(nv * C::GELEM * sizeof(T));
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&ready[slot])),
                          "r"(bytes)
@@ -471,29 +460,14 @@ __global__ void __launch_bounds__(64 * EB + 32, 3) k_sem_smooth8(const __grid_co
   T* su = sU + le * C::STAGE;
   T* sr = sR + le * C::STAGE;
   T* ss = sS + le * C::STAGE;
-  // The next operator item's gather, started while the current item is worked on when that item
-  // is already handed over (its dependencies are complete, so its source values are final).
-  // Per thread: each thread gathers its own column.
-  uint32_t gn[8];
-  T cn[8];
-  bool pref = false;
+  // ids of the item's element column and the values of its first right-hand side
   auto gather = [&](const Item& it, uint32_t (&g)[8], T (&col)[8]) {
-    const T* src = static_cast<const T*>(a.ph[it.p].src == FSRC_X ? a.x : a.d);
-    const int64_t e = (int64_t)it.s * a.spp + (int64_t)it.k * EB + le;
-    column_ids<true>(nullptr, a.lat, e, it.k * EB + le < a.spp, ca, cb, g);
+    const int bt = it.k / a.ngroups, q0 = (it.k % a.ngroups) * a.gsz;
+    const T* src = static_cast<const T*>(a.ph[it.p].src == FSRC_X ? a.x : a.d) + (int64_t)q0 * a.ld;
+    const int64_t e = (int64_t)it.s * a.spp + (int64_t)bt * EB + le;
+    column_ids<true>(nullptr, a.lat, e, bt * EB + le < a.spp, ca, cb, g);
 #pragma unroll
     for (int k = 0; k < 8; ++k) col[k] = (g[k] & kGidDirichlet) ? T(0) : __ldcg(src + (g[k] & kGidMask));
-  };
-  auto prefetch_next = [&](uint32_t j) {
-    const int ns = (j + 1) & 1;
-    pref = false;
-    if (mbar_test(&ready[ns], ((j + 1) >> 1) & 1u)) {
-      const Item nx = sh_item[ns];
-      if (nx.kind == 1) {
-        gather(nx, gn, cn);
-        pref = true;
-      }
-    }
   };
   for (uint32_t j = 0;; ++j) {
     const int slot = j & 1;
@@ -514,82 +488,94 @@ __global__ void __launch_bounds__(64 * EB + 32, 3) k_sem_smooth8(const __grid_co
     if (cur.kind == 0) break;
     const FusedPhase& ph = a.ph[cur.p];
     if (cur.kind == 1) {
-      // ---- operator on EB elements of plane cur.s: y += A v ----
+      // ---- operator on EB elements of plane cur.s, for the item's right-hand sides: y += A v ----
+      const int bt = cur.k / a.ngroups, q0 = (cur.k % a.ngroups) * a.gsz;
+      const int q1 = q0 + a.gsz < a.nb ? q0 + a.gsz : a.nb;
+      const bool valid = bt * EB + le < a.spp;
+      const T* srcb = static_cast<const T*>(ph.src == FSRC_X ? a.x : a.d);
       uint32_t g[8];
       T col[8];
-      if (pref) {
+      gather(cur, g, col);
+      const T* gG = sG + slot * EB * C::GELEM + le * C::GELEM;
+      for (int q = q0; q < q1; ++q) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) su[k * P + cb * R + ca] = col[k];
+        T ut[8];
+        line8<T, 0>(col, ut);
+        T nxt[8];
+        if (q + 1 < q1) {   // the next right-hand side's values, in flight during this one
+          const T* src = srcb + (int64_t)(q + 1) * a.ld;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) nxt[k] = (g[k] & kGidDirichlet) ? T(0) : __ldcg(src + (g[k] & kGidMask));
+        }
+        named_sync(1, NC);
+        {
+          T v[8], o[8];
+          ld_row(su + cb * P + ca * R, v);
+          line8<T, 0>(v, o);
+          st_row(sr + cb * P + ca * R, o);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) v[jj] = su[cb * P + jj * R + ca];
+          line8<T, 0>(v, o);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) ss[cb * P + jj * R + ca] = o[jj];
+        }
+        named_sync(1, NC);   // the r and s passes wrote points that other threads read next
+        T wt[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          g[k] = gn[k];
-          col[k] = cn[k];
+          const int p = k * 64 + cb * 8 + ca;
+          const int qq = k * P + cb * R + ca;
+          const T ur = sr[qq], us = ss[qq], utk = ut[k];
+          const T g00 = gG[p], g01 = gG[512 + p], g02 = gG[1024 + p];
+          const T g11 = gG[1536 + p], g12 = gG[2048 + p], g22 = gG[2560 + p];
+          sr[qq] = g00 * ur + g01 * us + g02 * utk;
+          ss[qq] = g01 * ur + g11 * us + g12 * utk;
+          wt[k] = g02 * ur + g12 * us + g22 * utk;
         }
-      } else {
-        gather(cur, g, col);
-      }
-      prefetch_next(j);
+        T yt[8];
+        line8<T, 1>(wt, yt);
+        named_sync(1, NC);
+        {
+          T v[8], o[8];
+          ld_row(sr + cb * P + ca * R, v);
+          line8<T, 1>(v, o);
+          st_row(su + cb * P + ca * R, o);
+        }
+        named_sync(1, NC);
+        {
+          T v[8], o[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) su[k * P + cb * R + ca] = col[k];
-      T ut[8];
-      line8<T, 0>(col, ut);
-      named_sync(1, NC);
-      {
-        T v[8], o[8];
-        ld_row(su + cb * P + ca * R, v);
-        line8<T, 0>(v, o);
-        st_row(sr + cb * P + ca * R, o);
+          for (int jj = 0; jj < 8; ++jj) v[jj] = ss[cb * P + jj * R + ca];
+          line8<T, 1>(v, o);
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) v[jj] = su[cb * P + jj * R + ca];
-        line8<T, 0>(v, o);
+          for (int jj = 0; jj < 8; ++jj) su[cb * P + jj * R + ca] += o[jj];
+        }
+        named_sync(1, NC);
+        if (valid) {
+          T* Yq = Y + (int64_t)q * a.ld;
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) ss[cb * P + jj * R + ca] = o[jj];
-      }
-      named_sync(1, NC);   // the r and s passes wrote points that other threads read next
-      T wt[8];
-      const T* gG = sG + slot * EB * C::GELEM + le * C::GELEM;
+          for (int k = 0; k < 8; ++k) {
+            const T v = su[k * P + cb * R + ca] + yt[k];
+            if (!(g[k] & kGidDirichlet)) atomicAdd(&Yq[g[k] & kGidMask], v);
+          }
+        }
+        if (q + 1 < q1) {
+          named_sync(1, NC);   // stage buffers free for the next right-hand side
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int p = k * 64 + cb * 8 + ca;
-        const int q = k * P + cb * R + ca;
-        const T ur = sr[q], us = ss[q], utk = ut[k];
-        const T g00 = gG[p], g01 = gG[512 + p], g02 = gG[1024 + p];
-        const T g11 = gG[1536 + p], g12 = gG[2048 + p], g22 = gG[2560 + p];
-        sr[q] = g00 * ur + g01 * us + g02 * utk;
-        ss[q] = g01 * ur + g11 * us + g12 * utk;
-        wt[k] = g02 * ur + g12 * us + g22 * utk;
-      }
-      T yt[8];
-      line8<T, 1>(wt, yt);
-      named_sync(1, NC);
-      {
-        T v[8], o[8];
-        ld_row(sr + cb * P + ca * R, v);
-        line8<T, 1>(v, o);
-        st_row(su + cb * P + ca * R, o);
-      }
-      named_sync(1, NC);
-      {
-        T v[8], o[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) v[jj] = ss[cb * P + jj * R + ca];
-        line8<T, 1>(v, o);
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) su[cb * P + jj * R + ca] += o[jj];
-      }
-      named_sync(1, NC);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const T v = su[k * P + cb * R + ca] + yt[k];
-        if (!(g[k] & kGidDirichlet)) atomicAdd(&Y[g[k] & kGidMask], v);
+          for (int k = 0; k < 8; ++k) col[k] = nxt[k];
+        }
       }
     } else {
       // ---- pointwise operation on chunk cur.k of slab cur.s's nodes ----
+      const int ck = cur.k / a.ngroups, q0 = (cur.k % a.ngroups) * a.gsz;
+      const int q1 = q0 + a.gsz < a.nb ? q0 + a.gsz : a.nb;
       const int64_t s0 = slab_start(a, cur.s), s1 = slab_start(a, cur.s + 1);
-      const int64_t lo = s0 + (int64_t)cur.k * a.chunk;
+      const int64_t lo = s0 + (int64_t)ck * a.chunk;
       const int64_t hi = lo + a.chunk < s1 ? lo + a.chunk : s1;
-      prefetch_next(j);
       if (lo < hi) {
         PointOp<T> f{ph.op, (T)ph.c[0], (T)ph.c[1], (T)ph.c[2], (T)ph.c[3]};
-        pointwise<T, NC>(a, f, lo, hi);
+        for (int q = q0; q < q1; ++q) pointwise<T, NC>(a, f, lo, hi, (int64_t)q * a.ld);
       }
     }
     named_sync(1, NC);   // the item is done in every compute thread (stage buffers free)
@@ -635,7 +621,9 @@ bool fused_plan(FusedSmooth& a, int variant) {
   if ((int64_t)L.NX * L.NY * L.NZ != a.n || L.NX != 7 * L.nex + 1 || L.NY != 7 * L.ney + 1 ||
       L.NZ != 7 * L.nez + 1)
     return false;
-  a.m1 = (a.spp + EB - 1) / EB;
+  if (a.nb < 1 || a.gsz < 1 || (a.nb > 1 && a.ld % 4 != 0)) return false;
+  a.ngroups = (a.nb + a.gsz - 1) / a.gsz;
+  a.m1 = (a.spp + EB - 1) / EB * a.ngroups;
   a.chunk = 64 * EB * 32;
   const int64_t plane = (int64_t)L.NX * L.NY;
   int64_t maxr = 0;
@@ -644,7 +632,7 @@ bool fused_plan(FusedSmooth& a, int variant) {
     const int64_t s1 = s + 1 == a.nslab ? a.n : ((7 * (int64_t)(s + 1) * plane) & ~int64_t(3));
     maxr = std::max(maxr, s1 - s0);
   }
-  a.m2 = (int)((maxr + a.chunk - 1) / a.chunk);
+  a.m2 = (int)((maxr + a.chunk - 1) / a.chunk) * a.ngroups;
   a.tsteps = 3 * (a.nphase - 1) + a.nslab + 1;
   if (a.tsteps > kFusedMaxT) return false;
   uint64_t acc = 0;

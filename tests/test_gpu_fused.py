@@ -166,3 +166,57 @@ def test_fused_smoother_refused_where_it_does_not_apply():
     with pytest.raises(cm.ChebmgError):
         cm.chebmg_set_fused_smoother(f.ctx, 0, F64, 2)
     f.close()
+
+
+# ---- batches: a work item covers several right-hand sides (the geometric factors staged once) ----
+
+def _rows(a):
+    return T(np.ascontiguousarray(np.stack(a)))
+
+
+@pytest.mark.parametrize("rhs_per_item", [1, 3, 8])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_fused_vcycle_matches_oracle(rhs_per_item, prec):
+    mesh = (2, 3, 7)
+    v = W.sem_box_vertices(*mesh)
+    H = P.sem_hierarchy(v, (7, 3, 1), kind="opt4th", k=3, sided="one-sided")
+    s = solver(v, k=3, sided="one-sided", prec=prec, lmax=[Lv.lmax for Lv in H.levels[:-1]])
+    dt, var = (F32, 1) if prec == "mixed" else (F64, 2)
+    nrhs = 7   # not a multiple of the group size: the last group is ragged
+    R = [W.sem_rhs(*mesh, 7, seed=q) for q in range(nrhs)]
+    Z = {}
+    for v_ in (0, var):
+        cm.chebmg_set_batch_fused_smoother(s.ctx, nrhs, 0, dt, v_, rhs_per_item)
+        assert cm.chebmg_batch_fused_smoother(s.ctx, nrhs, 0, dt) == ((v_, rhs_per_item) if v_ else (0, 0))
+        Z[v_] = torch.zeros((nrhs, len(R[0])), dtype=torch.float64, device="cuda")
+        cm.chebmg_vcycle_batched(s.ctx, _rows(R), Z[v_])
+    for q in range(nrhs):
+        ref = M.vcycle(H, R[q])
+        if prec == "fp64":
+            assert relerr(N(Z[var][q]), ref) < 1e-8
+            assert relerr(N(Z[var][q]), N(Z[0][q])) < 1e-8
+        else:
+            assert relerr(N(Z[var][q]), N(Z[0][q])) < 1e-5
+            assert relerr(N(Z[var][q]), ref) < 1e-4
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_fused_solve_iterations_match_oracle(prec):
+    mesh = (3, 4, 5)
+    v = W.sem_box_vertices(*mesh)
+    H = P.sem_hierarchy(v, (7, 3, 1), kind="opt4th", k=2, sided="one-sided")
+    s = solver(v, k=2, sided="one-sided", prec=prec, lmax=[Lv.lmax for Lv in H.levels[:-1]])
+    nrhs = 5
+    cm.chebmg_set_batch_fused_smoother(s.ctx, nrhs, 0, F32 if prec == "mixed" else F64,
+                                       1 if prec == "mixed" else 2, 4)
+    A = H.levels[0].apply_A
+    B = [W.sem_rhs(*mesh, 7, seed=q) for q in range(nrhs)]
+    U = torch.zeros((nrhs, len(B[0])), dtype=torch.float64, device="cuda")
+    code, its, rel = cm.chebmg_pcg_solve_batched(s.ctx, _rows(B), U, 1e-8, 200, graph=False)
+    assert code == cm.CHEBMG_OK
+    for q in range(nrhs):
+        _, it_ref, _ = K.fcg(A, lambda r: M.vcycle(H, r), B[q], 1e-8)
+        assert abs(its[q] - it_ref) <= 1 and rel[q] <= 1e-8
+        assert np.linalg.norm(B[q] - A(N(U[q]))) <= 1.01e-8 * np.linalg.norm(B[q])
+    s.close()
