@@ -396,6 +396,16 @@ int chebmg_fd_smooth_noalloc(int m, double Lx, double Ly, int kind, int order, d
                              double lmin_ratio, const double* b, double* x, int x_is_zero,
                              void* stream);
 
+/* ---- utilities ----------------------------------------------------------------- */
+
+/* out = in converted between CHEBMG_F32 and CHEBMG_F64 (or copied), n entries, device
+ * vectors, on `stream` (NULL = default stream): the conversion kernel the mixed-precision solve
+ * uses between its FP64 Krylov vectors and its FP32 V-cycle.  It converts in integer
+ * arithmetic (GB300 issues hardware FP64 conversions at its small FP64 rate) and gives the
+ * IEEE result: exact widening, narrowing rounded to nearest with ties to even.  EINVAL on bad
+ * arguments. */
+int chebmg_convert(const void* in, int in_dtype, void* out, int out_dtype, int64_t n, void* stream);
+
 /* ---- errors ------------------------------------------------------------------ */
 const char* chebmg_strerror(int code);
 const char* chebmg_last_error(void);

@@ -90,6 +90,7 @@ _SIGNATURES = {
     "chebmg_set_tile_choice": (c_int, [c_void_p, c_int, c_int, c_int]),
     "chebmg_fused_smoother": (c_int, [c_void_p, c_int, c_int, POINTER(c_int)]),
     "chebmg_set_fused_smoother": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "chebmg_convert": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int64, c_void_p]),
     "chebmg_batch_fused_smoother": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_int), POINTER(c_int)]),
     "chebmg_set_batch_fused_smoother": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int]),
     "chebmg_set_coarse_precond_dtype": (c_int, [c_void_p, c_int, c_int]),
@@ -532,6 +533,18 @@ def chebmg_selftest_coarse_timeout(ctx) -> int:
     st = c_int()
     _check(lib().chebmg_selftest_coarse_timeout(ctx, byref(st)), "chebmg_selftest_coarse_timeout")
     return st.value
+
+
+def chebmg_convert(x, y, stream=None):
+    """y = x converted (FP32 <-> FP64) by the library's conversion kernel; x, y CUDA tensors."""
+    import torch
+    dt = {torch.float32: CHEBMG_F32, torch.float64: CHEBMG_F64}
+    if x.dtype not in dt or y.dtype not in dt or x.numel() != y.numel():
+        raise ValueError("x, y: float32/float64 CUDA tensors of the same length")
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x, y must be contiguous CUDA tensors")
+    _check(lib().chebmg_convert(c_void_p(x.data_ptr()), dt[x.dtype], c_void_p(y.data_ptr()), dt[y.dtype],
+                                x.numel(), _stream_handle(stream)), "chebmg_convert")
 
 
 def chebmg_fd_smooth_noalloc(m, Lx, Ly, kind, order, lmax, lmin_ratio, b, x, x_is_zero, stream=None):

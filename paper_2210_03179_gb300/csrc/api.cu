@@ -2494,6 +2494,26 @@ int chebmg_set_batch_fused_smoother(chebmg_ctx* c, int nrhs, int level, int dtyp
   });
 }
 
+int chebmg_convert(const void* in, int in_dtype, void* out, int out_dtype, int64_t n, void* stream) {
+  return guard([&]() -> int {
+    if (n < 0 || (n > 0 && (!in || !out))) throw Error(CHEBMG_EINVAL, "bad conversion arguments");
+    if ((in_dtype != CHEBMG_F32 && in_dtype != CHEBMG_F64) || (out_dtype != CHEBMG_F32 && out_dtype != CHEBMG_F64))
+      throw Error(CHEBMG_EINVAL, "dtype must be CHEBMG_F32 or CHEBMG_F64");
+    if (n == 0) return CHEBMG_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (in_dtype == CHEBMG_F32 && out_dtype == CHEBMG_F64)
+      cast<float, double>(n, static_cast<const float*>(in), static_cast<double*>(out), s);
+    else if (in_dtype == CHEBMG_F64 && out_dtype == CHEBMG_F32)
+      cast<double, float>(n, static_cast<const double*>(in), static_cast<float*>(out), s);
+    else if (in_dtype == CHEBMG_F32)
+      cast<float, float>(n, static_cast<const float*>(in), static_cast<float*>(out), s);
+    else
+      cast<double, double>(n, static_cast<const double*>(in), static_cast<double*>(out), s);
+    check_launch();
+    return CHEBMG_OK;
+  });
+}
+
 int chebmg_launch_count(const chebmg_ctx* c, int64_t* count) {
   (void)c;
   if (!count) return CHEBMG_EINVAL;

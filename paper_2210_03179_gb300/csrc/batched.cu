@@ -154,7 +154,7 @@ k_bfcg_update_xr32(int64_t n, int64_t ld, int nblk, double* __restrict__ x, doub
     x[g] += alpha * p[g];
     const double rn = r[g] - alpha * q[g];
     r[g] = rn;
-    if (r32) r32[g] = (float)rn;
+    if (r32) r32[g] = narrow_f64(rn);
     s0 += rn * rn;
   }
   bsum2(s0, s1);
@@ -171,7 +171,7 @@ k_bdot_zr_zq(int64_t n, int64_t ld, int nblk, const Tz* __restrict__ z, const do
   const int64_t off = (int64_t)blockIdx.y * ld;
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n; g += (int64_t)nblk * kThreads) {
-    const double zv = (double)z[g];
+    const double zv = to_f64(z[g]);
     s0 += zv * r[g];
     if (q) s1 += zv * q[g];
   }
@@ -190,7 +190,7 @@ k_bupdate_p_from(int64_t n, int64_t ld, const Tz* __restrict__ z, double* __rest
   const double beta = first ? 0.0 : scal[blockIdx.y * S_NSLOTS + S_BETA];
   for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n;
        g += (int64_t)gridDim.x * kThreads)
-    p[g] = first ? (double)z[g] : (double)z[g] + beta * p[g];
+    p[g] = first ? to_f64(z[g]) : to_f64(z[g]) + beta * p[g];
 }
 
 // ---------------------------------------------------------------------------

@@ -185,7 +185,7 @@ __global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__
   in += (int64_t)blockIdx.y * ldi;
   out += (int64_t)blockIdx.y * ldo;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    out[g] = (Tout)in[g];
+    out[g] = convert_to<Tout>(in[g]);
 }
 
 __global__ void k_masked_copy(int64_t n, const double* __restrict__ in, const double* __restrict__ invD,
@@ -272,5 +272,6 @@ CHEBMG_CHEB_INST(double)
 template void cast<double, float>(int64_t, const double*, float*, cudaStream_t, int, int64_t, int64_t);
 template void cast<float, double>(int64_t, const float*, double*, cudaStream_t, int, int64_t, int64_t);
 template void cast<double, double>(int64_t, const double*, double*, cudaStream_t, int, int64_t, int64_t);
+template void cast<float, float>(int64_t, const float*, float*, cudaStream_t, int, int64_t, int64_t);
 
 }  // namespace chebmg

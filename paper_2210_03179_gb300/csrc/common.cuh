@@ -29,7 +29,7 @@ enum Slot {
 };
 enum PostOp { POST_NONE = 0, POST_ALPHA, POST_BETA_CG, POST_SET_RZ_FROM_ZR, POST_BETA_FLEX_Q };
 
-constexpr int kRedBlocks = 592;    // 152 SMs x 4: partial sums per reduction pass
+constexpr int kRedBlocks = 1216;   // 152 SMs x 8: partial sums per reduction pass (full occupancy)
 
 template <typename T>
 struct Stencil9 {
@@ -288,6 +288,48 @@ __device__ __forceinline__ double block_div(double* slot, double num, double den
   __syncthreads();
   return *slot;
 }
+#endif
+
+// Conversions between FP32 and FP64 in integer arithmetic.  GB300 issues FP64 instructions --
+// the hardware conversions F2F included -- at a small fraction of its FP32 and integer rates, so
+// the FP64 vector kernels of the Krylov loop, which convert every FP32 value they touch, are
+// bound by the FP64 pipe.  These give the hardware conversion's exact result: widening re-biases
+// the exponent and shifts the mantissa (exact for every finite float); narrowing rounds the
+// 52-bit mantissa to 23 bits to nearest, ties to even, a carry running into the exponent (and to
+// infinity above the largest float).  Values outside the normal range (zeros and subnormals on
+// the float side, infinities and NaN) take the hardware conversion.
+#ifdef __CUDACC__
+__device__ __forceinline__ double widen_f32(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)v;
+  const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ float narrow_f64(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const uint32_t e = (uint32_t)(u >> 52) & 0x7ffu;
+  if (e < 897u || e > 1150u) return (float)v;
+  const unsigned long long m = u & 0xfffffffffffffull;
+  uint32_t f = ((e - 896u) << 23) | (uint32_t)(m >> 29);
+  const unsigned long long rem = m & 0x1fffffffull;
+  f += (rem > 0x10000000ull || (rem == 0x10000000ull && (f & 1u))) ? 1u : 0u;
+  return __uint_as_float(f | ((uint32_t)(u >> 32) & 0x80000000u));
+}
+__device__ __forceinline__ double to_f64(float v) { return widen_f32(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+template <typename Tout>
+__device__ __forceinline__ Tout convert_to(float v);
+template <typename Tout>
+__device__ __forceinline__ Tout convert_to(double v);
+template <>
+__device__ __forceinline__ double convert_to<double>(float v) { return widen_f32(v); }
+template <>
+__device__ __forceinline__ float convert_to<float>(double v) { return narrow_f64(v); }
+template <>
+__device__ __forceinline__ float convert_to<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ double convert_to<double>(double v) { return v; }
 #endif
 
 // Rows per thread the persistent coarse kernel can keep in registers.

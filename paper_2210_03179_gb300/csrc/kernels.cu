@@ -470,7 +470,7 @@ k_fcg_update_xr32(int64_t n, double* __restrict__ x, double* __restrict__ r, flo
     x[g] += alpha * p[g];
     const double rn = r[g] - alpha * q[g];
     r[g] = rn;
-    if (r32) r32[g] = (float)rn;
+    if (r32) r32[g] = narrow_f64(rn);
     s0 += rn * rn;
   }
   block_sum2(s0, s1);
@@ -493,7 +493,7 @@ k_dot_zr_zq(int64_t n, const Tz* __restrict__ z, const double* __restrict__ r, c
             double* __restrict__ partial) {
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const double zv = (double)z[g];
+    const double zv = to_f64(z[g]);
     s0 += zv * r[g];
     if (q) s1 += zv * q[g];
   }
@@ -521,7 +521,7 @@ __global__ void k_update_p_from(int64_t n, const Tz* __restrict__ z, double* __r
                                 const double* __restrict__ scal, int first) {
   const double beta = first ? 0.0 : scal[S_BETA];
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    p[g] = first ? (double)z[g] : (double)z[g] + beta * p[g];
+    p[g] = first ? to_f64(z[g]) : to_f64(z[g]) + beta * p[g];
 }
 
 template <typename Tz>
