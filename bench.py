@@ -808,14 +808,19 @@ def main():
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     achieved = alg_bytes32 / step32 / 1e9
+    fused32 = cm.chebmg_fused_smoother(s32.ctx, 0, cm.CHEBMG_F32)
+    tile32 = cm.chebmg_tile_choice(s32.ctx, 0, cm.CHEBMG_F32)
     roofline = {"bound": "hbm",
-                "kernel": "fine FP32 Chebyshev step: k_sem_ax8p (element Ax + gather-scatter) + k_cheb4_step",
+                "kernel": ("fine FP32 Chebyshev step, fused: k_sem_smooth8 (one launch per smoother application)"
+                           if fused32 else
+                           "fine FP32 Chebyshev step: k_sem_ax8p (element Ax + gather-scatter) + k_cheb4_step"),
                 "achieved": achieved, "peak": hbm if hbm else 6800.0, "unit": "GB/s",
                 "frac": achieved / (hbm if hbm else 6800.0),
                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "of fallback",
-                "traffic": recorded_traffic(cm.chebmg_tile_choice(s32.ctx, 0, 1)),
+                # the recorded DRAM bytes belong to the separate kernels of that variant
+                "traffic": recorded_traffic(tile32) if fused32 == 0 else None,
                 "alg_bytes_per_step": alg_bytes32, "step_us": step32 * 1e6,
-                "elements_per_block_variant": cm.chebmg_tile_choice(s32.ctx, 0, 1)}
+                "elements_per_block_variant": tile32, "fused_variant": fused32}
     # ---- the FP64 outer operator q = A p (k_sem_ax8<double>), bound by the FP64 pipe ----
     # Executed FP64 instructions per element point, counted from the kernel source: six line
     # passes of 44 per 8-point line (8 even-odd sums, 4 x 9 chain FMAs) = 33, the geometric
