@@ -263,8 +263,9 @@ void read_cscal(chebmg_ctx* c) {
 }
 
 // y = A x on level j; for SEM y must be zero on entry (element contributions accumulate).
+// pdl: the order-7 kernel may launch as a programmatic dependent of the preceding kernel.
 template <typename T>
-void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld) {
+void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld, bool pdl = false) {
   Level& L = c->L[j];
   const int dt = dt_of<T>();
   if (L.type == TYPE_SEM) {
@@ -272,7 +273,7 @@ void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld) {
       sem_ax8_batched<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.beb[dt], nb, ld,
                          c->s);
     else if (L.Q == 8)
-      sem_ax8<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s);
+      sem_ax8<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s, pdl);
     else
       sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s, nb,
                 ld);
@@ -284,8 +285,8 @@ void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld) {
 
 // y = A x on level j for the current batch (y zero on entry for SEM).
 template <typename T>
-void apply_into(chebmg_ctx* c, int j, const T* x, T* y) {
-  apply_into_ld<T>(c, j, x, y, c->nb, ldv(c, c->L[j]));
+void apply_into(chebmg_ctx* c, int j, const T* x, T* y, bool pdl = false) {
+  apply_into_ld<T>(c, j, x, y, c->nb, ldv(c, c->L[j]), pdl);
 }
 
 template <typename T>
@@ -419,13 +420,16 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
     if (!c->beta_ovr.empty() && (int)c->beta_ovr.size() == order) beta = c->beta_ovr.data();
     cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), x_zero ? 1 : 0, c->s, nb, ld);
     const double beta_k = beta ? beta[order - 1] : 1.0;
+    // single right-hand side: each kernel of the step loop launches as a programmatic dependent
+    // of the one before, so its start overlaps that kernel's tail (both wait before reading)
+    const bool pdl = nb == 1;
     for (int i = 1; i < order; ++i) {
-      apply_into<T>(c, j, d, y);
+      apply_into<T>(c, j, d, y, pdl);
       const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0);
       const double c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lmax);
       // the last step also applies the final update x += beta_k d_k (one pass fewer)
       cheb4_step<T>(n, x, r, d, y, S, beta ? beta[i - 1] : 1.0, c1, c2, c->s, nb, ld,
-                    i + 1 == order ? beta_k : 0.0);
+                    i + 1 == order ? beta_k : 0.0, pdl);
     }
     if (order == 1 || beta_k == 0.0) axpy<T>(n, beta_k, d, x, c->s, nb, ld);
   }

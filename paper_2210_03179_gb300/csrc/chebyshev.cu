@@ -104,6 +104,11 @@ template <typename T, bool VEC>
 __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
                              T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, T beta_next,
                              int64_t ld) {
+  // Launched as a programmatic dependent of the operator kernel (a no-op otherwise): the launch
+  // overlaps that kernel's end, and everything read here is its output or older, so wait for it
+  // before the first load.  (Triggering the next kernel early as well was measured slower: its
+  // waiting blocks cost this grid's last wave more than they saved.)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
   using VT = typename V16<T>::type;
   constexpr int L = V16<T>::L;
@@ -207,10 +212,22 @@ void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, do
 }
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
-                cudaStream_t s, int nb, int64_t ld, double beta_next) {
+                cudaStream_t s, int nb, int64_t ld, double beta_next, bool pdl) {
   if (!ld) ld = n;
   const uintptr_t align = (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
-  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
+  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0) && pdl) {
+    // programmatic dependent launch: the blocks may start while the operator kernel drains
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb);
+    cfg.blockDim = dim3(kVecThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_cheb4_step<T, true>, n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
+  } else if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
     k_cheb4_step<T, true><<<dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), kVecThreads, 0, s>>>(
         n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
   else
@@ -260,7 +277,7 @@ void masked_copy(int64_t n, const double* in, const double* invD, double* out, c
   template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t, int,   \
-                              int64_t, double);                                                         \
+                              int64_t, double, bool);                                                   \
   template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t, int, int64_t); \

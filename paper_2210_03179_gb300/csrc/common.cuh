@@ -69,9 +69,11 @@ void sem_ax8_x2(int64_t E, const uint32_t* gid, const Lattice& lat, const void* 
 // variant chosen per level by a setup-time autotuner: 1, 2 or 4 elements per thread block,
 // or 12 / 14 for the persistent software-pipelined kernel with 2 / 4 elements; +100 computes
 // global ids from the box lattice instead of reading the element-to-global map.
+// pdl: the persistent variants (12, 14) launch as programmatic dependents of the preceding kernel
+// (the first geometric-factor copy starts before waiting for it).
 template <typename T>
 void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
-             unsigned* err, int variant, cudaStream_t s);
+             unsigned* err, int variant, cudaStream_t s, bool pdl = false);
 // Batched form: nb right-hand sides at leading dimension ld.  variant = 1000 * RB + (100 if
 // implicit ids) + EB: a block stages the geometric factors of EB elements once and applies them
 // to RB right-hand sides; EB + 10 (EB 1 or 2) takes the right-hand sides two at a time through
@@ -171,10 +173,12 @@ template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0,
                 int x_is_zero, cudaStream_t s, int nb = 1, int64_t ld = 0);
 // 4th kind step: x += beta d; r -= y; d = c1 d + c2 S r; y = 0; then, if beta_next != 0 (the
-// last step), the final update x += beta_next d with the new d.
+// last step), the final update x += beta_next d with the new d.  pdl: launch as a programmatic
+// dependent of the preceding kernel (its blocks may start during that kernel's tail and wait).
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1,
-                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0, double beta_next = 0.0);
+                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0, double beta_next = 0.0,
+                bool pdl = false);
 // 1st kind init: r = S (b - y) (or S b), d = r / theta, y = 0 (x = 0 if x_is_zero).
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,

@@ -275,6 +275,10 @@ k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
     for (int k = 0; k < 8; ++k) v[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
   };
   if (tid == 0) issue(batch, 0);
+  // Launched as a programmatic dependent of the preceding kernel (a no-op otherwise): u and y
+  // come from that kernel, so wait for it now -- after the first geometric-factor copy is on its
+  // way.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   uint32_t g[8];
   T col[8];
   gather(batch, g, col);
@@ -707,7 +711,7 @@ static void launch_ax8g(int64_t E, const uint32_t* gid, const Lattice& lat, cons
 
 template <typename T, int EB, bool IM>
 static void launch_ax8p(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
-                        unsigned* err, cudaStream_t s) {
+                        unsigned* err, cudaStream_t s, bool pdl) {
   using C = Ax8<T, EB>;
   const size_t smem = sizeof(T) * (size_t)EB * (2 * C::GELEM + 3 * C::STAGE);
   static int grid = 0;
@@ -721,7 +725,21 @@ static void launch_ax8p(int64_t E, const uint32_t* gid, const Lattice& lat, cons
   }
   const int64_t nbatch = (E + EB - 1) / EB;
   const unsigned blocks = (unsigned)(nbatch < grid ? nbatch : grid);
-  k_sem_ax8p<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y, err);
+  if (pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(64 * EB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_sem_ax8p<T, EB, IM>, E, gid, lat, G, u, y, err);
+  } else {
+    k_sem_ax8p<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y, err);
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
@@ -792,23 +810,23 @@ bool sem_ax8_variant_fits(int eb) {
 
 template <typename T, bool IM>
 static void dispatch_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
-                         unsigned* err, int eb, cudaStream_t s) {
+                         unsigned* err, int eb, cudaStream_t s, bool pdl) {
   switch (eb) {
     case 21: launch_ax8g<T, 1, IM>(E, gid, lat, G, u, y, s); break;
     case 22: launch_ax8g<T, 2, IM>(E, gid, lat, G, u, y, s); break;
     case 1: launch_ax8<T, 1, IM>(E, gid, lat, G, u, y, err, s); break;
     case 4: launch_ax8<T, 4, IM>(E, gid, lat, G, u, y, err, s); break;
-    case 12: launch_ax8p<T, 2, IM>(E, gid, lat, G, u, y, err, s); break;
-    case 14: launch_ax8p<T, 4, IM>(E, gid, lat, G, u, y, err, s); break;
+    case 12: launch_ax8p<T, 2, IM>(E, gid, lat, G, u, y, err, s, pdl); break;
+    case 14: launch_ax8p<T, 4, IM>(E, gid, lat, G, u, y, err, s, pdl); break;
     default: launch_ax8<T, 2, IM>(E, gid, lat, G, u, y, err, s); break;
   }
 }
 
 template <typename T>
 void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y, unsigned* err,
-             int variant, cudaStream_t s) {
-  if (variant >= 100) dispatch_ax8<T, true>(E, gid, lat, G, u, y, err, variant - 100, s);
-  else dispatch_ax8<T, false>(E, gid, lat, G, u, y, err, variant, s);
+             int variant, cudaStream_t s, bool pdl) {
+  if (variant >= 100) dispatch_ax8<T, true>(E, gid, lat, G, u, y, err, variant - 100, s, pdl);
+  else dispatch_ax8<T, false>(E, gid, lat, G, u, y, err, variant, s, pdl);
 }
 
 template <typename T>
@@ -854,9 +872,9 @@ template bool sem_ax8_batched_fits<double>(int);
 template bool sem_ax8_variant_fits<float>(int);
 template bool sem_ax8_variant_fits<double>(int);
 template void sem_ax8<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
-                             unsigned*, int, cudaStream_t);
+                             unsigned*, int, cudaStream_t, bool);
 template void sem_ax8<double>(int64_t, const uint32_t*, const Lattice&, const double*, const double*, double*,
-                              unsigned*, int, cudaStream_t);
+                              unsigned*, int, cudaStream_t, bool);
 template void sem_ax8_batched<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
                                      unsigned*, int, int, int64_t, cudaStream_t);
 template void sem_ax8_batched<double>(int64_t, const uint32_t*, const Lattice&, const double*, const double*,
