@@ -135,7 +135,9 @@ int chebmg_launch_count(const chebmg_ctx* ctx, int64_t* count);
  * in `dtype`: 1, 2 or 4 elements per thread block, or 12 / 14 for the persistent pipelined
  * kernel with 2 / 4 elements per block, or 21 / 22 for 1 / 2 elements per block with the
  * geometric factors read from global memory where used (no shared-memory copy: more blocks
- * per SM); +100 when global ids are computed from the box lattice instead of read from the
+ * per SM), or 31 / 32 for the persistent kernel with 1 / 2 elements per block and one
+ * geometric-factor buffer (refilled during the second half of each element batch: half the
+ * shared memory, more blocks per SM); +100 when global ids are computed from the box lattice instead of read from the
  * element-to-global map (0 if the level does not use that kernel). */
 int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* elements_per_block);
 /* Overrides that choice (same codes); EINVAL for other levels or codes. */

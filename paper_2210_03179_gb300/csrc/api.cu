@@ -263,9 +263,8 @@ void read_cscal(chebmg_ctx* c) {
 }
 
 // y = A x on level j; for SEM y must be zero on entry (element contributions accumulate).
-// pdl: the order-7 kernel may launch as a programmatic dependent of the preceding kernel.
 template <typename T>
-void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld, bool pdl = false) {
+void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld) {
   Level& L = c->L[j];
   const int dt = dt_of<T>();
   if (L.type == TYPE_SEM) {
@@ -273,7 +272,7 @@ void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld, b
       sem_ax8_batched<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.beb[dt], nb, ld,
                          c->s);
     else if (L.Q == 8)
-      sem_ax8<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s, pdl);
+      sem_ax8<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s);
     else
       sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s, nb,
                 ld);
@@ -285,8 +284,8 @@ void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld, b
 
 // y = A x on level j for the current batch (y zero on entry for SEM).
 template <typename T>
-void apply_into(chebmg_ctx* c, int j, const T* x, T* y, bool pdl = false) {
-  apply_into_ld<T>(c, j, x, y, c->nb, ldv(c, c->L[j]), pdl);
+void apply_into(chebmg_ctx* c, int j, const T* x, T* y) {
+  apply_into_ld<T>(c, j, x, y, c->nb, ldv(c, c->L[j]));
 }
 
 template <typename T>
@@ -394,6 +393,8 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
   Level& L = c->L[j];
   const int64_t n = L.n;
   const int nb = c->nb;
+  // one right-hand side: the step kernels launch as programmatic dependents of each other
+  const PdlScope pdl_(g_pdl || nb == 1);
   const int64_t ld = ldv(c, L);
   T* r = vec<T>(L, VR);
   T* d = vec<T>(L, VD);
@@ -420,16 +421,13 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
     if (!c->beta_ovr.empty() && (int)c->beta_ovr.size() == order) beta = c->beta_ovr.data();
     cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), x_zero ? 1 : 0, c->s, nb, ld);
     const double beta_k = beta ? beta[order - 1] : 1.0;
-    // single right-hand side: each kernel of the step loop launches as a programmatic dependent
-    // of the one before, so its start overlaps that kernel's tail (both wait before reading)
-    const bool pdl = nb == 1;
     for (int i = 1; i < order; ++i) {
-      apply_into<T>(c, j, d, y, pdl);
+      apply_into<T>(c, j, d, y);
       const double c1 = (2.0 * i - 1.0) / (2.0 * i + 3.0);
       const double c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lmax);
       // the last step also applies the final update x += beta_k d_k (one pass fewer)
       cheb4_step<T>(n, x, r, d, y, S, beta ? beta[i - 1] : 1.0, c1, c2, c->s, nb, ld,
-                    i + 1 == order ? beta_k : 0.0, pdl);
+                    i + 1 == order ? beta_k : 0.0);
     }
     if (order == 1 || beta_k == 0.0) axpy<T>(n, beta_k, d, x, c->s, nb, ld);
   }
@@ -888,7 +886,7 @@ void autotune_ax8(chebmg_ctx* c, int j) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_eb = 2;
-  for (int eb : {1, 2, 4, 12, 14, 21, 22, 101, 102, 104, 112, 114, 121, 122}) {
+  for (int eb : {1, 2, 4, 12, 14, 21, 22, 31, 32, 101, 102, 104, 112, 114, 121, 122, 131, 132}) {
     if (!sem_ax8_variant_fits<T>(eb)) continue;
     if (eb >= 100 && !L.boxed) continue;   // lattice ids need the box lattice
     L.eb[dt] = eb;
@@ -2428,7 +2426,8 @@ int chebmg_set_tile_choice(chebmg_ctx* c, int level, int dtype, int variant) {
   if (L.type != TYPE_SEM || L.Q != 8) return CHEBMG_EINVAL;
   const int base = variant % 100;
   if ((variant != base && variant != base + 100) ||
-      (base != 1 && base != 2 && base != 4 && base != 12 && base != 14 && base != 21 && base != 22))
+      (base != 1 && base != 2 && base != 4 && base != 12 && base != 14 && base != 21 && base != 22 && base != 31 &&
+       base != 32))
     return CHEBMG_EINVAL;
   const bool fits = dtype == CHEBMG_F64 ? sem_ax8_variant_fits<double>(variant) : sem_ax8_variant_fits<float>(variant);
   if (!fits || (variant >= 100 && !L.boxed)) return CHEBMG_EINVAL;
@@ -2622,6 +2621,7 @@ int chebmg_inv_diagonal(chebmg_ctx* c, int level, int dtype, void* out) {
 int chebmg_smooth(chebmg_ctx* c, int level, int dtype, const void* b, void* x, int order, int x_is_zero) {
   return guard([&]() -> int {
     enter(c);
+    const PdlScope pdl_(c->nb == 1);
     Level& L = level_checked(c, level);
     check_dtype(c, dtype);
     if (level + 1 >= (int)c->L.size()) throw Error(CHEBMG_EINVAL, "the coarsest level is not smoothed");
@@ -2687,6 +2687,7 @@ int chebmg_coarse_solve(chebmg_ctx* c, const double* r, double* z, int* iters) {
 int chebmg_vcycle(chebmg_ctx* c, const double* r, double* z) {
   return guard([&]() -> int {
     enter(c);
+    const PdlScope pdl_(c->nb == 1);
     if (!r || !z) throw Error(CHEBMG_EINVAL, "NULL vector");
     reset_coarse_sticky(c);
     int rc = vcycle_top(c, r, z);
@@ -2701,6 +2702,7 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
                      double* relres, double* history) {
   return guard([&]() -> int {
     enter(c);
+    const PdlScope pdl_(c->nb == 1);   // the solve's kernels launch as programmatic dependents
     if (!b || !u || maxit < 0 || !(rtol > 0.0)) throw Error(CHEBMG_EINVAL, "bad solve arguments");
     Level& L = c->L[0];
     const int64_t n = L.n;
@@ -2976,6 +2978,7 @@ int chebmg_gmres_solve(chebmg_ctx* c, const double* b, double* u, double rtol, i
     enter(c);
     if (!b || !u || maxit < 0 || !(rtol > 0.0) || restart < 1 || restart + 1 > gmres_max_basis())
       throw Error(CHEBMG_EINVAL, "bad GMRES arguments");
+    const PdlScope pdl_(c->nb == 1);
     return gmres_solve(c, b, u, rtol, restart, maxit, iters, relres, history);
   });
 }

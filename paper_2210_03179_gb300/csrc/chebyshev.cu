@@ -18,8 +18,6 @@ inline unsigned grid_for(int64_t n, int bs) {
   return (unsigned)g;
 }
 
-inline void count() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-
 }  // namespace
 
 // ===========================================================================
@@ -29,6 +27,7 @@ template <typename T>
 __global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                              T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD, T c0,
                              int x_is_zero, int64_t ld) {
+  pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     T rv;
@@ -104,11 +103,10 @@ template <typename T, bool VEC>
 __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
                              T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, T beta_next,
                              int64_t ld) {
-  // Launched as a programmatic dependent of the operator kernel (a no-op otherwise): the launch
-  // overlaps that kernel's end, and everything read here is its output or older, so wait for it
-  // before the first load.  (Triggering the next kernel early as well was measured slower: its
-  // waiting blocks cost this grid's last wave more than they saved.)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // Everything read here is the operator kernel's output or older: wait for that kernel before
+  // the first load.  (Triggering the next kernel early as well, griddepcontrol.launch_dependents,
+  // was measured slower: its waiting blocks cost this grid's last wave more than they saved.)
+  pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
   using VT = typename V16<T>::type;
   constexpr int L = V16<T>::L;
@@ -140,6 +138,7 @@ template <typename T>
 __global__ void k_cheb1_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                              T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD,
                              T inv_theta, int x_is_zero, int64_t ld) {
+  pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     T rv;
@@ -158,6 +157,7 @@ __global__ void k_cheb1_init(int64_t n, const T* __restrict__ b, T* __restrict__
 template <typename T>
 __global__ void k_cheb1_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
                              T* __restrict__ y, const T* __restrict__ invD, T c1, T c2, int64_t ld) {
+  pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const T dv = d[g];
@@ -171,6 +171,7 @@ __global__ void k_cheb1_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
 
 template <typename T>
 __global__ void k_axpy(int64_t n, T a, const T* __restrict__ d, T* __restrict__ x, int64_t ld) {
+  pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; d += off_; x += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     x[g] += a * d[g];
@@ -178,6 +179,7 @@ __global__ void k_axpy(int64_t n, T a, const T* __restrict__ d, T* __restrict__ 
 
 template <typename T>
 __global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y, T* __restrict__ r, int64_t ld) {
+  pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; y += off_; r += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     r[g] = b[g] - y[g];
@@ -187,6 +189,7 @@ __global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y
 
 template <typename Tin, typename Tout>
 __global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out, int64_t ldi, int64_t ldo) {
+  pdl_wait();
   in += (int64_t)blockIdx.y * ldi;
   out += (int64_t)blockIdx.y * ldo;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
@@ -195,6 +198,7 @@ __global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__
 
 __global__ void k_masked_copy(int64_t n, const double* __restrict__ in, const double* __restrict__ invD,
                               double* __restrict__ out, int64_t ldi, int64_t ldo) {
+  pdl_wait();
   in += (int64_t)blockIdx.y * ldi;
   out += (int64_t)blockIdx.y * ldo;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
@@ -206,70 +210,50 @@ constexpr int kVecThreads = 256;
 template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0, int x_is_zero,
                 cudaStream_t s, int nb, int64_t ld) {
-  k_cheb4_init<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)c0,
-                                                                             x_is_zero, ld ? ld : n);
-  count();
+  launch_dep(k_cheb4_init<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, x, r, d, y, invD,
+             (T)c0, x_is_zero, ld ? ld : n);
 }
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
-                cudaStream_t s, int nb, int64_t ld, double beta_next, bool pdl) {
+                cudaStream_t s, int nb, int64_t ld, double beta_next) {
   if (!ld) ld = n;
   const uintptr_t align = (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
-  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0) && pdl) {
-    // programmatic dependent launch: the blocks may start while the operator kernel drains
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb);
-    cfg.blockDim = dim3(kVecThreads);
-    cfg.stream = s;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr.val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_cheb4_step<T, true>, n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
-  } else if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
-    k_cheb4_step<T, true><<<dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), kVecThreads, 0, s>>>(
-        n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
+  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
+    launch_dep(k_cheb4_step<T, true>, dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), dim3(kVecThreads), 0, s,
+               n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
   else
-    k_cheb4_step<T, false><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(
-        n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
-  count();
+    launch_dep(k_cheb4_step<T, false>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, x, r, d, y,
+               invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
 }
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
                 int x_is_zero, cudaStream_t s, int nb, int64_t ld) {
-  k_cheb1_init<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, x, r, d, y, invD, (T)inv_theta,
-                                                                             x_is_zero, ld ? ld : n);
-  count();
+  launch_dep(k_cheb1_init<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, x, r, d, y, invD,
+             (T)inv_theta, x_is_zero, ld ? ld : n);
 }
 template <typename T>
 void cheb1_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double c1, double c2, cudaStream_t s, int nb,
                 int64_t ld) {
-  k_cheb1_step<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, x, r, d, y, invD, (T)c1, (T)c2,
-                                                                             ld ? ld : n);
-  count();
+  launch_dep(k_cheb1_step<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, x, r, d, y, invD,
+             (T)c1, (T)c2, ld ? ld : n);
 }
 template <typename T>
 void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s, int nb, int64_t ld) {
-  k_axpy<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, (T)a, d, x, ld ? ld : n);
-  count();
+  launch_dep(k_axpy<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, (T)a, d, x, ld ? ld : n);
 }
 template <typename T>
 void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s, int nb, int64_t ld) {
-  k_residual<T><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, b, y, r, ld ? ld : n);
-  count();
+  launch_dep(k_residual<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, y, r, ld ? ld : n);
 }
 template <typename Tin, typename Tout>
 void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s, int nb, int64_t ldi, int64_t ldo) {
-  k_cast<Tin, Tout><<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, in, out, ldi ? ldi : n,
-                                                                               ldo ? ldo : n);
-  count();
+  launch_dep(k_cast<Tin, Tout>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, in, out,
+             ldi ? ldi : n, ldo ? ldo : n);
 }
 void masked_copy(int64_t n, const double* in, const double* invD, double* out, cudaStream_t s, int nb, int64_t ldi,
                  int64_t ldo) {
-  k_masked_copy<<<dim3(grid_for(n, kVecThreads), nb), kVecThreads, 0, s>>>(n, in, invD, out, ldi ? ldi : n,
-                                                                           ldo ? ldo : n);
-  count();
+  launch_dep(k_masked_copy, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, in, invD, out,
+             ldi ? ldi : n, ldo ? ldo : n);
 }
 
 
@@ -277,7 +261,7 @@ void masked_copy(int64_t n, const double* in, const double* invD, double* out, c
   template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t, int,   \
-                              int64_t, double, bool);                                                   \
+                              int64_t, double);                                                         \
   template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t, int, int64_t); \

@@ -12,6 +12,45 @@ namespace chebmg {
 // Number of kernel launches issued by this library in this process.
 extern std::atomic<int64_t> g_launches;
 
+// Programmatic dependent launch.  While g_pdl is set on the calling host thread (single
+// right-hand-side solves, V-cycles and smoother applications set it while they enqueue), the
+// kernels of the solve path are launched as programmatic dependents of the kernel before them
+// in the stream: their blocks may be scheduled while that kernel drains, and each of them
+// executes pdl_wait() -- which returns once the preceding grid has completed and its memory
+// operations are visible -- before its first global memory access.  Launches into a stream
+// that is being captured are ordinary launches.
+extern thread_local bool g_pdl;
+struct PdlScope {
+  bool old;
+  explicit PdlScope(bool on) : old(g_pdl) { g_pdl = on; }
+  ~PdlScope() { g_pdl = old; }
+  PdlScope(const PdlScope&) = delete;
+  PdlScope& operator=(const PdlScope&) = delete;
+};
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+inline bool pdl_on(cudaStream_t s) {
+  if (!g_pdl) return false;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusNone;
+}
+// Launches kernel k (which must begin with pdl_wait()) as a programmatic dependent when
+// pdl_on(s), else as an ordinary launch; counts the launch.
+template <typename... KArgs, typename... Args>
+inline void launch_dep(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = pdl_on(s) ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 // Scalar slots of the device-side reduction buffer (FP64).
 enum Slot {
   S_RZ = 0,      // (r, z) of the current Krylov iteration
@@ -67,13 +106,14 @@ void sem_to_x2(int64_t n, const double* in, void* out, cudaStream_t s);
 void sem_ax8_x2(int64_t E, const uint32_t* gid, const Lattice& lat, const void* G, const double* u, double* y,
                 unsigned* err, int variant, cudaStream_t s, int nb = 1, int64_t ld = 0, int rb = 1);
 // variant chosen per level by a setup-time autotuner: 1, 2 or 4 elements per thread block,
-// or 12 / 14 for the persistent software-pipelined kernel with 2 / 4 elements; +100 computes
-// global ids from the box lattice instead of reading the element-to-global map.
-// pdl: the persistent variants (12, 14) launch as programmatic dependents of the preceding kernel
-// (the first geometric-factor copy starts before waiting for it).
+// or 12 / 14 for the persistent software-pipelined kernel with 2 / 4 elements, 31 / 32 for that
+// kernel with 1 / 2 elements and a single geometric-factor buffer, 21 / 22 for factors read
+// where used; +100 computes global ids from the box lattice instead of reading the
+// element-to-global map.  Programmatic dependent launch (g_pdl) on every single-vector variant;
+// the persistent ones start their first geometric-factor copy before pdl_wait().
 template <typename T>
 void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
-             unsigned* err, int variant, cudaStream_t s, bool pdl = false);
+             unsigned* err, int variant, cudaStream_t s);
 // Batched form: nb right-hand sides at leading dimension ld.  variant = 1000 * RB + (100 if
 // implicit ids) + EB: a block stages the geometric factors of EB elements once and applies them
 // to RB right-hand sides; EB + 10 (EB 1 or 2) takes the right-hand sides two at a time through
@@ -173,12 +213,10 @@ template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0,
                 int x_is_zero, cudaStream_t s, int nb = 1, int64_t ld = 0);
 // 4th kind step: x += beta d; r -= y; d = c1 d + c2 S r; y = 0; then, if beta_next != 0 (the
-// last step), the final update x += beta_next d with the new d.  pdl: launch as a programmatic
-// dependent of the preceding kernel (its blocks may start during that kernel's tail and wait).
+// last step), the final update x += beta_next d with the new d.
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1,
-                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0, double beta_next = 0.0,
-                bool pdl = false);
+                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0, double beta_next = 0.0);
 // 1st kind init: r = S (b - y) (or S b), d = r / theta, y = 0 (x = 0 if x_is_zero).
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,

@@ -17,6 +17,7 @@
 namespace chebmg {
 
 std::atomic<int64_t> g_launches{0};
+thread_local bool g_pdl = false;
 
 namespace {
 
@@ -76,6 +77,7 @@ k_sem_ax(int64_t E, const uint32_t* __restrict__ gid, const T* __restrict__ G,
     g22 = Ge[5 * NP];
   }
   const uint32_t id = valid ? gid[e * NP + p] : kGidDirichlet;
+  pdl_wait();   // u and y may come from the kernel before (programmatic dependent launch)
   T* su = s_u + le * NP;
   su[p] = (id & kGidDirichlet) ? T(0) : u[id & kGidMask];
   __syncthreads();
@@ -114,8 +116,7 @@ static void launch_sem_ax(int64_t E, const uint32_t* gid, const T* G, const T* D
                           cudaStream_t s, int nb, int64_t ld) {
   using S = SemShape<Q>;
   const unsigned blocks = (unsigned)((E + S::EPB - 1) / S::EPB);
-  k_sem_ax<T, Q><<<dim3(blocks, nb), S::THREADS, 0, s>>>(E, gid, G, D, u, y, ld);
-  count();
+  launch_dep(k_sem_ax<T, Q>, dim3(blocks, nb), dim3(S::THREADS), 0, s, E, gid, G, D, u, y, ld);
 }
 
 template <typename T>
@@ -146,6 +147,7 @@ template <typename T>
 __global__ void __launch_bounds__(kTransferThreads)
 k_sem_restrict(int Qf, int Qc, const uint32_t* __restrict__ gidf, const uint32_t* __restrict__ gidc,
                const T* __restrict__ J, const T* __restrict__ rf, T* __restrict__ rc, int64_t ldf, int64_t ldc) {
+  pdl_wait();
   rf += (int64_t)blockIdx.y * ldf;
   rc += (int64_t)blockIdx.y * ldc;
   extern __shared__ unsigned char smem_raw[];
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(kTransferThreads)
 k_sem_prolong(int Qf, int Qc, const uint32_t* __restrict__ gidf, const uint32_t* __restrict__ gidc,
               const T* __restrict__ J, const T* __restrict__ zc, T* __restrict__ zf, int accumulate, int64_t ldf,
               int64_t ldc) {
+  pdl_wait();
   zf += (int64_t)blockIdx.y * ldf;
   zc += (int64_t)blockIdx.y * ldc;
   extern __shared__ unsigned char smem_raw[];
@@ -241,17 +244,15 @@ static size_t transfer_smem(int Qf, int Qc) {
 template <typename T>
 void sem_restrict(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc, const T* J,
                   const T* rf, T* rc, cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
-  k_sem_restrict<T><<<dim3((unsigned)E, nb), kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(
-      Qf, Qc, gidf, gidc, J, rf, rc, ldf, ldc);
-  count();
+  launch_dep(k_sem_restrict<T>, dim3((unsigned)E, nb), dim3(kTransferThreads), transfer_smem<T>(Qf, Qc), s, Qf, Qc,
+             gidf, gidc, J, rf, rc, ldf, ldc);
 }
 
 template <typename T>
 void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t* gidc, const T* J,
                  const T* zc, T* zf, int accumulate, cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
-  k_sem_prolong<T><<<dim3((unsigned)E, nb), kTransferThreads, transfer_smem<T>(Qf, Qc), s>>>(
-      Qf, Qc, gidf, gidc, J, zc, zf, accumulate, ldf, ldc);
-  count();
+  launch_dep(k_sem_prolong<T>, dim3((unsigned)E, nb), dim3(kTransferThreads), transfer_smem<T>(Qf, Qc), s, Qf, Qc,
+             gidf, gidc, J, zc, zf, accumulate, ldf, ldc);
 }
 
 // ===========================================================================
@@ -260,6 +261,7 @@ void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t
 template <typename T>
 __global__ void k_fd_apply(int mx, int my, Stencil9<T> st, const T* __restrict__ u, T* __restrict__ y,
                            int64_t ld) {
+  pdl_wait();
   u += (int64_t)blockIdx.z * ld;   // right-hand side of a batch
   y += (int64_t)blockIdx.z * ld;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -284,14 +286,14 @@ template <typename T>
 void fd_apply(int mx, int my, const Stencil9<T>& st, const T* u, T* y, cudaStream_t s, int nb, int64_t ld) {
   dim3 bs(32, 8);
   dim3 gs((mx + 31) / 32, (my + 7) / 8, nb);
-  k_fd_apply<T><<<gs, bs, 0, s>>>(mx, my, st, u, y, ld);
-  count();
+  launch_dep(k_fd_apply<T>, gs, bs, 0, s, mx, my, st, u, y, ld);
 }
 
 // rc(I,J) = sum_{|a|,|b| < c} w_a w_b rf(c(I+1)-1+b, c(J+1)-1+a), w_d = (c - |d|)/c
 template <typename T>
 __global__ void k_fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* __restrict__ rf,
                               T* __restrict__ rc, int64_t ldf, int64_t ldc) {
+  pdl_wait();
   rf += (int64_t)blockIdx.z * ldf;
   rc += (int64_t)blockIdx.z * ldc;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -318,6 +320,7 @@ __global__ void k_fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T
 template <typename T>
 __global__ void k_fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* __restrict__ zc,
                              T* __restrict__ zf, int accumulate, int64_t ldf, int64_t ldc) {
+  pdl_wait();
   zf += (int64_t)blockIdx.z * ldf;
   zc += (int64_t)blockIdx.z * ldc;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,8 +350,7 @@ void fd_restrict(int mfx, int mfy, int mcx, int mcy, int c, const T* rf, T* rc, 
                  int64_t ldf, int64_t ldc) {
   dim3 bs(16, 16);
   dim3 gs((mcx + 15) / 16, (mcy + 15) / 16, nb);
-  k_fd_restrict<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, rf, rc, ldf, ldc);
-  count();
+  launch_dep(k_fd_restrict<T>, gs, bs, 0, s, mfx, mfy, mcx, mcy, c, rf, rc, ldf, ldc);
 }
 
 template <typename T>
@@ -356,12 +358,12 @@ void fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* zc, T* zf, i
                 cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
   dim3 bs(32, 8);
   dim3 gs((mfx + 31) / 32, (mfy + 7) / 8, nb);
-  k_fd_prolong<T><<<gs, bs, 0, s>>>(mfx, mfy, mcx, mcy, c, zc, zf, accumulate, ldf, ldc);
-  count();
+  launch_dep(k_fd_prolong<T>, gs, bs, 0, s, mfx, mfy, mcx, mcy, c, zc, zf, accumulate, ldf, ldc);
 }
 
 __global__ void k_dense_matvec(int n, const double* __restrict__ M, const double* __restrict__ x,
                                double* __restrict__ y, int64_t ld) {
+  pdl_wait();
   x += (int64_t)blockIdx.y * ld;
   y += (int64_t)blockIdx.y * ld;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -372,8 +374,7 @@ __global__ void k_dense_matvec(int n, const double* __restrict__ M, const double
 }
 
 void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s, int nb, int64_t ld) {
-  k_dense_matvec<<<dim3((n + 127) / 128, nb), 128, 0, s>>>(n, M, x, y, ld);
-  count();
+  launch_dep(k_dense_matvec, dim3((n + 127) / 128, nb), dim3(128), 0, s, n, M, x, y, ld);
 }
 
 // ===========================================================================
@@ -409,6 +410,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 __global__ void __launch_bounds__(kRedThreads)
 k_dot2_partial(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
                const double* __restrict__ a1, const double* __restrict__ b1, double* __restrict__ partial) {
+  pdl_wait();
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     s0 += a0[g] * b0[g];
@@ -440,6 +442,7 @@ __device__ void apply_post(int post, double* scal) {
 // One block: sums the partials of two slots in a fixed order, then the post-op.
 __global__ void __launch_bounds__(kRedThreads)
 k_dot2_finish(const double* __restrict__ partial, int slot0, int slot1, int post, double* __restrict__ scal) {
+  pdl_wait();
   double s0 = 0.0, s1 = 0.0;
   for (int q = threadIdx.x; q < kRedBlocks; q += blockDim.x) {
     s0 += partial[q];
@@ -455,15 +458,16 @@ k_dot2_finish(const double* __restrict__ partial, int slot0, int slot1, int post
 
 void dot2(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, int slot0,
           int slot1, int post, double* partial, double* scal, cudaStream_t s) {
-  k_dot2_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a0, b0, a1, b1, partial);
-  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, slot0, a1 ? slot1 : -1, post, scal);
-  g_launches.fetch_add(2, std::memory_order_relaxed);
+  launch_dep(k_dot2_partial, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, a0, b0, a1, b1, partial);
+  launch_dep(k_dot2_finish, dim3(1), dim3(kRedThreads), 0, s, (const double*)partial, slot0, a1 ? slot1 : -1, post,
+             scal);
 }
 
 __global__ void __launch_bounds__(kRedThreads)
 k_fcg_update_xr32(int64_t n, double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
                   const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ partial,
                   const double* __restrict__ scal) {
+  pdl_wait();
   const double alpha = scal[S_ALPHA];
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
@@ -482,15 +486,17 @@ k_fcg_update_xr32(int64_t n, double* __restrict__ x, double* __restrict__ r, flo
 
 void fcg_update_xr32(int64_t n, double* x, double* r, float* r32, const double* p, const double* q,
                      double* partial, double* scal, cudaStream_t s) {
-  k_fcg_update_xr32<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, r32, p, q, partial, scal);
-  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, -1, POST_NONE, scal);
-  g_launches.fetch_add(2, std::memory_order_relaxed);
+  launch_dep(k_fcg_update_xr32, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, x, r, r32, p, q, partial,
+             (const double*)scal);
+  launch_dep(k_dot2_finish, dim3(1), dim3(kRedThreads), 0, s, (const double*)partial, (int)S_RR, -1, (int)POST_NONE,
+             scal);
 }
 
 template <typename Tz>
 __global__ void __launch_bounds__(kRedThreads)
 k_dot_zr_zq(int64_t n, const Tz* __restrict__ z, const double* __restrict__ r, const double* __restrict__ q,
             double* __restrict__ partial) {
+  pdl_wait();
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const double zv = to_f64(z[g]);
@@ -507,9 +513,9 @@ k_dot_zr_zq(int64_t n, const Tz* __restrict__ z, const double* __restrict__ r, c
 template <typename Tz>
 void dot_zr_zq(int64_t n, const Tz* z, const double* r, const double* q, int post, double* partial, double* scal,
                cudaStream_t s) {
-  k_dot_zr_zq<Tz><<<kRedBlocks, kRedThreads, 0, s>>>(n, z, r, q, partial);
-  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_ZR, q ? S_ZQ : -1, post, scal);
-  g_launches.fetch_add(2, std::memory_order_relaxed);
+  launch_dep(k_dot_zr_zq<Tz>, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, z, r, q, partial);
+  launch_dep(k_dot2_finish, dim3(1), dim3(kRedThreads), 0, s, (const double*)partial, (int)S_ZR,
+             q ? (int)S_ZQ : -1, post, scal);
 }
 template void dot_zr_zq<float>(int64_t, const float*, const double*, const double*, int, double*, double*,
                                cudaStream_t);
@@ -519,6 +525,7 @@ template void dot_zr_zq<double>(int64_t, const double*, const double*, const dou
 template <typename Tz>
 __global__ void k_update_p_from(int64_t n, const Tz* __restrict__ z, double* __restrict__ p,
                                 const double* __restrict__ scal, int first) {
+  pdl_wait();
   const double beta = first ? 0.0 : scal[S_BETA];
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     p[g] = first ? to_f64(z[g]) : to_f64(z[g]) + beta * p[g];
@@ -526,28 +533,29 @@ __global__ void k_update_p_from(int64_t n, const Tz* __restrict__ z, double* __r
 
 template <typename Tz>
 void update_p_from(int64_t n, const Tz* z, double* p, const double* scal, bool first, cudaStream_t s) {
-  k_update_p_from<Tz><<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, z, p, scal, first ? 1 : 0);
-  count();
+  launch_dep(k_update_p_from<Tz>, dim3(grid_for(n, kVecThreads)), dim3(kVecThreads), 0, s, n, z, p, scal,
+             first ? 1 : 0);
 }
 template void update_p_from<float>(int64_t, const float*, double*, const double*, bool, cudaStream_t);
 template void update_p_from<double>(int64_t, const double*, double*, const double*, bool, cudaStream_t);
 
 __global__ void k_update_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                            const double* __restrict__ scal) {
+  pdl_wait();
   const double beta = scal[S_BETA];
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     p[g] = z[g] + beta * p[g];
 }
 
 void update_p(int64_t n, const double* z, double* p, const double* scal, cudaStream_t s) {
-  k_update_p<<<grid_for(n, kVecThreads), kVecThreads, 0, s>>>(n, z, p, scal);
-  count();
+  launch_dep(k_update_p, dim3(grid_for(n, kVecThreads)), dim3(kVecThreads), 0, s, n, z, p, scal);
 }
 
 __global__ void __launch_bounds__(kRedThreads)
 k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
             const double* __restrict__ p, const double* __restrict__ q, const double* __restrict__ invD,
             double* __restrict__ partial, const double* __restrict__ scal) {
+  pdl_wait();
   const double alpha = scal[S_ALPHA];
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
@@ -568,9 +576,10 @@ k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double* _
 
 void cg_update(int64_t n, double* x, double* r, double* z, const double* p, const double* q,
                const double* invD, double* partial, double* scal, cudaStream_t s) {
-  k_cg_update<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, z, p, q, invD, partial, scal);
-  k_dot2_finish<<<1, kRedThreads, 0, s>>>(partial, S_RR, S_ZR, POST_BETA_CG, scal);
-  g_launches.fetch_add(2, std::memory_order_relaxed);
+  launch_dep(k_cg_update, dim3(kRedBlocks), dim3(kRedThreads), 0, s, n, x, r, z, p, q, invD, partial,
+             (const double*)scal);
+  launch_dep(k_dot2_finish, dim3(1), dim3(kRedThreads), 0, s, (const double*)partial, (int)S_RR, (int)S_ZR,
+             (int)POST_BETA_CG, scal);
 }
 
 // ===========================================================================

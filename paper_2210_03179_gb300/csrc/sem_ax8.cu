@@ -59,6 +59,7 @@ k_sem_ax8(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __r
                  : "memory");
     bulk_copy_g(sG, G + e0 * C::GELEM, bytes, &bar);
   }
+  pdl_wait();   // u and y may come from the kernel before (programmatic dependent launch)
 
   T* su = sU + le * C::STAGE;
   T* sr = sR + le * C::STAGE;
@@ -169,6 +170,7 @@ k_sem_ax8g(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
   uint32_t g[8];
   T col[8];
   column_ids<IMPLICIT>(gid, lat, e, valid, a, b, g);
+  pdl_wait();   // u and y may come from the kernel before (programmatic dependent launch)
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     col[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
@@ -231,20 +233,23 @@ k_sem_ax8g(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
 }
 
 // Persistent, software-pipelined variant: each block walks batches of EB elements
-// (blockIdx.x, blockIdx.x + gridDim.x, ...).  While it computes batch i, the TMA copy of
-// batch i+1's geometric factors runs into the second buffer and batch i+1's gather
-// (element-to-global ids and u values) is already in flight into registers.  Waits on the
-// copies are bounded like in k_sem_ax8.
-template <typename T, int EB, bool IMPLICIT>
+// (blockIdx.x, blockIdx.x + gridDim.x, ...), and batch i+1's gather (element-to-global ids
+// and u values) is in flight into registers while batch i is computed.  NB = 2: the TMA copy
+// of batch i+1's geometric factors runs into the second buffer during all of batch i.  NB = 1
+// (half the shared memory, so more blocks per SM): one buffer, refilled for batch i+1 as soon
+// as batch i's factor multiply has read it, so the copy overlaps the transposed passes, the
+// scatter and batch i+1's forward passes.  Waits on the copies are bounded like in k_sem_ax8.
+template <typename T, int EB, bool IMPLICIT, int NB = 2>
 __global__ void __launch_bounds__(64 * EB)
 k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
            const T* __restrict__ u, T* __restrict__ y, unsigned* __restrict__ err) {
+  static_assert(NB == 1 || NB == 2, "one or two geometric-factor buffers");
   using C = Ax8<T, EB>;
   constexpr int R = C::R, P = C::P;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
-  T* sG = reinterpret_cast<T*>(smem_raw);                 // [2][EB * GELEM]
-  T* sU = sG + 2 * EB * C::GELEM;
+  T* sG = reinterpret_cast<T*>(smem_raw);                 // [NB][EB * GELEM]
+  T* sU = sG + NB * EB * C::GELEM;
   T* sR = sU + EB * C::STAGE;
   T* sS = sR + EB * C::STAGE;
   const int tid = threadIdx.x;
@@ -275,10 +280,9 @@ k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
     for (int k = 0; k < 8; ++k) v[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
   };
   if (tid == 0) issue(batch, 0);
-  // Launched as a programmatic dependent of the preceding kernel (a no-op otherwise): u and y
-  // come from that kernel, so wait for it now -- after the first geometric-factor copy is on its
-  // way.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // u and y may come from the kernel before (programmatic dependent launch): wait for it now,
+  // after the first geometric-factor copy (G is never written by the solve) is on its way.
+  pdl_wait();
   uint32_t g[8];
   T col[8];
   gather(batch, g, col);
@@ -287,9 +291,9 @@ k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
   T* sr = sR + le * C::STAGE;
   T* ss = sS + le * C::STAGE;
   for (int it = 0; batch < nbatch; ++it, batch += gridDim.x) {
-    const int buf = it & 1;
+    const int buf = NB == 2 ? (it & 1) : 0;
     const int64_t next = batch + gridDim.x;
-    if (tid == 0 && next < nbatch) issue(next, buf ^ 1);
+    if (NB == 2 && tid == 0 && next < nbatch) issue(next, buf ^ 1);
 #pragma unroll
     for (int k = 0; k < 8; ++k) su[k * P + b * R + a] = col[k];
     T ut[8];
@@ -322,7 +326,7 @@ k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
       // let copies still in flight finish before the block leaves
       for (uint32_t w = 0; w < kWaitLimit; ++w)
         if (mbar_try_wait(&bar[buf], par)) break;
-      if (next < nbatch)
+      if (NB == 2 && next < nbatch)
         for (uint32_t w = 0; w < kWaitLimit; ++w)
           if (mbar_try_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u)) break;
       return;
@@ -343,6 +347,8 @@ k_sem_ax8p(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
     T yt[8];
     line8<T, 1>(wt, yt);
     __syncthreads();
+    // single buffer: every thread has read it (the barrier above), so batch i+1's copy starts
+    if (NB == 1 && tid == 0 && next < nbatch) issue(next, 0);
     {
       T v[8], o[8];
       ld_row(sr + b * P + a * R, v);
@@ -690,8 +696,7 @@ static void launch_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const
     configured = true;
   }
   const unsigned blocks = (unsigned)((E + EB - 1) / EB);
-  k_sem_ax8<T, EB, IM><<<blocks, 64 * EB, C::smem_bytes(), s>>>(E, gid, lat, G, u, y, err);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  launch_dep(k_sem_ax8<T, EB, IM>, dim3(blocks), dim3(64 * EB), C::smem_bytes(), s, E, gid, lat, G, u, y, err);
 }
 
 template <typename T, int EB, bool IM>
@@ -705,42 +710,26 @@ static void launch_ax8g(int64_t E, const uint32_t* gid, const Lattice& lat, cons
     configured = true;
   }
   const unsigned blocks = (unsigned)((E + EB - 1) / EB);
-  k_sem_ax8g<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  launch_dep(k_sem_ax8g<T, EB, IM>, dim3(blocks), dim3(64 * EB), smem, s, E, gid, lat, G, u, y);
 }
 
-template <typename T, int EB, bool IM>
+template <typename T, int EB, bool IM, int NB = 2>
 static void launch_ax8p(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
-                        unsigned* err, cudaStream_t s, bool pdl) {
+                        unsigned* err, cudaStream_t s) {
   using C = Ax8<T, EB>;
-  const size_t smem = sizeof(T) * (size_t)EB * (2 * C::GELEM + 3 * C::STAGE);
+  const size_t smem = sizeof(T) * (size_t)EB * (NB * C::GELEM + 3 * C::STAGE);
   static int grid = 0;
   if (grid == 0) {
-    cudaFuncSetAttribute(k_sem_ax8p<T, EB, IM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sem_ax8p<T, EB, IM, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_ax8p<T, EB, IM>, 64 * EB, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_ax8p<T, EB, IM, NB>, 64 * EB, smem);
     grid = sms * (per_sm > 0 ? per_sm : 1);
   }
   const int64_t nbatch = (E + EB - 1) / EB;
   const unsigned blocks = (unsigned)(nbatch < grid ? nbatch : grid);
-  if (pdl) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(64 * EB);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr.val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_sem_ax8p<T, EB, IM>, E, gid, lat, G, u, y, err);
-  } else {
-    k_sem_ax8p<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y, err);
-  }
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  launch_dep(k_sem_ax8p<T, EB, IM, NB>, dim3(blocks), dim3(64 * EB), smem, s, E, gid, lat, G, u, y, err);
 }
 
 template <typename T, int EB, bool IM>
@@ -784,6 +773,8 @@ size_t sem_ax8_smem(int eb) {
     case 4: return sizeof(T) * 4 * (Ax8<T, 4>::GELEM + 3 * Ax8<T, 4>::STAGE);
     case 12: return sizeof(T) * 2 * (2 * Ax8<T, 2>::GELEM + 3 * Ax8<T, 2>::STAGE);
     case 14: return sizeof(T) * 4 * (2 * Ax8<T, 4>::GELEM + 3 * Ax8<T, 4>::STAGE);
+    case 31: return sizeof(T) * 1 * (Ax8<T, 1>::GELEM + 3 * Ax8<T, 1>::STAGE);
+    case 32: return sizeof(T) * 2 * (Ax8<T, 2>::GELEM + 3 * Ax8<T, 2>::STAGE);
     case 21: return sizeof(T) * 1 * 3 * Ax8<T, 1>::STAGE;
     case 22: return sizeof(T) * 2 * 3 * Ax8<T, 2>::STAGE;
     default: return ~size_t(0);
@@ -810,23 +801,25 @@ bool sem_ax8_variant_fits(int eb) {
 
 template <typename T, bool IM>
 static void dispatch_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
-                         unsigned* err, int eb, cudaStream_t s, bool pdl) {
+                         unsigned* err, int eb, cudaStream_t s) {
   switch (eb) {
     case 21: launch_ax8g<T, 1, IM>(E, gid, lat, G, u, y, s); break;
     case 22: launch_ax8g<T, 2, IM>(E, gid, lat, G, u, y, s); break;
     case 1: launch_ax8<T, 1, IM>(E, gid, lat, G, u, y, err, s); break;
     case 4: launch_ax8<T, 4, IM>(E, gid, lat, G, u, y, err, s); break;
-    case 12: launch_ax8p<T, 2, IM>(E, gid, lat, G, u, y, err, s, pdl); break;
-    case 14: launch_ax8p<T, 4, IM>(E, gid, lat, G, u, y, err, s, pdl); break;
+    case 12: launch_ax8p<T, 2, IM>(E, gid, lat, G, u, y, err, s); break;
+    case 14: launch_ax8p<T, 4, IM>(E, gid, lat, G, u, y, err, s); break;
+    case 31: launch_ax8p<T, 1, IM, 1>(E, gid, lat, G, u, y, err, s); break;
+    case 32: launch_ax8p<T, 2, IM, 1>(E, gid, lat, G, u, y, err, s); break;
     default: launch_ax8<T, 2, IM>(E, gid, lat, G, u, y, err, s); break;
   }
 }
 
 template <typename T>
 void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y, unsigned* err,
-             int variant, cudaStream_t s, bool pdl) {
-  if (variant >= 100) dispatch_ax8<T, true>(E, gid, lat, G, u, y, err, variant - 100, s, pdl);
-  else dispatch_ax8<T, false>(E, gid, lat, G, u, y, err, variant, s, pdl);
+             int variant, cudaStream_t s) {
+  if (variant >= 100) dispatch_ax8<T, true>(E, gid, lat, G, u, y, err, variant - 100, s);
+  else dispatch_ax8<T, false>(E, gid, lat, G, u, y, err, variant, s);
 }
 
 template <typename T>
@@ -872,9 +865,9 @@ template bool sem_ax8_batched_fits<double>(int);
 template bool sem_ax8_variant_fits<float>(int);
 template bool sem_ax8_variant_fits<double>(int);
 template void sem_ax8<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
-                             unsigned*, int, cudaStream_t, bool);
+                             unsigned*, int, cudaStream_t);
 template void sem_ax8<double>(int64_t, const uint32_t*, const Lattice&, const double*, const double*, double*,
-                              unsigned*, int, cudaStream_t, bool);
+                              unsigned*, int, cudaStream_t);
 template void sem_ax8_batched<float>(int64_t, const uint32_t*, const Lattice&, const float*, const float*, float*,
                                      unsigned*, int, int, int64_t, cudaStream_t);
 template void sem_ax8_batched<double>(int64_t, const uint32_t*, const Lattice&, const double*, const double*,

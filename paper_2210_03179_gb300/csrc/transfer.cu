@@ -72,6 +72,7 @@ template <typename T, int QF, int QC>
 __global__ void __launch_bounds__(64 * kEB)
 k_restrict_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ rf, T* __restrict__ rc, int64_t ldf,
                int64_t ldc) {
+  pdl_wait();   // rf (and the zeroed rc) may come from the kernel before
   rf += (int64_t)blockIdx.y * ldf;   // right-hand side of a batch
   rc += (int64_t)blockIdx.y * ldc;
   constexpr int NF = QF - 1, NC = QC - 1;
@@ -156,6 +157,7 @@ template <typename T, int QF, int QC>
 __global__ void __launch_bounds__(64 * kEB)
 k_prolong_box(int64_t E, Lattice Lf, Lattice Lc, const T* __restrict__ zc, T* __restrict__ zf, int accumulate,
               int64_t ldf, int64_t ldc) {
+  pdl_wait();   // zc and zf may come from the kernels before
   zf += (int64_t)blockIdx.y * ldf;
   zc += (int64_t)blockIdx.y * ldc;
   constexpr int NF = QF - 1, NC = QC - 1;
@@ -263,11 +265,12 @@ template <typename T>
 void restrict_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc, const T* rf, T* rc,
                   cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
   const dim3 blocks((unsigned)((E + kEB - 1) / kEB), nb);
-  if (Qf == 8 && Qc == 4) k_restrict_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
-  else if (Qf == 8 && Qc == 6) k_restrict_box<T, 8, 6><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
-  else if (Qf == 6 && Qc == 4) k_restrict_box<T, 6, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
-  else k_restrict_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, rf, rc, ldf, ldc);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (Qf == 8 && Qc == 4) launch_dep(k_restrict_box<T, 8, 4>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, rf, rc, ldf, ldc);
+  else if (Qf == 8 && Qc == 6)
+    launch_dep(k_restrict_box<T, 8, 6>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, rf, rc, ldf, ldc);
+  else if (Qf == 6 && Qc == 4)
+    launch_dep(k_restrict_box<T, 6, 4>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, rf, rc, ldf, ldc);
+  else launch_dep(k_restrict_box<T, 4, 2>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, rf, rc, ldf, ldc);
 }
 
 template <typename T>
@@ -275,14 +278,13 @@ void prolong_box(int Qf, int Qc, int64_t E, const Lattice& Lf, const Lattice& Lc
                  int accumulate, cudaStream_t s, int nb, int64_t ldf, int64_t ldc) {
   const dim3 blocks((unsigned)((E + kEB - 1) / kEB), nb);
   if (Qf == 8 && Qc == 4)
-    k_prolong_box<T, 8, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+    launch_dep(k_prolong_box<T, 8, 4>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
   else if (Qf == 8 && Qc == 6)
-    k_prolong_box<T, 8, 6><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+    launch_dep(k_prolong_box<T, 8, 6>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
   else if (Qf == 6 && Qc == 4)
-    k_prolong_box<T, 6, 4><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
+    launch_dep(k_prolong_box<T, 6, 4>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
   else
-    k_prolong_box<T, 4, 2><<<blocks, 64 * kEB, 0, s>>>(E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+    launch_dep(k_prolong_box<T, 4, 2>, blocks, dim3(64 * kEB), 0, s, E, Lf, Lc, zc, zf, accumulate, ldf, ldc);
 }
 
 template void restrict_box<float>(int, int, int64_t, const Lattice&, const Lattice&, const float*, float*,

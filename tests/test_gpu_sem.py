@@ -239,12 +239,12 @@ def test_bounded_barrier_wait_reports_timeout_and_context_survives(verts):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 4, 12, 14, 21, 22, 101, 102, 104, 112, 114, 121, 122])
+@pytest.mark.parametrize("variant", [1, 2, 4, 12, 14, 21, 22, 31, 32, 101, 102, 104, 112, 114, 121, 122, 131, 132])
 def test_every_order7_kernel_variant(verts, variant):
     # the setup autotuner may pick any of these; each must match the oracle
     L = SemLevel(verts, 7)
     s = solver(verts, (7, 3, 1), prec="mixed", lmax=[1.0, 1.0])
-    assert cm.chebmg_tile_choice(s.ctx, 0, F64) % 100 in (1, 2, 4, 12, 14, 21, 22)
+    assert cm.chebmg_tile_choice(s.ctx, 0, F64) % 100 in (1, 2, 4, 12, 14, 21, 22, 31, 32)
     x = np.where(L.dirichlet, 0.0, np.random.default_rng(variant).uniform(-1, 1, L.n))
     ref = L.apply_A(x)
     for dt, tol in ((F64, 1e-12), (F32, 2e-5)):
