@@ -232,7 +232,19 @@ BATCH_NE, BATCH_NRHS = 8, 64
 UNEVEN = [(ne, Nn) for ne in (4, 6, 8, 12) for Nn in (5, 7, 9)]
 
 
-def bench_batched(cm, W, torch, timed, reps):
+# Shared-memory bytes per point and right-hand side of the batched FP32 order-7 operator, counted
+# from the kernel source (4-byte words): staging the gathered column 4, the forward r and s
+# passes 8 + 8, the factor multiply (two derivatives read and written, six factors read) 40, the
+# transposed r and s passes 8 + 12, the scatter read 4 = 84 with the factors staged in shared
+# memory; 60 with them in registers (the six factor reads go); 72 taking the right-hand sides in
+# pairs (each factor read serves two).  Keyed by the variant's form, (variant % 100) // 10.
+BATCHED_SHARED_BYTES = {0: 84, 1: 72, 2: 60}
+BATCHED_FORMS = {0: "k_sem_ax8b (factors staged in shared memory once per block)",
+                 1: "k_sem_ax8b2 (right-hand sides in pairs through each line pass)",
+                 2: "k_sem_ax8bg (factors in registers across the block's right-hand sides)"}
+
+
+def bench_batched(cm, W, torch, timed, reps, sm_mhz=None):
     """64 right-hand sides on E = 8^3, N = 7 in one batched solve, and the uneven group of meshes
     E in {4^3, 6^3, 8^3, 12^3} x N in {5, 7, 9} (one right-hand side each) in one grouped solve,
     each against the same problems solved one after another by the single-right-hand-side
@@ -294,21 +306,31 @@ def bench_batched(cm, W, torch, timed, reps):
     Y32 = torch.zeros_like(X32)
     cm.chebmg_apply_A_batched(s32.ctx, 0, cm.CHEBMG_F32, X32, Y32)
     t_ax, _ = timed(lambda: cm.chebmg_apply_A_batched(s32.ctx, 0, cm.CHEBMG_F32, X32, Y32), 10)
+    t_zero, _ = timed(lambda: Y32.zero_(), 10)      # apply_A_batched zeroes Y first: take that out
+    t_k = max(t_ax - t_zero, 1e-9)
     Lb = BATCH_NE ** 3 * (NORDER + 1) ** 3
     alg = 4 * (6 * Lb + 2 * BATCH_NRHS * n)
     hbm = peaks().get("hbm_gbs") or 6800.0
-    # FP32 pipe: 152 SMs x 128 FMA/clock x 2 flops x max SM clock
-    fp32_peak = 152 * 128 * 2 * (peaks().get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
-    flops = 111 * Lb * BATCH_NRHS
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or peaks().get("sm_max_mhz") or 2070.0
+    form = (out["ax8_batched_variant"]["fp32"] % 100) // 10
+    shb = BATCHED_SHARED_BYTES[form] * Lb * BATCH_NRHS
+    shared_peak = 128 * sms * mhz * 1e6 / 1e9          # 32 banks x 4 bytes per SM per clock
+    # executed FP32 instructions per point and right-hand side: six line passes of 48 per
+    # 8-point line (8 even-odd sums, 32 chain FMAs, 8 recombinations) = 36, the factors 9, the
+    # two transposed-contribution additions 2
+    fp32_instr = 47 * Lb * BATCH_NRHS
+    fp32_peak = 128 * sms * mhz * 1e6 / 1e9           # G instructions/s: 128 FP32 lanes per SM
     out["roofline_batched_operator"] = {
-        "bound": "hbm", "kernel": "k_sem_ax8b<float> (64 RHS, geometric factors staged once per block) with the "
-                                  "output zeroing", "alg_bytes": alg, "time_us": t_ax * 1e6,
-        "achieved": alg / t_ax / 1e9, "peak": hbm, "unit": "GB/s", "frac": alg / t_ax / 1e9 / hbm,
-        "peak_source": "of measured" if peaks().get("hbm_gbs") else "of fallback",
-        "alu": {"achieved_tflops": flops / t_ax / 1e12, "peak_tflops": fp32_peak,
-                "frac": flops / t_ax / 1e12 / fp32_peak,
-                "peak_source": "FP32 pipe from unit counts and the maximum SM clock (152 x 128 FMA x 2)",
-                "flops": flops}}
+        "bound": "shared", "kernel": BATCHED_FORMS[form], "variant": out["ax8_batched_variant"]["fp32"],
+        "time_us": t_k * 1e6, "time_with_zeroing_us": t_ax * 1e6,
+        "shared_bytes": shb, "shared_bytes_per_point": BATCHED_SHARED_BYTES[form],
+        "achieved": shb / t_k / 1e9, "peak": shared_peak, "unit": "GB/s", "frac": shb / t_k / 1e9 / shared_peak,
+        "peak_source": f"unit count: 128 bytes / SM / clock x {sms} SMs x {mhz:.0f} MHz",
+        "hbm": {"alg_bytes": alg, "achieved": alg / t_k / 1e9, "peak": hbm, "frac": alg / t_k / 1e9 / hbm,
+                "peak_source": "of measured" if peaks().get("hbm_gbs") else "of fallback"},
+        "fp32_pipe": {"instructions": fp32_instr, "achieved": fp32_instr / t_k / 1e9, "peak": fp32_peak,
+                      "unit": "G instructions/s", "frac": fp32_instr / t_k / 1e9 / fp32_peak}}
     del X32, Y32
     s32.close()
     s64.close()
@@ -903,7 +925,7 @@ def main():
     if not args.no_batched:
         s32.close()
         s64.close()
-        line["batched"] = bench_batched(cm, W, torch, timed, max(1, min(args.steps, 3)))
+        line["batched"] = bench_batched(cm, W, torch, timed, max(1, min(args.steps, 3)), clk.get("sm_mhz"))
     if not args.no_schedules:
         s32.close()
         s64.close()

@@ -298,7 +298,9 @@ int chebmg_vcycle_batched(chebmg_ctx* ctx, int nrhs, const double* R, double* Z)
  * would): *variant = 1000 * right-hand sides per block + (100 if global ids come from the
  * box lattice) + elements per block of the batched order-7 operator on `level` (1, 2, 4; or
  * 11, 12 for 1 or 2 elements with the right-hand sides taken two at a time through every
- * line pass, at least 2 per block) (0 for other levels or nrhs = 1); *coarse_degree = degree of the Algorithm 2 preconditioner of the
+ * line pass, at least 2 per block; or, FP32 only, 21, 22 for 1 or 2 elements with the geometric
+ * factors held in registers across the block's right-hand sides instead of in shared memory)
+ * (0 for other levels or nrhs = 1); *coarse_degree = degree of the Algorithm 2 preconditioner of the
  * per-right-hand-side coarse CG (0 if the coarsest level is not solved that way). */
 int chebmg_batch_info(chebmg_ctx* ctx, int nrhs, int level, int dtype, int* variant,
                       int* coarse_degree);

@@ -1247,7 +1247,7 @@ void autotune_batch(chebmg_ctx* c, int nrhs) {
         int best_v = L.beb[dt];
         for (int rb : {1, 2, 4, 8, 16}) {
           if (rb > nrhs) break;
-          for (int eb : {1, 2, 4, 101, 102, 104, 11, 12, 111, 112}) {
+          for (int eb : {1, 2, 4, 101, 102, 104, 11, 12, 111, 112, 21, 22, 121, 122}) {
             if (eb >= 100 && !L.boxed) continue;
             if (eb % 100 >= 10 && rb < 2) continue;   // pairs of right-hand sides
             const int v = 1000 * rb + eb;
@@ -2905,9 +2905,9 @@ int chebmg_set_batch_tile_choice(chebmg_ctx* c, int nrhs, int level, int dtype, 
     check_dtype(c, dtype);
     if (L.type != TYPE_SEM || L.Q != 8 || nrhs < 2 || nrhs > 65535) throw Error(CHEBMG_EINVAL, "no batched variant");
     const int rb = variant / 1000, rest = variant % 1000, eb = rest % 100;
-    const bool paired = eb == 11 || eb == 12;
-    if (rb < 1 || rb > 64 || (rest != eb && rest != eb + 100) || (eb != 1 && eb != 2 && eb != 4 && !paired) ||
-        (paired && rb < 2))
+    const bool paired = eb == 11 || eb == 12, in_regs = eb == 21 || eb == 22;
+    if (rb < 1 || rb > 64 || (rest != eb && rest != eb + 100) ||
+        (eb != 1 && eb != 2 && eb != 4 && !paired && !in_regs) || (paired && rb < 2))
       throw Error(CHEBMG_EINVAL, "bad batched variant");
     const bool fits = dtype == CHEBMG_F64 ? sem_ax8_batched_fits<double>(variant) : sem_ax8_batched_fits<float>(variant);
     if (!fits || (dtype == CHEBMG_F32 && !L.G[CHEBMG_F32]) || (rest >= 100 && !L.boxed))

@@ -117,7 +117,7 @@ void sem_ax8(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, con
 // Batched form: nb right-hand sides at leading dimension ld.  variant = 1000 * RB + (100 if
 // implicit ids) + EB: a block stages the geometric factors of EB elements once and applies them
 // to RB right-hand sides; EB + 10 (EB 1 or 2) takes the right-hand sides two at a time through
-// each line pass (RB at least 2).
+// each line pass (RB at least 2); EB + 20 (EB 1 or 2) keeps the factors in registers instead.
 template <typename T>
 void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y,
                      unsigned* err, int variant, int nb, int64_t ld, cudaStream_t s);

@@ -508,6 +508,110 @@ k_sem_ax8b(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __
   }
 }
 
+// Batched variant with the geometric factors in registers: each thread loads the six factors
+// of the eight points of its t-line once (48 values; for a given factor and point the 64
+// threads of an element read 64 consecutive words) and keeps them for all the block's
+// right-hand sides.  No shared-memory copy of G: the factor multiply reads only the staged
+// derivatives (60 instead of 84 bytes of shared-memory traffic per point and right-hand side)
+// and the block holds just the three stage buffers.
+template <typename T, int EB, bool IMPLICIT>
+__global__ void __launch_bounds__(64 * EB)
+k_sem_ax8bg(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
+            const T* __restrict__ u, T* __restrict__ y, int nb, int64_t ld, int rb) {
+  using C = Ax8<T, EB>;
+  constexpr int R = C::R, P = C::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  T* sR = sU + EB * C::STAGE;
+  T* sS = sR + EB * C::STAGE;
+  const int tid = threadIdx.x;
+  const int le = tid >> 6, t = tid & 63, a = t & 7, b = t >> 3;
+  const int64_t e = (int64_t)blockIdx.x * EB + le;
+  const bool valid = e < E;
+  const int q0 = blockIdx.y * rb;
+  const int q1 = q0 + rb < nb ? q0 + rb : nb;
+  T gr[6][8];
+  {
+    const T* gG = G + (valid ? e : 0) * C::GELEM + b * 8 + a;
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) gr[c][k] = __ldg(gG + c * 512 + k * 64);
+  }
+  T* su = sU + le * C::STAGE;
+  T* sr = sR + le * C::STAGE;
+  T* ss = sS + le * C::STAGE;
+  uint32_t g[8];
+  column_ids<IMPLICIT>(gid, lat, e, valid, a, b, g);
+  auto gather = [&](int q, T (&v)[8]) {
+    const T* uq = u + (int64_t)q * ld;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (q < q1 && !(g[k] & kGidDirichlet)) ? uq[g[k] & kGidMask] : T(0);
+  };
+  T col[8];
+  gather(q0, col);
+  for (int q = q0; q < q1; ++q) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) su[k * P + b * R + a] = col[k];
+    T ut[8];
+    line8<T, 0>(col, ut);
+    T cn[8];
+    gather(q + 1, cn);           // next right-hand side's loads overlap this one's work
+    __syncthreads();
+    {
+      T v[8], o[8];
+      ld_row(su + b * P + a * R, v);
+      line8<T, 0>(v, o);
+      st_row(sr + b * P + a * R, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = su[b * P + j * R + a];
+      line8<T, 0>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ss[b * P + j * R + a] = o[j];
+    }
+    __syncthreads();             // the line passes above wrote points other threads read next
+    T wt[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int qq = k * P + b * R + a;
+      const T ur = sr[qq], us = ss[qq], utk = ut[k];
+      sr[qq] = gr[0][k] * ur + gr[1][k] * us + gr[2][k] * utk;
+      ss[qq] = gr[1][k] * ur + gr[3][k] * us + gr[4][k] * utk;
+      wt[k] = gr[2][k] * ur + gr[4][k] * us + gr[5][k] * utk;
+    }
+    T yt[8];
+    line8<T, 1>(wt, yt);
+    __syncthreads();
+    {
+      T v[8], o[8];
+      ld_row(sr + b * P + a * R, v);
+      line8<T, 1>(v, o);
+      st_row(su + b * P + a * R, o);
+    }
+    __syncthreads();
+    {
+      T v[8], o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = ss[b * P + j * R + a];
+      line8<T, 1>(v, o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) su[b * P + j * R + a] += o[j];
+    }
+    __syncthreads();
+    if (valid) {
+      T* yq = y + (int64_t)q * ld;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const T v = su[k * P + b * R + a] + yt[k];
+        if (!(g[k] & kGidDirichlet)) atomicAdd(&yq[g[k] & kGidMask], v);
+      }
+    }
+    __syncthreads();             // stage buffers free for the next right-hand side
+#pragma unroll
+    for (int k = 0; k < 8; ++k) col[k] = cn[k];
+  }
+}
+
 // Paired batched variant: like k_sem_ax8b, but every line pass works on two right-hand sides
 // at once (q and q + 1): each thread carries two independent lines through each contraction,
 // the geometric factors read from shared memory serve both, and a block barrier covers two
@@ -764,6 +868,22 @@ static void launch_ax8b2(int64_t E, const uint32_t* gid, const Lattice& lat, con
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+template <typename T, int EB, bool IM>
+static void launch_ax8bg(int64_t E, const uint32_t* gid, const Lattice& lat, const T* G, const T* u, T* y, int nb,
+                         int64_t ld, int rb, cudaStream_t s) {
+  using C = Ax8<T, EB>;
+  const size_t smem = sizeof(T) * (size_t)EB * 3 * C::STAGE;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_sem_ax8bg<T, EB, IM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  if (rb < 1) rb = 1;
+  const dim3 blocks((unsigned)((E + EB - 1) / EB), (unsigned)((nb + rb - 1) / rb));
+  k_sem_ax8bg<T, EB, IM><<<blocks, 64 * EB, smem, s>>>(E, gid, lat, G, u, y, nb, ld, rb);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 template <typename T>
 size_t sem_ax8_smem(int eb) {
   eb %= 100;
@@ -827,8 +947,22 @@ void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T
                      unsigned* err, int variant, int nb, int64_t ld, cudaStream_t s) {
   const int rb = variant / 1000;
   const bool im = (variant % 1000) >= 100;
-  const bool pair = (variant % 100) >= 10;
+  const int form = (variant % 100) / 10;   // 0 single, 1 paired, 2 factors in registers
+  const bool pair = form == 1;
   const int eb = variant % 10;
+  if (form == 2) {
+    // FP32 only: 48 FP64 factors per thread do not fit the register file
+    if constexpr (sizeof(T) == 4) {
+      if (im) {
+        if (eb == 1) launch_ax8bg<T, 1, true>(E, gid, lat, G, u, y, nb, ld, rb, s);
+        else launch_ax8bg<T, 2, true>(E, gid, lat, G, u, y, nb, ld, rb, s);
+      } else {
+        if (eb == 1) launch_ax8bg<T, 1, false>(E, gid, lat, G, u, y, nb, ld, rb, s);
+        else launch_ax8bg<T, 2, false>(E, gid, lat, G, u, y, nb, ld, rb, s);
+      }
+    }
+    return;
+  }
   if (pair) {
     if (im) {
       if (eb == 1) launch_ax8b2<T, 1, true>(E, gid, lat, G, u, y, err, nb, ld, rb, s);
@@ -853,6 +987,9 @@ void sem_ax8_batched(int64_t E, const uint32_t* gid, const Lattice& lat, const T
 template <typename T>
 bool sem_ax8_batched_fits(int variant) {
   const int rest = variant % 100;
+  // factors in registers (21, 22: the stage buffers alone, like the single-vector variants 21
+  // and 22) and single (1, 2, 4) forms
+  if (rest >= 20) return sizeof(T) == 4 && sem_ax8_variant_fits<T>(rest);   // FP32 only
   if (rest < 10) return sem_ax8_variant_fits<T>(rest);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);

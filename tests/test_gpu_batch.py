@@ -53,6 +53,11 @@ def batch_variants():
         for eb in (11, 12):
             for im in (0, 100):
                 out.append(1000 * rb + im + eb)
+    # geometric factors held in registers across the block's right-hand sides
+    for rb in (1, 3, 8):
+        for eb in (21, 22):
+            for im in (0, 100):
+                out.append(1000 * rb + im + eb)
     return out
 
 
@@ -201,7 +206,7 @@ def test_64_rhs_on_8cubed_mixed():
     code, its, rel = cm.chebmg_pcg_solve_batched(s.ctx, B, U, 1e-8, 200)
     assert code == cm.CHEBMG_OK and max(rel) <= 1e-8
     variant, degree = cm.chebmg_batch_info(s.ctx, 64, 0, F32)
-    assert variant // 1000 >= 1 and variant % 100 in (1, 2, 4, 11, 12) and degree in (1, 2, 4, 8, 12, 16)
+    assert variant // 1000 >= 1 and variant % 100 in (1, 2, 4, 11, 12, 21, 22) and degree in (1, 2, 4, 8, 12, 16)
     # true residuals with the FP64 operator (checked against the oracle above)
     AU = torch.zeros_like(U)
     cm.chebmg_apply_A_batched(s.ctx, 0, F64, U, AU)
