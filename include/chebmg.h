@@ -138,7 +138,9 @@ int chebmg_launch_count(const chebmg_ctx* ctx, int64_t* count);
  * per SM), or 31 / 32 for the persistent kernel with 1 / 2 elements per block and one
  * geometric-factor buffer (refilled during the second half of each element batch: half the
  * shared memory, more blocks per SM); +100 when global ids are computed from the box lattice instead of read from the
- * element-to-global map (0 if the level does not use that kernel). */
+ * element-to-global map.  Order-3 levels (N = 3): 40 for one thread per element point, 41
+ * for line passes (16 threads per element, one 4-point line each, synchronised within the
+ * warp), 141 for line passes with lattice ids.  0 for levels of other orders. */
 int chebmg_tile_choice(const chebmg_ctx* ctx, int level, int dtype, int* elements_per_block);
 /* Overrides that choice (same codes); EINVAL for other levels or codes. */
 /* SEM coarse solver: PCG whose preconditioner is Algorithm 2 (4th kind, beta = 1) of

@@ -93,6 +93,7 @@ struct Level {
   void* Jn[2] = {nullptr, nullptr};   // interpolation from level+1 to this level, [Qf][Qc]
   void* v[2][NV] = {{nullptr}};
   int eb[2] = {2, 2};   // variant of the order-7 operator, per dtype (autotuned)
+  int ax4[2] = {41, 41};   // order-3 operator: 40 one thread per point, 41 line passes (+100 lattice ids)
   int beb[2] = {2002, 2002};   // variant of the batched order-7 operator (autotuned per batch size)
   Lattice lat = {0, 0, 0, 0, 0, 0};
   bool boxed = true;    // SEM: the level carries the box lattice (lattice-indexed kernels usable)
@@ -273,6 +274,9 @@ void apply_into_ld(chebmg_ctx* c, int j, const T* x, T* y, int nb, int64_t ld) {
                          c->s);
     else if (L.Q == 8)
       sem_ax8<T>(L.E, L.gid, L.lat, static_cast<const T*>(L.G[dt]), x, y, c->dstat, L.eb[dt], c->s);
+    else if (L.Q == 4 && L.ax4[dt] % 100 == 41)
+      sem_ax4<T>(L.E, L.gid, L.ax4[dt] >= 100 ? &L.lat : nullptr, static_cast<const T*>(L.G[dt]),
+                 static_cast<const T*>(L.D[dt]), x, y, c->s, nb, ld);
     else
       sem_ax<T>(L.Q, L.E, L.gid, static_cast<const T*>(L.G[dt]), static_cast<const T*>(L.D[dt]), x, y, c->s, nb,
                 ld);
@@ -912,6 +916,46 @@ void autotune_ax8(chebmg_ctx* c, int j) {
   CK(cudaMemsetAsync(y, 0, sizeof(T) * L.n, c->s));
 }
 
+// Picks the order-3 operator (one thread per point, or line passes with map or lattice ids)
+// by timing each on the level's own data, like autotune_ax8.
+template <typename T>
+void autotune_ax4(chebmg_ctx* c, int j) {
+  Level& L = c->L[j];
+  const int dt = dt_of<T>();
+  if (L.type != TYPE_SEM || L.Q != 4 || !L.G[dt]) return;
+  T* x = vec<T>(L, VB);
+  T* y = vec<T>(L, VY);
+  CK(cudaMemsetAsync(x, 0, sizeof(T) * L.n, c->s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_v = L.boxed ? 141 : 41;
+  for (int v : {40, 41, 141}) {
+    if (v >= 100 && !L.boxed) continue;
+    L.ax4[dt] = v;
+    apply_into<T>(c, j, x, y);   // warm-up
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CK(cudaEventRecord(e0, c->s));
+      apply_into<T>(c, j, x, y);
+      CK(cudaEventRecord(e1, c->s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      t_min = std::min(t_min, ms);
+    }
+    if (t_min < best) {
+      best = t_min;
+      best_v = v;
+    }
+  }
+  L.ax4[dt] = best_v;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaMemsetAsync(y, 0, sizeof(T) * L.n, c->s));
+}
+
 // Picks the coarse CG's kernel, the degree of its polynomial preconditioner and (grid-wide
 // kernel) the rows per thread by timing full coarse solves of a seeded right-hand side
 // (degree 1 = Jacobi-PCG).  More rows per thread means fewer blocks: cheaper exchanges and
@@ -1027,6 +1071,8 @@ void finish_setup(chebmg_ctx* c) {
   for (int j = 0; j < nl; ++j) {
     autotune_ax8<double>(c, j);
     if (c->fp32) autotune_ax8<float>(c, j);
+    autotune_ax4<double>(c, j);
+    if (c->fp32) autotune_ax4<float>(c, j);
   }
   c->pre = c->o.sided == CHEBMG_ONE_SIDED ? 2 * c->o.order : c->o.order;
   c->post = c->o.sided == CHEBMG_ONE_SIDED ? 0 : c->o.order;
@@ -2350,7 +2396,7 @@ int chebmg_tile_choice(const chebmg_ctx* c, int level, int dtype, int* elements_
   if (!c || !elements_per_block || level < 0 || level >= (int)c->L.size() || (dtype != 0 && dtype != 1))
     return CHEBMG_EINVAL;
   const Level& L = c->L[level];
-  *elements_per_block = (L.type == TYPE_SEM && L.Q == 8) ? L.eb[dtype] : 0;
+  *elements_per_block = L.type != TYPE_SEM ? 0 : L.Q == 8 ? L.eb[dtype] : L.Q == 4 ? L.ax4[dtype] : 0;
   return CHEBMG_OK;
 }
 
@@ -2423,6 +2469,12 @@ int chebmg_set_coarse_degree(chebmg_ctx* c, int degree) {
 int chebmg_set_tile_choice(chebmg_ctx* c, int level, int dtype, int variant) {
   if (!c || level < 0 || level >= (int)c->L.size() || (dtype != 0 && dtype != 1)) return CHEBMG_EINVAL;
   Level& L = c->L[level];
+  if (L.type == TYPE_SEM && L.Q == 4) {
+    if ((variant != 40 && variant != 41 && variant != 141) || (variant == 141 && !L.boxed)) return CHEBMG_EINVAL;
+    L.ax4[dtype] = variant;
+    drop_graphs(c);
+    return CHEBMG_OK;
+  }
   if (L.type != TYPE_SEM || L.Q != 8) return CHEBMG_EINVAL;
   const int base = variant % 100;
   if ((variant != base && variant != base + 100) ||

@@ -92,11 +92,16 @@ void sem_prolong(int Qf, int Qc, int64_t E, const uint32_t* gidf, const uint32_t
 // Order-7 element operator (line passes, even-odd D, TMA-staged geometric factors).
 // sem_ax8_set_D uploads the even-odd blocks of the 8x8 GLL derivative matrix (row-major).
 cudaError_t sem_ax8_set_D(const double* D);
-// Box lattice of an order-7 level (element counts and global node counts per direction).
+// Box lattice of a level (element counts and global node counts per direction).
 struct Lattice {
   int nex, ney, nez;
   int NX, NY, NZ;
 };
+// Order-3 element operator by line passes (16 threads per element, no block barrier): as
+// sem_ax for Q = 4; ids from the box lattice when lat is given, else from gid.
+template <typename T>
+void sem_ax4(int64_t E, const uint32_t* gid, const Lattice* lat, const T* G, const T* D, const T* u, T* y,
+             cudaStream_t s, int nb = 1, int64_t ld = 0);
 // The order-7 operator in FP64-class arithmetic on FP32 pairs (sem_ax8_x2.cu): G in that
 // format (sem_to_x2 converts an FP64 array of n values), u and y FP64; variant as sem_ax8's
 // non-persistent codes (1, 2, 4; +100 box lattice ids); batches of nb vectors at stride ld,

@@ -119,6 +119,161 @@ static void launch_sem_ax(int64_t E, const uint32_t* gid, const T* G, const T* D
   launch_dep(k_sem_ax<T, Q>, dim3(blocks, nb), dim3(S::THREADS), 0, s, E, gid, G, D, u, y, ld);
 }
 
+// Order-3 element operator (N = 3, 4 points per direction) by line passes: 16 threads per
+// element, thread (a, b) owning one 4-point line in each pass -- its t-line (i = a, j = b) in
+// registers for the gather, the t derivative, the geometric factors and the scatter; the r and
+// s lines (j = a, k = b and i = a, k = b) through shared memory.  An element's 16 threads are
+// half a warp, so the passes synchronise with __syncwarp() and the block has no barrier.  The
+// factors of the t-line (24 values) and D (16) are loaded into registers before the gather
+// (and, under programmatic dependent launch, before waiting for the kernel that wrote u).
+// IMPLICIT: global ids from the box lattice (ids and Dirichlet flags computed, no map read).
+constexpr int kAx4Threads = 256;                 // 16 elements per block
+constexpr int kAx4Plane = 20;                    // padded k-plane stride: conflict-free s lines
+
+template <typename T, bool IMPLICIT>
+__global__ void __launch_bounds__(kAx4Threads)
+k_sem_ax4(int64_t E, const uint32_t* __restrict__ gid, Lattice lat, const T* __restrict__ G,
+          const T* __restrict__ Dg, const T* __restrict__ u, T* __restrict__ y, int64_t ld) {
+  constexpr int PK = kAx4Plane, EL = 4 * kAx4Plane;
+  __shared__ __align__(16) T sU[kAx4Threads / 16][EL];
+  __shared__ __align__(16) T sR[kAx4Threads / 16][EL];
+  __shared__ __align__(16) T sS[kAx4Threads / 16][EL];
+  const int tid = threadIdx.x, le = tid >> 4, t = tid & 15, a = t & 3, b = t >> 2;
+  const int64_t e = (int64_t)blockIdx.x * (kAx4Threads / 16) + le;
+  const bool valid = e < E;
+  T D[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) D[i][l] = __ldg(Dg + i * 4 + l);
+  T gr[6][4];
+  {
+    const T* Ge = G + (valid ? e : 0) * 384 + b * 4 + a;
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) gr[c][k] = __ldg(Ge + c * 64 + k * 16);
+  }
+  uint32_t g[4];
+  if (!valid) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g[k] = kGidDirichlet;
+  } else if constexpr (IMPLICIT) {
+    const uint32_t ee = (uint32_t)e, exy = (uint32_t)lat.nex * (uint32_t)lat.ney;
+    const uint32_t ez = ee / exy, rem = ee - ez * exy, ey = rem / (uint32_t)lat.nex, ex = rem - ey * (uint32_t)lat.nex;
+    const uint32_t gx = ex * 3 + a, gy = ey * 3 + b;
+    const bool side = gx == 0 || gx == (uint32_t)lat.NX - 1 || gy == 0 || gy == (uint32_t)lat.NY - 1;
+    const uint32_t plane = (uint32_t)lat.NX * (uint32_t)lat.NY;
+    const uint32_t g0 = (ez * 3 * (uint32_t)lat.NY + gy) * (uint32_t)lat.NX + gx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t gz = ez * 3 + k;
+      g[k] = (g0 + k * plane) | ((side || gz == 0 || gz == (uint32_t)lat.NZ - 1) ? kGidDirichlet : 0u);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g[k] = __ldg(gid + e * 64 + k * 16 + b * 4 + a);
+  }
+  u += (int64_t)blockIdx.y * ld;   // right-hand side of a batch
+  y += (int64_t)blockIdx.y * ld;
+  pdl_wait();   // u and y may come from the kernel before (programmatic dependent launch)
+  T col[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) col[k] = (g[k] & kGidDirichlet) ? T(0) : u[g[k] & kGidMask];
+  T* su = sU[le];
+  T* sr = sR[le];
+  T* ss = sS[le];
+  T ut[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    su[k * PK + b * 4 + a] = col[k];
+    T acc = D[k][0] * col[0];
+#pragma unroll
+    for (int l = 1; l < 4; ++l) acc = fma(D[k][l], col[l], acc);
+    ut[k] = acc;
+  }
+  __syncwarp();
+  {
+    T v[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) v[l] = su[b * PK + a * 4 + l];         // r-line (j = a, k = b)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T acc = D[i][0] * v[0];
+#pragma unroll
+      for (int l = 1; l < 4; ++l) acc = fma(D[i][l], v[l], acc);
+      sr[b * PK + a * 4 + i] = acc;
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) v[l] = su[b * PK + l * 4 + a];         // s-line (i = a, k = b)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      T acc = D[j][0] * v[0];
+#pragma unroll
+      for (int l = 1; l < 4; ++l) acc = fma(D[j][l], v[l], acc);
+      ss[b * PK + j * 4 + a] = acc;
+    }
+  }
+  __syncwarp();
+  T wt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {                                         // own t-line points
+    const int q = k * PK + b * 4 + a;
+    const T ur = sr[q], us = ss[q], utk = ut[k];
+    sr[q] = gr[0][k] * ur + gr[1][k] * us + gr[2][k] * utk;
+    ss[q] = gr[1][k] * ur + gr[3][k] * us + gr[4][k] * utk;
+    wt[k] = gr[2][k] * ur + gr[4][k] * us + gr[5][k] * utk;
+  }
+  T yt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {                                         // D^T along t
+    T acc = D[0][k] * wt[0];
+#pragma unroll
+    for (int l = 1; l < 4; ++l) acc = fma(D[l][k], wt[l], acc);
+    yt[k] = acc;
+  }
+  __syncwarp();
+  {
+    T v[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) v[l] = sr[b * PK + a * 4 + l];         // D^T along r
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T acc = D[0][i] * v[0];
+#pragma unroll
+      for (int l = 1; l < 4; ++l) acc = fma(D[l][i], v[l], acc);
+      su[b * PK + a * 4 + i] = acc;
+    }
+  }
+  __syncwarp();
+  {
+    T v[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) v[l] = ss[b * PK + l * 4 + a];         // D^T along s
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      T acc = D[0][j] * v[0];
+#pragma unroll
+      for (int l = 1; l < 4; ++l) acc = fma(D[l][j], v[l], acc);
+      su[b * PK + j * 4 + a] += acc;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (!(g[k] & kGidDirichlet)) atomicAdd(&y[g[k] & kGidMask], su[k * PK + b * 4 + a] + yt[k]);
+}
+
+template <typename T>
+void sem_ax4(int64_t E, const uint32_t* gid, const Lattice* lat, const T* G, const T* D, const T* u, T* y,
+             cudaStream_t s, int nb, int64_t ld) {
+  const dim3 blocks((unsigned)((E + kAx4Threads / 16 - 1) / (kAx4Threads / 16)), nb);
+  if (lat)
+    launch_dep(k_sem_ax4<T, true>, blocks, dim3(kAx4Threads), 0, s, E, gid, *lat, G, D, u, y, ld);
+  else
+    launch_dep(k_sem_ax4<T, false>, blocks, dim3(kAx4Threads), 0, s, E, gid, Lattice{}, G, D, u, y, ld);
+}
+
 template <typename T>
 void sem_ax(int Q, int64_t E, const uint32_t* gid, const T* G, const T* D, const T* u, T* y,
             cudaStream_t s, int nb, int64_t ld) {
@@ -1175,6 +1330,8 @@ void scale(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
 // explicit instantiations
 // ===========================================================================
 #define CHEBMG_INST(T)                                                                                \
+  template void sem_ax4<T>(int64_t, const uint32_t*, const Lattice*, const T*, const T*, const T*, T*,           \
+                           cudaStream_t, int, int64_t);                                                    \
   template void sem_ax<T>(int, int64_t, const uint32_t*, const T*, const T*, const T*, T*, cudaStream_t, int,  \
                           int64_t);                                                                   \
   template void sem_restrict<T>(int, int, int64_t, const uint32_t*, const uint32_t*, const T*, const T*,  \

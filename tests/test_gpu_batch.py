@@ -82,6 +82,29 @@ def test_batched_order7_operator_every_variant(verts, variant):
     s.close()
 
 
+@pytest.mark.parametrize("variant", [1002, 3004, 2102, 3012, 2112, 1022, 3122, 5021])
+def test_batched_order7_operator_ragged_last_batch(variant):
+    # 3 x 3 x 3 = 27 elements: a ragged last element batch for 2 and 4 elements per block
+    v = W.sem_box_vertices(3, 3, 3)
+    L = SemLevel(v, 7)
+    s = sem_solver(v, (7, 3, 1), prec="mixed", lmax=[1.0, 1.0])
+    nrhs = 5
+    X = np.random.default_rng(variant).uniform(-1, 1, (nrhs, L.n))
+    for dt in (F64, F32):
+        try:
+            cm.chebmg_set_batch_tile_choice(s.ctx, nrhs, 0, dt, variant)
+        except cm.ChebmgError as e:
+            assert e.code == cm.CHEBMG_EINVAL and dt == F64 and variant % 100 >= 20   # FP32-only form
+            continue
+        tdt = torch.float64 if dt == F64 else torch.float32
+        Y = torch.zeros((nrhs, L.n), dtype=tdt, device="cuda")
+        cm.chebmg_apply_A_batched(s.ctx, 0, dt, T(X, tdt), Y)
+        for q in range(nrhs):
+            xq = X[q] if dt == F64 else X[q].astype(np.float32).astype(np.float64)
+            assert relerr(N(Y[q]), L.apply_A(xq)) < (1e-12 if dt == F64 else 1e-5), (variant, dt, q)
+    s.close()
+
+
 @pytest.mark.parametrize("orders", [(7, 3, 1), (9, 5, 2), (6, 1)])
 def test_batched_operator_all_levels(verts, orders):
     levels = [SemLevel(verts, Nn) for Nn in orders]

@@ -265,3 +265,93 @@ def test_every_order7_kernel_variant(verts, variant):
     with pytest.raises(cm.ChebmgError):
         cm.chebmg_set_tile_choice(s.ctx, 1, F64, 2)   # level 1 is order 3
     s.close()
+
+
+# 3 x 3 x 3 = 27 elements: a ragged last element batch for 2 and 4 elements per block (MESH
+# divides by both)
+@pytest.mark.parametrize("variant", [2, 4, 12, 14, 22, 32, 102, 104, 112, 114, 122, 132])
+def test_order7_variants_ragged_last_batch(variant):
+    v = W.sem_box_vertices(3, 3, 3)
+    L = SemLevel(v, 7)
+    s = solver(v, (7, 3, 1), prec="mixed", lmax=[1.0, 1.0])
+    x = np.where(L.dirichlet, 0.0, np.random.default_rng(variant + 1).uniform(-1, 1, L.n))
+    for dt, tol in ((F64, 1e-12), (F32, 2e-5)):
+        try:
+            cm.chebmg_set_tile_choice(s.ctx, 0, dt, variant)
+        except cm.ChebmgError:
+            assert dt == F64 and variant % 100 == 14   # 264 KB of shared memory in FP64
+            continue
+        if dt == F64:
+            xt, y, ref = T(x), empty(L.n), L.apply_A(x)
+        else:
+            xt, y = T(x, torch.float32), empty(L.n, True)
+            ref = L.apply_A(x.astype(np.float32).astype(np.float64))
+        cm.chebmg_apply_A(s.ctx, 0, dt, xt, y)
+        assert relerr(N(y), ref) < tol, (variant, dt)
+        assert np.all(N(y)[L.dirichlet] == 0.0)
+    s.close()
+
+
+@pytest.mark.parametrize("mesh", [MESH, (3, 3, 3)])
+@pytest.mark.parametrize("variant", [40, 41, 141])
+def test_order3_operator_variants(mesh, variant):
+    # the order-3 level of a (7, 3, 1) hierarchy: one thread per point (40) or line passes with
+    # map (41) or lattice (141) ids; 16 elements per line-pass block, so both meshes end in a
+    # ragged block (60 = 3 x 16 + 12, 27 = 16 + 11)
+    v = W.sem_box_vertices(*mesh)
+    L = SemLevel(v, 3)
+    s = solver(v, (7, 3, 1), prec="mixed", lmax=[1.0, 1.0])
+    assert cm.chebmg_tile_choice(s.ctx, 1, F64) in (40, 41, 141)
+    rng = np.random.default_rng(variant)
+    x = np.where(L.dirichlet, 0.0, rng.uniform(-1, 1, L.n))
+    for dt, tol in ((F64, 1e-12), (F32, 2e-5)):
+        cm.chebmg_set_tile_choice(s.ctx, 1, dt, variant)
+        if dt == F64:
+            xt, y, ref = T(x), empty(L.n), L.apply_A(x)
+        else:
+            xt, y = T(x, torch.float32), empty(L.n, True)
+            ref = L.apply_A(x.astype(np.float32).astype(np.float64))
+        cm.chebmg_apply_A(s.ctx, 1, dt, xt, y)
+        assert relerr(N(y), ref) < tol, (variant, dt)
+        assert np.all(N(y)[L.dirichlet] == 0.0)
+    # a batch of three vectors through the same kernel (one grid row per vector)
+    X = rng.uniform(-1, 1, (3, L.n))
+    Y = torch.zeros((3, L.n), dtype=torch.float64, device="cuda")
+    cm.chebmg_apply_A_batched(s.ctx, 1, F64, T(X), Y)
+    for q in range(3):
+        assert relerr(N(Y[q]), L.apply_A(X[q])) < 1e-12
+    with pytest.raises(cm.ChebmgError):
+        cm.chebmg_set_tile_choice(s.ctx, 1, F64, 42)
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def many_batches():
+    # 13 x 11 x 11 = 1573 elements: more element batches than resident blocks of every
+    # persistent variant, so each block walks several batches (and the geometric-factor buffers
+    # are refilled), with a ragged last batch for 2 and 4 elements per block
+    v = W.sem_box_vertices(13, 11, 11)
+    L = SemLevel(v, 7)
+    s = solver(v, (7, 3, 1), prec="mixed", lmax=[1.0, 1.0])
+    yield L, s
+    s.close()
+
+
+@pytest.mark.parametrize("variant", [12, 14, 31, 32, 112, 114, 131, 132])
+def test_persistent_variants_several_batches_per_block(many_batches, variant):
+    L, s = many_batches
+    x = np.where(L.dirichlet, 0.0, np.random.default_rng(variant + 2).uniform(-1, 1, L.n))
+    for dt, tol in ((F64, 1e-12), (F32, 2e-5)):
+        try:
+            cm.chebmg_set_tile_choice(s.ctx, 0, dt, variant)
+        except cm.ChebmgError:
+            assert dt == F64 and variant % 100 == 14
+            continue
+        if dt == F64:
+            xt, y, ref = T(x), empty(L.n), L.apply_A(x)
+        else:
+            xt, y = T(x, torch.float32), empty(L.n, True)
+            ref = L.apply_A(x.astype(np.float32).astype(np.float64))
+        for _ in range(2):   # a second application over the same (re-zeroed) output
+            cm.chebmg_apply_A(s.ctx, 0, dt, xt, y)
+        assert relerr(N(y), ref) < tol, (variant, dt)
