@@ -590,6 +590,10 @@ def main():
     ap.add_argument("--profile-outer", choices=["fp64", "f32x2"], default=None,
                     help="apply only the outer operator (FP64 or FP32 pairs) twice, the second inside an "
                          "NVTX range 'outer' (for ncu)")
+    ap.add_argument("--pin-tiles", default=None,
+                    help="profiling runs only (--profile-solve): JSON {\"level,dtype\": variant} of operator "
+                         "variants to set after setup (the autotuner's timings are distorted under a profiler); "
+                         "the run prints the variants it used")
     ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
                     help="set up, warm up, run one solve inside the NVTX range 'solve' and exit "
                          "(for ncu --nvtx-include solve/)")
@@ -682,8 +686,8 @@ def main():
         bb = xb.clone().uniform_(-1, 1)
         if args.tile is not None:
             cm.chebmg_set_tile_choice(s.ctx, 0, dt, args.tile)
-        if args.fused:
-            cm.chebmg_set_fused_smoother(s.ctx, 0, dt, 1 if f32 else 2)
+        # the separate kernels unless the fused one is asked for (whatever the autotuner chose)
+        cm.chebmg_set_fused_smoother(s.ctx, 0, dt, (1 if f32 else 2) if args.fused else 0)
         cm.chebmg_smooth(s.ctx, 0, dt, bb, xb, 9, True)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("smooth")
@@ -717,11 +721,20 @@ def main():
         s = s32 if args.profile_solve == "mixed" else s64
         solve(s)
         torch.cuda.synchronize()
+        if args.pin_tiles:
+            for key, var in json.loads(args.pin_tiles).items():
+                lev, dt = (int(x) for x in key.split(","))
+                cm.chebmg_set_tile_choice(s.ctx, lev, dt, int(var))
+            solve(s)
+            torch.cuda.synchronize()
+        tiles = {f"{j},{dt}": cm.chebmg_tile_choice(s.ctx, j, dt)
+                 for j in range(len(ORDERS)) for dt in ((0, 1) if args.profile_solve == "mixed" else (0,))
+                 if cm.chebmg_tile_choice(s.ctx, j, dt)}
         torch.cuda.nvtx.range_push("solve")
         it = solve(s)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"profile_solve": args.profile_solve, "iterations": it}))
+        print(json.dumps({"profile_solve": args.profile_solve, "iterations": it, "tiles": tiles}))
         s32.close()
         s64.close()
         return 0

@@ -423,7 +423,10 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
   } else {
     const double* beta = (c->o.kind == CHEBMG_CHEB_4TH_OPT) ? kBeta[order - 1] : nullptr;
     if (!c->beta_ovr.empty() && (int)c->beta_ovr.size() == order) beta = c->beta_ovr.data();
-    cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), x_zero ? 1 : 0, c->s, nb, ld);
+    // from x = 0 with more than one step, the init writes only d and the first step reads b
+    // for r and writes x (two vector writes and a read fewer than x = 0, r = b in the init)
+    const bool lean = x_zero && order > 1;
+    cheb4_init<T>(n, b, x, r, d, y, S, 4.0 / (3.0 * lmax), lean ? 2 : x_zero ? 1 : 0, c->s, nb, ld);
     const double beta_k = beta ? beta[order - 1] : 1.0;
     for (int i = 1; i < order; ++i) {
       apply_into<T>(c, j, d, y);
@@ -431,7 +434,7 @@ void smooth(chebmg_ctx* c, int j, const T* b, T* x, int order, bool x_zero) {
       const double c2 = (8.0 * i + 4.0) / ((2.0 * i + 3.0) * lmax);
       // the last step also applies the final update x += beta_k d_k (one pass fewer)
       cheb4_step<T>(n, x, r, d, y, S, beta ? beta[i - 1] : 1.0, c1, c2, c->s, nb, ld,
-                    i + 1 == order ? beta_k : 0.0);
+                    i + 1 == order ? beta_k : 0.0, lean && i == 1 ? b : nullptr);
     }
     if (order == 1 || beta_k == 0.0) axpy<T>(n, beta_k, d, x, c->s, nb, ld);
   }
@@ -2786,16 +2789,16 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
     };
     int rc = precondition(false);
     if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
+    // the p updates also zero q, which the next product accumulates into
     if (mixed) {
-      update_p_from<float>(n, z32, p, c->scal, true, c->s);
+      update_p_from<float>(n, z32, p, c->scal, true, c->s, q);
       dot_zr_zq<float>(n, z32, r, nullptr, POST_SET_RZ_FROM_ZR, c->partial, c->scal, c->s);
     } else {
-      update_p_from<double>(n, z, p, c->scal, true, c->s);
+      update_p_from<double>(n, z, p, c->scal, true, c->s, q);
       dot_zr_zq<double>(n, z, r, nullptr, POST_SET_RZ_FROM_ZR, c->partial, c->scal, c->s);
     }
     double rel = 1.0;
     for (int it = 1; it <= maxit; ++it) {
-      zero<double>(c, q, n);
       apply_outer(c, p, q);
       dot2(n, p, q, nullptr, nullptr, S_PQ, -1, POST_ALPHA, c->partial, c->scal, c->s);
       fcg_update_xr32(n, u, r, r32, p, q, c->partial, c->scal, c->s);
@@ -2828,10 +2831,10 @@ int chebmg_pcg_solve(chebmg_ctx* c, const double* b, double* u, double rtol, int
       if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) return rc;
       if (mixed) {
         dot_zr_zq<float>(n, z32, r, q, POST_BETA_FLEX_Q, c->partial, c->scal, c->s);
-        update_p_from<float>(n, z32, p, c->scal, false, c->s);
+        update_p_from<float>(n, z32, p, c->scal, false, c->s, q);
       } else {
         dot_zr_zq<double>(n, z, r, q, POST_BETA_FLEX_Q, c->partial, c->scal, c->s);
-        update_p_from<double>(n, z, p, c->scal, false, c->s);
+        update_p_from<double>(n, z, p, c->scal, false, c->s, q);
       }
       check_launch();
     }

@@ -31,6 +31,10 @@ __global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__
   { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     T rv;
+    if (x_is_zero == 2) {   // x = 0 and r = b are left to the first step, which reads b
+      d[g] = c0 * invD[g] * b[g];
+      continue;
+    }
     if (x_is_zero) {
       rv = b[g];
       x[g] = T(0);
@@ -57,11 +61,12 @@ struct V16<double> {
   static constexpr int L = 2;
 };
 
-template <typename T>
+template <typename T, bool FIRST = false>
 __device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T c1, T c2, T beta_next) {
   const T dv = d;
   const T rv = r - y;
-  x += beta * dv;
+  if (FIRST) x = beta * dv;    // first step from x = 0 (r holds b)
+  else x += beta * dv;
   r = rv;
   d = c1 * dv + c2 * s * rv;
   y = T(0);
@@ -99,15 +104,18 @@ __device__ __forceinline__ void st16(VT* p, const VT& val, uint64_t pol) {
                : "memory");
 }
 
-template <typename T, bool VEC>
-__global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ d,
+// FIRST: the first step of a smoother application from x = 0, after an init that wrote only d:
+// r is read from b (rin) and x is not read (x = beta d), so the init writes neither x nor r.
+// (rin is r itself in the other steps, so neither is declared __restrict__.)
+template <typename T, bool VEC, bool FIRST = false>
+__global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* r, T* __restrict__ d,
                              T* __restrict__ y, const T* __restrict__ invD, T beta, T c1, T c2, T beta_next,
-                             int64_t ld) {
+                             int64_t ld, const T* rin) {
   // Everything read here is the operator kernel's output or older: wait for that kernel before
   // the first load.  (Triggering the next kernel early as well, griddepcontrol.launch_dependents,
   // was measured slower: its waiting blocks cost this grid's last wave more than they saved.)
   pdl_wait();
-  { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; }
+  { const int64_t off_ = (int64_t)blockIdx.y * ld; x += off_; r += off_; d += off_; y += off_; rin += off_; }
   using VT = typename V16<T>::type;
   constexpr int L = V16<T>::L;
   const int64_t nv = VEC ? n / L : 0;
@@ -115,7 +123,8 @@ __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const uint64_t first = l2_policy_first(), last = l2_policy_last();
   for (int64_t q = tid; q < nv; q += stride) {
-    VT xv = ld16(reinterpret_cast<VT*>(x) + q, first), rv = ld16(reinterpret_cast<VT*>(r) + q, first);
+    VT xv = {}, rv = ld16(reinterpret_cast<const VT*>(rin) + q, first);
+    if (!FIRST) xv = ld16(reinterpret_cast<VT*>(x) + q, first);
     VT dv = ld16(reinterpret_cast<VT*>(d) + q, last), yv = ld16(reinterpret_cast<VT*>(y) + q, last);
     const VT sv = ld16(reinterpret_cast<const VT*>(invD) + q, first);
     T* xs = reinterpret_cast<T*>(&xv);
@@ -124,14 +133,18 @@ __global__ void k_cheb4_step(int64_t n, T* __restrict__ x, T* __restrict__ r, T*
     T* ys = reinterpret_cast<T*>(&yv);
     const T* ss = reinterpret_cast<const T*>(&sv);
 #pragma unroll
-    for (int l = 0; l < L; ++l) cheb4_one(xs[l], rs[l], ds[l], ys[l], ss[l], beta, c1, c2, beta_next);
+    for (int l = 0; l < L; ++l) cheb4_one<T, FIRST>(xs[l], rs[l], ds[l], ys[l], ss[l], beta, c1, c2, beta_next);
     st16(reinterpret_cast<VT*>(x) + q, xv, first);
     st16(reinterpret_cast<VT*>(r) + q, rv, first);
     st16(reinterpret_cast<VT*>(d) + q, dv, last);
     st16(reinterpret_cast<VT*>(y) + q, yv, last);
   }
-  for (int64_t g = nv * L + tid; g < n; g += stride)
-    cheb4_one(x[g], r[g], d[g], y[g], invD[g], beta, c1, c2, beta_next);
+  for (int64_t g = nv * L + tid; g < n; g += stride) {
+    T xg = FIRST ? T(0) : x[g], rg = rin[g];
+    cheb4_one<T, FIRST>(xg, rg, d[g], y[g], invD[g], beta, c1, c2, beta_next);
+    x[g] = xg;
+    r[g] = rg;
+  }
 }
 
 template <typename T>
@@ -213,17 +226,26 @@ void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, do
   launch_dep(k_cheb4_init<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, x, r, d, y, invD,
              (T)c0, x_is_zero, ld ? ld : n);
 }
+template <typename T, bool FIRST>
+static void launch_cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
+                              cudaStream_t s, int nb, int64_t ld, double beta_next, const T* rin) {
+  const uintptr_t align =
+      (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD | (uintptr_t)rin;
+  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
+    launch_dep(k_cheb4_step<T, true, FIRST>, dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), dim3(kVecThreads),
+               0, s, n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld, rin);
+  else
+    launch_dep(k_cheb4_step<T, false, FIRST>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, x, r,
+               d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld, rin);
+}
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
-                cudaStream_t s, int nb, int64_t ld, double beta_next) {
+                cudaStream_t s, int nb, int64_t ld, double beta_next, const T* b_first) {
   if (!ld) ld = n;
-  const uintptr_t align = (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
-  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
-    launch_dep(k_cheb4_step<T, true>, dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), dim3(kVecThreads), 0, s,
-               n, x, r, d, y, invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
+  if (b_first)
+    launch_cheb4_step<T, true>(n, x, r, d, y, invD, beta, c1, c2, s, nb, ld, beta_next, b_first);
   else
-    launch_dep(k_cheb4_step<T, false>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, x, r, d, y,
-               invD, (T)beta, (T)c1, (T)c2, (T)beta_next, ld);
+    launch_cheb4_step<T, false>(n, x, r, d, y, invD, beta, c1, c2, s, nb, ld, beta_next, r);
 }
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
@@ -261,7 +283,7 @@ void masked_copy(int64_t n, const double* in, const double* invD, double* out, c
   template void cheb4_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb4_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, double, cudaStream_t, int,   \
-                              int64_t, double);                                                         \
+                              int64_t, double, const T*);                                               \
   template void cheb1_init<T>(int64_t, const T*, T*, T*, T*, T*, const T*, double, int, cudaStream_t, int,    \
                               int64_t);                                                                 \
   template void cheb1_step<T>(int64_t, T*, T*, T*, T*, const T*, double, double, cudaStream_t, int, int64_t); \

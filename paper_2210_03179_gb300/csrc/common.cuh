@@ -213,15 +213,18 @@ void fd_prolong(int mfx, int mfy, int mcx, int mcy, int c, const T* zc, T* zf, i
 void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream_t s, int nb = 1, int64_t ld = 0);
 
 // ---- Chebyshev recurrences (Algorithms 1 and 2), elementwise over n ----
-// 4th kind init: x_is_zero: x = 0, r = b; else r = b - y, y = 0.  d = c0 S r.
+// 4th kind init: x_is_zero 1: x = 0, r = b; 0: r = b - y, y = 0; then d = c0 S r.  x_is_zero 2:
+// d = c0 S b only (x = 0 and r = b are left to the first cheb4_step, given b_first = b).
 template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0,
                 int x_is_zero, cudaStream_t s, int nb = 1, int64_t ld = 0);
 // 4th kind step: x += beta d; r -= y; d = c1 d + c2 S r; y = 0; then, if beta_next != 0 (the
-// last step), the final update x += beta_next d with the new d.
+// last step), the final update x += beta_next d with the new d.  b_first: the first step from
+// x = 0 after cheb4_init with x_is_zero = 2 (d only): r = b_first - y and x = beta d.
 template <typename T>
 void cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1,
-                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0, double beta_next = 0.0);
+                double c2, cudaStream_t s, int nb = 1, int64_t ld = 0, double beta_next = 0.0,
+                const T* b_first = nullptr);
 // 1st kind init: r = S (b - y) (or S b), d = r / theta, y = 0 (x = 0 if x_is_zero).
 template <typename T>
 void cheb1_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double inv_theta,
@@ -259,9 +262,10 @@ void fcg_update_xr32(int64_t n, double* x, double* r, float* r32, const double* 
 template <typename Tz>
 void dot_zr_zq(int64_t n, const Tz* z, const double* r, const double* q, int post, double* partial, double* scal,
                cudaStream_t s);
-// p = z + scal[BETA] p, or p = z (first)
+// p = z + scal[BETA] p, or p = z (first); q_zero, if given, is set to 0 in the same pass
 template <typename Tz>
-void update_p_from(int64_t n, const Tz* z, double* p, const double* scal, bool first, cudaStream_t s);
+void update_p_from(int64_t n, const Tz* z, double* p, const double* scal, bool first, cudaStream_t s,
+                   double* q_zero = nullptr);
 // CG (coarse): x += alpha p; r -= alpha q; z = S r; partials (r, r) and (r, z)
 void cg_update(int64_t n, double* x, double* r, double* z, const double* p, const double* q,
                const double* invD, double* partial, double* scal, cudaStream_t s);
