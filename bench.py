@@ -51,18 +51,19 @@ def peaks():
         return {}
 
 
-def recorded_traffic(variant=None):
-    """DRAM bytes per fine step from profiles/roofline_traffic.json, or None if the kernels
-    that make up the step changed since those counters were taken (or another variant runs)."""
+def recorded_traffic(variant):
+    """DRAM bytes per fine step of the order-7 operator variant `variant` from
+    profiles/roofline_traffic.json, or None if that variant was not captured or the kernels that
+    make up the step changed since the counters were taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
         h = hashlib.sha256()
         for f in rec["source_files"]:
             h.update(open(os.path.join(ROOT, f), "rb").read())
-        if variant is not None and variant != rec.get("variant"):
+        if h.hexdigest() != rec["source_sha256"]:
             return None
-        return rec["traffic_bytes_per_step"] if h.hexdigest() == rec["source_sha256"] else None
+        return rec["variants"][str(variant)]["traffic_bytes_per_step"]
     except Exception:
         return None
 
