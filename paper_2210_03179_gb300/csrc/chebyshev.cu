@@ -23,15 +23,64 @@ inline unsigned grid_for(int64_t n, int bs) {
 // ===========================================================================
 // Chebyshev recurrences and vector updates
 // ===========================================================================
+// Vector type of 16 bytes for T (float4 / double2) and its lane count.
 template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int L = 4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int L = 2;
+};
+
+// 4th-kind init.  mode 2: d = c0 S b only; 1: x = 0, r = b, d = c0 S r; 0: r = b - y, y = 0,
+// d = c0 S r.  VEC: 16-byte accesses over the aligned body, scalar tail.
+template <typename T, bool VEC>
 __global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                              T* __restrict__ d, T* __restrict__ y, const T* __restrict__ invD, T c0,
                              int x_is_zero, int64_t ld) {
   pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; x += off_; r += off_; d += off_; y += off_; }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    T rv;
+  using VT = typename V16<T>::type;
+  constexpr int L = V16<T>::L;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nv = VEC ? n / L : 0;
+  for (int64_t q = tid; q < nv; q += stride) {
+    const VT bv = reinterpret_cast<const VT*>(b)[q], sv = reinterpret_cast<const VT*>(invD)[q];
+    const T* bs = reinterpret_cast<const T*>(&bv);
+    const T* ss = reinterpret_cast<const T*>(&sv);
+    VT rv, dv;
+    T* rs = reinterpret_cast<T*>(&rv);
+    T* ds = reinterpret_cast<T*>(&dv);
     if (x_is_zero == 2) {   // x = 0 and r = b are left to the first step, which reads b
+#pragma unroll
+      for (int l = 0; l < L; ++l) ds[l] = c0 * ss[l] * bs[l];
+      reinterpret_cast<VT*>(d)[q] = dv;
+      continue;
+    }
+    if (x_is_zero) {
+#pragma unroll
+      for (int l = 0; l < L; ++l) rs[l] = bs[l];
+      reinterpret_cast<VT*>(x)[q] = VT{};
+    } else {
+      const VT yv = reinterpret_cast<const VT*>(y)[q];
+      const T* ys = reinterpret_cast<const T*>(&yv);
+#pragma unroll
+      for (int l = 0; l < L; ++l) rs[l] = bs[l] - ys[l];
+      reinterpret_cast<VT*>(y)[q] = VT{};
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) ds[l] = c0 * ss[l] * rs[l];
+    reinterpret_cast<VT*>(r)[q] = rv;
+    reinterpret_cast<VT*>(d)[q] = dv;
+  }
+  for (int64_t g = nv * L + tid; g < n; g += stride) {
+    T rv;
+    if (x_is_zero == 2) {
       d[g] = c0 * invD[g] * b[g];
       continue;
     }
@@ -47,19 +96,6 @@ __global__ void k_cheb4_init(int64_t n, const T* __restrict__ b, T* __restrict__
   }
 }
 
-// Vector type of 16 bytes for T (float4 / double2) and its lane count.
-template <typename T>
-struct V16;
-template <>
-struct V16<float> {
-  using type = float4;
-  static constexpr int L = 4;
-};
-template <>
-struct V16<double> {
-  using type = double2;
-  static constexpr int L = 2;
-};
 
 template <typename T, bool FIRST = false>
 __device__ __forceinline__ void cheb4_one(T& x, T& r, T& d, T& y, T s, T beta, T c1, T c2, T beta_next) {
@@ -190,15 +226,31 @@ __global__ void k_axpy(int64_t n, T a, const T* __restrict__ d, T* __restrict__ 
     x[g] += a * d[g];
 }
 
-template <typename T>
+template <typename T, bool VEC>
 __global__ void k_residual(int64_t n, const T* __restrict__ b, T* __restrict__ y, T* __restrict__ r, int64_t ld) {
   pdl_wait();
   { const int64_t off_ = (int64_t)blockIdx.y * ld; b += off_; y += off_; r += off_; }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+  using VT = typename V16<T>::type;
+  constexpr int L = V16<T>::L;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nv = VEC ? n / L : 0;
+  for (int64_t q = tid; q < nv; q += stride) {
+    const VT bv = reinterpret_cast<const VT*>(b)[q], yv = reinterpret_cast<const VT*>(y)[q];
+    const T* bs = reinterpret_cast<const T*>(&bv);
+    const T* ys = reinterpret_cast<const T*>(&yv);
+    VT rv;
+    T* rs = reinterpret_cast<T*>(&rv);
+#pragma unroll
+    for (int l = 0; l < L; ++l) rs[l] = bs[l] - ys[l];
+    reinterpret_cast<VT*>(r)[q] = rv;
+    reinterpret_cast<VT*>(y)[q] = VT{};
+  }
+  for (int64_t g = nv * L + tid; g < n; g += stride) {
     r[g] = b[g] - y[g];
     y[g] = T(0);
   }
 }
+
 
 template <typename Tin, typename Tout>
 __global__ void k_cast(int64_t n, const Tin* __restrict__ in, Tout* __restrict__ out, int64_t ldi, int64_t ldo) {
@@ -223,8 +275,14 @@ constexpr int kVecThreads = 256;
 template <typename T>
 void cheb4_init(int64_t n, const T* b, T* x, T* r, T* d, T* y, const T* invD, double c0, int x_is_zero,
                 cudaStream_t s, int nb, int64_t ld) {
-  launch_dep(k_cheb4_init<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, x, r, d, y, invD,
-             (T)c0, x_is_zero, ld ? ld : n);
+  if (!ld) ld = n;
+  const uintptr_t align = (uintptr_t)b | (uintptr_t)x | (uintptr_t)r | (uintptr_t)d | (uintptr_t)y | (uintptr_t)invD;
+  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
+    launch_dep(k_cheb4_init<T, true>, dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), dim3(kVecThreads), 0, s,
+               n, b, x, r, d, y, invD, (T)c0, x_is_zero, ld);
+  else
+    launch_dep(k_cheb4_init<T, false>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, x, r, d,
+               y, invD, (T)c0, x_is_zero, ld);
 }
 template <typename T, bool FIRST>
 static void launch_cheb4_step(int64_t n, T* x, T* r, T* d, T* y, const T* invD, double beta, double c1, double c2,
@@ -265,7 +323,13 @@ void axpy(int64_t n, double a, const T* d, T* x, cudaStream_t s, int nb, int64_t
 }
 template <typename T>
 void residual(int64_t n, const T* b, T* y, T* r, cudaStream_t s, int nb, int64_t ld) {
-  launch_dep(k_residual<T>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, y, r, ld ? ld : n);
+  if (!ld) ld = n;
+  const uintptr_t align = (uintptr_t)b | (uintptr_t)y | (uintptr_t)r;
+  if (align % 16 == 0 && (nb == 1 || (ld * sizeof(T)) % 16 == 0))
+    launch_dep(k_residual<T, true>, dim3(grid_for(n / V16<T>::L + 1, kVecThreads), nb), dim3(kVecThreads), 0, s, n,
+               b, y, r, ld);
+  else
+    launch_dep(k_residual<T, false>, dim3(grid_for(n, kVecThreads), nb), dim3(kVecThreads), 0, s, n, b, y, r, ld);
 }
 template <typename Tin, typename Tout>
 void cast(int64_t n, const Tin* in, Tout* out, cudaStream_t s, int nb, int64_t ldi, int64_t ldo) {
