@@ -294,7 +294,9 @@ void apply_into(chebmg_ctx* c, int j, const T* x, T* y) {
 
 template <typename T>
 void zero(chebmg_ctx* c, T* p, int64_t n) {
-  CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, c->s));
+  // inside a chain of programmatic dependent launches a zeroing kernel keeps the chain going
+  if (pdl_on(c->s)) zero_bytes(p, (int64_t)sizeof(T) * n, c->s);
+  else CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, c->s));
 }
 
 // lambda_min / lambda_max of the 1st-kind smoother of the given order: the option's fixed ratio,
@@ -541,7 +543,7 @@ CoarseCG coarse_args(chebmg_ctx* c, const double* b, double* x) {
 
 // Resets the control words of the persistent coarse kernels (the exchange needs no reset:
 // each launch takes fresh tags).
-void coarse_reset(chebmg_ctx* c) { CK(cudaMemsetAsync(c->cctl, 0, sizeof(unsigned) * 4, c->s)); }
+void coarse_reset(chebmg_ctx* c) { zero<unsigned>(c, c->cctl, 4); }
 
 // FP64 coarse solve on the last level: FD dense inverse, SEM Jacobi-PCG.
 int coarse_solve64(chebmg_ctx* c, const double* b, double* x) {

@@ -75,6 +75,10 @@ struct Stencil9 {
   T c[9];
 };
 
+// p[0 .. bytes) = 0 by a kernel (programmatic dependent launch when g_pdl is set; 16-byte
+// aligned p), else by a memset.
+void zero_bytes(void* p, int64_t bytes, cudaStream_t s);
+
 // ---- SEM kernels (y must be zeroed by the caller; results accumulate) ----
 // Every operator, transfer and vector kernel also runs on a batch of nb right-hand sides:
 // vector b of the batch starts at offset b * ld (ld = 0 means n; per-node data shared).

@@ -532,6 +532,25 @@ void dense_matvec(int n, const double* M, const double* x, double* y, cudaStream
   launch_dep(k_dense_matvec, dim3((n + 127) / 128, nb), dim3(128), 0, s, n, M, x, y, ld);
 }
 
+// p[0 .. bytes) = 0, 16-byte stores over the aligned body: the zeroing of a work vector as a
+// kernel, so that it joins a chain of programmatic dependent launches (a memset node would end it).
+__global__ void k_zero_bytes(unsigned char* __restrict__ p, int64_t bytes) {
+  pdl_wait();
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n16 = bytes / 16;
+  for (int64_t q = tid; q < n16; q += stride) reinterpret_cast<uint4*>(p)[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t g = n16 * 16 + tid; g < bytes; g += stride) p[g] = 0;
+}
+
+void zero_bytes(void* p, int64_t bytes, cudaStream_t s) {
+  if ((uintptr_t)p % 16 != 0 || bytes <= 0) {
+    cudaMemsetAsync(p, 0, (size_t)(bytes > 0 ? bytes : 0), s);
+    return;
+  }
+  launch_dep(k_zero_bytes, dim3(grid_for(bytes / 16 + 1, kVecThreads)), dim3(kVecThreads), 0, s,
+             static_cast<unsigned char*>(p), bytes);
+}
+
 // ===========================================================================
 // Deterministic FP64 reductions: fixed kRedBlocks partials, fixed-order finish
 // ===========================================================================
