@@ -1414,10 +1414,10 @@ void bfcg_start(chebmg_ctx* c, const double* B, int64_t ldb, double rtol) {
   if (rc != CHEBMG_OK && rc != CHEBMG_ENOTCONV) throw Error(rc, "V-cycle failed");
   if (bfcg_mixed(c)) {
     const float* z32 = vec<float>(L, VX);
-    bupdate_p_from<float>(n, ld, nb, z32, c->kp, c->bscal, true, c->s);
+    bupdate_p_from<float>(n, ld, nb, z32, c->kp, c->bscal, true, c->s, c->kq);
     bdot_zr_zq<float>(n, ld, nb, z32, c->kr, nullptr, BPOST_SET_RZ, c->bpart, c->bscal, c->bstat, c->s);
   } else {
-    bupdate_p_from<double>(n, ld, nb, c->kz, c->kp, c->bscal, true, c->s);
+    bupdate_p_from<double>(n, ld, nb, c->kz, c->kp, c->bscal, true, c->s, c->kq);
     bdot_zr_zq<double>(n, ld, nb, c->kz, c->kr, nullptr, BPOST_SET_RZ, c->bpart, c->bscal, c->bstat, c->s);
   }
   check_launch();
@@ -1428,7 +1428,7 @@ void bfcg_body1(chebmg_ctx* c) {
   Level& L = c->L[0];
   const int nb = c->nb;
   const int64_t n = L.n, ld = ldv(c, L);
-  zero<double>(c, c->kq, span(c, L));
+  // q was zeroed by the p update that precedes every body1
   if (c->outer_op == 1 && c->G_x2) {
     // the FP32-pair operator with the batched FP64 kernel's elements and right-hand sides per block
     const int v = L.beb[CHEBMG_F64];
@@ -1452,10 +1452,10 @@ void bfcg_body2(chebmg_ctx* c) {
   if (bfcg_mixed(c)) {
     const float* z32 = vec<float>(L, VX);
     bdot_zr_zq<float>(n, ld, nb, z32, c->kr, c->kq, BPOST_BETA_Q, c->bpart, c->bscal, c->bstat, c->s);
-    bupdate_p_from<float>(n, ld, nb, z32, c->kp, c->bscal, false, c->s);
+    bupdate_p_from<float>(n, ld, nb, z32, c->kp, c->bscal, false, c->s, c->kq);
   } else {
     bdot_zr_zq<double>(n, ld, nb, c->kz, c->kr, c->kq, BPOST_BETA_Q, c->bpart, c->bscal, c->bstat, c->s);
-    bupdate_p_from<double>(n, ld, nb, c->kz, c->kp, c->bscal, false, c->s);
+    bupdate_p_from<double>(n, ld, nb, c->kz, c->kp, c->bscal, false, c->s, c->kq);
   }
   check_launch();
 }

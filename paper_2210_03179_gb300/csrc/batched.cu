@@ -182,15 +182,47 @@ k_bdot_zr_zq(int64_t n, int64_t ld, int nblk, const Tz* __restrict__ z, const do
   }
 }
 
-template <typename Tz>
+// p = z + beta p per right-hand side (p = z first), and q = 0 when q is given (the next product
+// accumulates into it).  VEC: four entries per thread with 16-byte accesses, scalar tail.
+template <typename Tz, bool VEC>
 __global__ void __launch_bounds__(kThreads)
 k_bupdate_p_from(int64_t n, int64_t ld, const Tz* __restrict__ z, double* __restrict__ p,
-                 const double* __restrict__ scal, int first) {
+                 const double* __restrict__ scal, int first, double* __restrict__ q) {
   const int64_t off = (int64_t)blockIdx.y * ld;
   const double beta = first ? 0.0 : scal[blockIdx.y * S_NSLOTS + S_BETA];
-  for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n;
-       g += (int64_t)gridDim.x * kThreads)
-    p[g] = first ? to_f64(z[g]) : to_f64(z[g]) + beta * p[g];
+  z += off;
+  p += off;
+  if (q) q += off;
+  const int64_t tid = blockIdx.x * (int64_t)kThreads + threadIdx.x, stride = (int64_t)gridDim.x * kThreads;
+  const int64_t nq = VEC ? n / 4 : 0;
+  for (int64_t g = tid; g < nq; g += stride) {
+    double zv[4];
+    if constexpr (sizeof(Tz) == 4) {
+      const float4 z4 = reinterpret_cast<const float4*>(z)[g];
+      zv[0] = widen_f32(z4.x); zv[1] = widen_f32(z4.y); zv[2] = widen_f32(z4.z); zv[3] = widen_f32(z4.w);
+    } else {
+      const double2 a = reinterpret_cast<const double2*>(z)[2 * g], b = reinterpret_cast<const double2*>(z)[2 * g + 1];
+      zv[0] = a.x; zv[1] = a.y; zv[2] = b.x; zv[3] = b.y;
+    }
+    double2* p2 = reinterpret_cast<double2*>(p) + 2 * g;
+    if (first) {
+      p2[0] = make_double2(zv[0], zv[1]);
+      p2[1] = make_double2(zv[2], zv[3]);
+    } else {
+      const double2 a = p2[0], b = p2[1];
+      p2[0] = make_double2(fma(beta, a.x, zv[0]), fma(beta, a.y, zv[1]));
+      p2[1] = make_double2(fma(beta, b.x, zv[2]), fma(beta, b.y, zv[3]));
+    }
+    if (q) {
+      double2* q2 = reinterpret_cast<double2*>(q) + 2 * g;
+      q2[0] = make_double2(0.0, 0.0);
+      q2[1] = make_double2(0.0, 0.0);
+    }
+  }
+  for (int64_t g = nq * 4 + tid; g < n; g += stride) {
+    p[g] = first ? to_f64(z[g]) : fma(beta, p[g], to_f64(z[g]));
+    if (q) q[g] = 0.0;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -482,15 +514,21 @@ template void bdot_zr_zq<double>(int64_t, int64_t, int, const double*, const dou
 
 template <typename Tz>
 void bupdate_p_from(int64_t n, int64_t ld, int nb, const Tz* z, double* p, const double* scal, bool first,
-                    cudaStream_t s) {
-  int64_t g = (n + kThreads - 1) / kThreads;
+                    cudaStream_t s, double* q) {
+  const bool vec = ((uintptr_t)z | (uintptr_t)p | (uintptr_t)q) % 16 == 0 && (ld * sizeof(Tz)) % 16 == 0 &&
+                   (ld * sizeof(double)) % 16 == 0;
+  int64_t g = ((vec ? n / 4 + 1 : n) + kThreads - 1) / kThreads;
   if (g > 1024) g = 1024;
-  k_bupdate_p_from<Tz><<<dim3((unsigned)g, nb), kThreads, 0, s>>>(n, ld, z, p, scal, first ? 1 : 0);
+  if (vec)
+    k_bupdate_p_from<Tz, true><<<dim3((unsigned)g, nb), kThreads, 0, s>>>(n, ld, z, p, scal, first ? 1 : 0, q);
+  else
+    k_bupdate_p_from<Tz, false><<<dim3((unsigned)g, nb), kThreads, 0, s>>>(n, ld, z, p, scal, first ? 1 : 0, q);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
-template void bupdate_p_from<float>(int64_t, int64_t, int, const float*, double*, const double*, bool, cudaStream_t);
+template void bupdate_p_from<float>(int64_t, int64_t, int, const float*, double*, const double*, bool, cudaStream_t,
+                                    double*);
 template void bupdate_p_from<double>(int64_t, int64_t, int, const double*, double*, const double*, bool,
-                                     cudaStream_t);
+                                     cudaStream_t, double*);
 
 bool coarse_block_supported(int64_t n) { return n >= 1 && n <= (int64_t)kCBThreads * kCBMaxRows; }
 

@@ -454,7 +454,7 @@ void bdot_zr_zq(int64_t n, int64_t ld, int nb, const Tz* z, const double* r, con
                 double* part, double* scal, int* stat, cudaStream_t s);
 template <typename Tz>
 void bupdate_p_from(int64_t n, int64_t ld, int nb, const Tz* z, double* p, const double* scal, bool first,
-                    cudaStream_t s);
+                    cudaStream_t s, double* q_zero = nullptr);
 
 // Coarse PCG with one thread block per right-hand side (no grid-wide synchronisation).
 struct CoarseBlock {
