@@ -50,10 +50,20 @@ __device__ __forceinline__ bool finite(double v) { return v == v && fabs(v) <= 1
 // grid (nblk, nb): partial sums of (a0, b0) and (a1, b1) of right-hand side blockIdx.y
 __global__ void __launch_bounds__(kThreads)
 k_bdot2_partial(int64_t n, int64_t ld, int nblk, const double* __restrict__ a0, const double* __restrict__ b0,
-                const double* __restrict__ a1, const double* __restrict__ b1, double* __restrict__ part) {
+                const double* __restrict__ a1, const double* __restrict__ b1, double* __restrict__ part, int vec) {
   const int64_t off = (int64_t)blockIdx.y * ld;
   double s0 = 0.0, s1 = 0.0;
-  for (int64_t g = blockIdx.x * (int64_t)kThreads + threadIdx.x; g < n; g += (int64_t)nblk * kThreads) {
+  const int64_t tid = blockIdx.x * (int64_t)kThreads + threadIdx.x, stride = (int64_t)nblk * kThreads;
+  const int64_t n2 = vec ? n / 2 : 0;   // 16-byte pairs over the aligned body
+  for (int64_t g = tid; g < n2; g += stride) {
+    const double2 x = reinterpret_cast<const double2*>(a0 + off)[g], y = reinterpret_cast<const double2*>(b0 + off)[g];
+    s0 = fma(x.y, y.y, fma(x.x, y.x, s0));
+    if (a1) {
+      const double2 u = reinterpret_cast<const double2*>(a1 + off)[g], w = reinterpret_cast<const double2*>(b1 + off)[g];
+      s1 = fma(u.y, w.y, fma(u.x, w.x, s1));
+    }
+  }
+  for (int64_t g = 2 * n2 + tid; g < n; g += stride) {
     s0 += a0[off + g] * b0[off + g];
     if (a1) s1 += a1[off + g] * b1[off + g];
   }
@@ -146,11 +156,31 @@ k_bdot2_finish(int nblk, int post, const double* __restrict__ part, double* __re
 __global__ void __launch_bounds__(kThreads)
 k_bfcg_update_xr32(int64_t n, int64_t ld, int nblk, double* __restrict__ x, double* __restrict__ r,
                    float* __restrict__ r32, const double* __restrict__ p, const double* __restrict__ q,
-                   double* __restrict__ part, const double* __restrict__ scal) {
+                   double* __restrict__ part, const double* __restrict__ scal, int vec) {
   const int64_t off = (int64_t)blockIdx.y * ld;
   const double alpha = scal[blockIdx.y * S_NSLOTS + S_ALPHA];
   double s0 = 0.0, s1 = 0.0;
-  for (int64_t g = off + blockIdx.x * (int64_t)kThreads + threadIdx.x; g < off + n; g += (int64_t)nblk * kThreads) {
+  const int64_t tid = blockIdx.x * (int64_t)kThreads + threadIdx.x, stride = (int64_t)nblk * kThreads;
+  const int64_t n2 = vec ? n / 2 : 0;   // 16-byte pairs (8-byte for r32) over the aligned body
+  x += off;
+  r += off;
+  p += off;
+  q += off;
+  if (r32) r32 += off;
+  for (int64_t g = tid; g < n2; g += stride) {
+    double2 xv = reinterpret_cast<double2*>(x)[g], rv = reinterpret_cast<double2*>(r)[g];
+    const double2 pv = reinterpret_cast<const double2*>(p)[g], qv = reinterpret_cast<const double2*>(q)[g];
+    xv.x += alpha * pv.x;
+    xv.y += alpha * pv.y;
+    rv.x = rv.x - alpha * qv.x;
+    rv.y = rv.y - alpha * qv.y;
+    reinterpret_cast<double2*>(x)[g] = xv;
+    reinterpret_cast<double2*>(r)[g] = rv;
+    if (r32) reinterpret_cast<float2*>(r32)[g] = make_float2(narrow_f64(rv.x), narrow_f64(rv.y));
+    s0 += rv.x * rv.x;
+    s0 += rv.y * rv.y;
+  }
+  for (int64_t g = 2 * n2 + tid; g < n; g += stride) {
     x[g] += alpha * p[g];
     const double rn = r[g] - alpha * q[g];
     r[g] = rn;
@@ -486,7 +516,8 @@ int bred_blocks(int64_t n) {
 void bdot2(int64_t n, int64_t ld, int nb, const double* a0, const double* b0, const double* a1, const double* b1,
            int post, double rtol, double* part, double* scal, int* stat, cudaStream_t s) {
   const int nblk = bred_blocks(n);
-  k_bdot2_partial<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, a0, b0, a1, b1, part);
+  const int vec = ((uintptr_t)a0 | (uintptr_t)b0 | (uintptr_t)a1 | (uintptr_t)b1) % 16 == 0 && ld % 2 == 0;
+  k_bdot2_partial<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, a0, b0, a1, b1, part, vec);
   k_bdot2_finish<<<nb, kThreads, 0, s>>>(nblk, post, part, scal, stat, rtol);
   g_launches.fetch_add(2, std::memory_order_relaxed);
 }
@@ -494,7 +525,9 @@ void bdot2(int64_t n, int64_t ld, int nb, const double* a0, const double* b0, co
 void bfcg_update_xr32(int64_t n, int64_t ld, int nb, double* x, double* r, float* r32, const double* p,
                       const double* q, double* part, double* scal, int* stat, cudaStream_t s) {
   const int nblk = bred_blocks(n);
-  k_bfcg_update_xr32<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, x, r, r32, p, q, part, scal);
+  const int vec = ((uintptr_t)x | (uintptr_t)r | (uintptr_t)p | (uintptr_t)q) % 16 == 0 && (uintptr_t)r32 % 8 == 0 &&
+                  ld % 2 == 0;
+  k_bfcg_update_xr32<<<dim3(nblk, nb), kThreads, 0, s>>>(n, ld, nblk, x, r, r32, p, q, part, scal, vec);
   k_bdot2_finish<<<nb, kThreads, 0, s>>>(nblk, BPOST_CHECK, part, scal, stat, 0.0);
   g_launches.fetch_add(2, std::memory_order_relaxed);
 }
