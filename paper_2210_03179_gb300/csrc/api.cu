@@ -881,7 +881,8 @@ T* upload(chebmg_ctx* c, const std::vector<double>& h) {
 }
 
 // Picks the elements-per-block of the order-7 operator by timing each candidate on the
-// level's own data (3 launches each, best of them) -- a small autotuner run once at setup.
+// level's own data (6 launches each, best of them: variants within a few per cent of each other
+// are told apart more reliably than by 3) -- a small autotuner run once at setup.
 template <typename T>
 void autotune_ax8(chebmg_ctx* c, int j) {
   Level& L = c->L[j];
@@ -901,7 +902,7 @@ void autotune_ax8(chebmg_ctx* c, int j) {
     L.eb[dt] = eb;
     apply_into<T>(c, j, x, y);   // warm-up / first-launch configuration
     float t_min = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
+    for (int rep = 0; rep < 6; ++rep) {
       CK(cudaEventRecord(e0, c->s));
       apply_into<T>(c, j, x, y);
       CK(cudaEventRecord(e1, c->s));
