@@ -3046,8 +3046,6 @@ int chebmg_selftest_coarse_timeout(chebmg_ctx* c, int* status) {
     enter(c);
     if (!status) throw Error(CHEBMG_EINVAL, "status is NULL");
     if (!c->cctl || !c->coop_ok) throw Error(CHEBMG_EINVAL, "no persistent coarse solver in this context");
-    Level& C = c->L.back();
-    const int64_t n = C.n;
     coarse_reset(c);
     CK(cudaMemsetAsync(c->cctl + 4, 0, sizeof(unsigned), c->s));
     CoarseCG a = coarse_args(c, c->cb, c->cx);
